@@ -1,0 +1,279 @@
+"""Seeded geometry generators for the ternary (two fluids + one solid) LB workloads.
+
+Every array is float64, C order, indexed ``[y, x]`` in 2D and ``[z, y, x]`` in
+3D (x fastest).  Node ``(x, y)`` sits at integer coordinates; a half-way
+bounce-back wall lies half a spacing outside the first and last node.
+
+Diffuse profiles follow the paper's initial conditions (Sec. 4.1-4.3, 4.6):
+a phase indicator across an interface at signed distance ``d`` (positive
+inside) of width ``W`` is ``1/2 + 1/2 tanh(2 d / W)``.  The solid indicator is
+``phi0`` and the droplet / driving fluid is ``phi1 = (1 - phi0) * indicator``.
+
+Nothing here is part of the method; it only produces inputs.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "diffuse",
+    "Geometry",
+    "wall_droplet",
+    "wall_cap",
+    "cylinder_droplet",
+    "free_drop",
+    "flat_layer",
+    "random_disks_droplet",
+    "rsa_spheres",
+    "porous_inlet_slab",
+    "splitmix64",
+]
+
+
+def diffuse(signed_distance, W):
+    """``1/2 + 1/2 tanh(2 d / W)``: 1 well inside (d > 0), 0 well outside."""
+    return 0.5 + 0.5 * np.tanh(2.0 * np.asarray(signed_distance, dtype=np.float64) / W)
+
+
+@dataclasses.dataclass
+class Geometry:
+    """A lattice workload: fields plus the descriptors the diagnostics need."""
+
+    phi0: np.ndarray
+    phi1: np.ndarray
+    periodic: tuple
+    # probe line used for the droplet height: origin node coordinates and axis
+    probe_origin: tuple = (0.0, 0.0)
+    probe_axis: int = 1
+    # wall level (flat wall, in node coordinates) or solid disk radius/centre
+    wall_level: float | None = None
+    disk_center: tuple | None = None
+    disk_radius: float | None = None
+    droplet_radius: float | None = None
+    kappa: float = 0.0
+    note: str = ""
+
+    @property
+    def shape(self):
+        return self.phi0.shape
+
+
+def _grid2(nx, ny):
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y
+
+
+def wall_droplet(nx=128, ny=64, wall_rows=8, R=25.0, W=4.0, xc=None):
+    """Half-disk droplet resting on a flat solid wall (Sec. 4.2 set-up).
+
+    The bottom ``wall_rows`` rows are solid: the wall surface lies at
+    ``y_w = wall_rows - 1/2``.  The droplet of radius ``R`` is centred on the
+    wall at ``(xc, y_w)``; x is periodic, y has no-flux walls.
+    """
+    x, y = _grid2(nx, ny)
+    yw = wall_rows - 0.5
+    xc = nx / 2.0 if xc is None else xc
+    phi0 = diffuse(yw - y, W)
+    r = np.hypot(x - xc, y - yw)
+    phi1 = (1.0 - phi0) * diffuse(R - r, W)
+    return Geometry(phi0, phi1, (True, False), probe_origin=(xc, 0.0), probe_axis=1,
+                    wall_level=yw, droplet_radius=R, kappa=0.0,
+                    note=f"flat wall, {nx}x{ny}, wall rows {wall_rows}, R={R}, W={W}")
+
+
+def wall_cap(nx=64, ny=40, wall_rows=8, R0=15.0, theta_deg=60.0, W=4.0, xc=None):
+    """Circular cap resting on a flat wall with apparent contact angle ``theta_deg``.
+
+    The cap holds the area of a half-disk of radius ``R0`` (pi R0^2 / 2), so
+    its circle radius is R = R0 sqrt((pi/2)/(t - sin t cos t)) and its centre
+    sits R cos(t) below the wall surface (Sec. 4.2 geometry).  x periodic,
+    y walls.
+    """
+    x, y = _grid2(nx, ny)
+    yw = wall_rows - 0.5
+    xc = nx / 2.0 if xc is None else xc
+    t = math.radians(theta_deg)
+    R = R0 * math.sqrt((math.pi / 2.0) / (t - math.sin(t) * math.cos(t)))
+    yc = yw - R * math.cos(t)
+    phi0 = diffuse(yw - y, W)
+    phi1 = (1.0 - phi0) * diffuse(R - np.hypot(x - xc, y - yc), W)
+    return Geometry(phi0, phi1, (True, False), probe_origin=(xc, 0.0), probe_axis=1,
+                    wall_level=yw, droplet_radius=R0, kappa=0.0,
+                    note=f"cap theta={theta_deg} on flat wall, {nx}x{ny}, R0={R0}, W={W}")
+
+
+def cylinder_droplet(n=1024, Rs=160.0, R0=120.0, W=4.0, ny=None):
+    """Droplet of radius ``R0`` centred on the top of a solid disk (Sec. 4.3 set-up).
+
+    The disk of radius ``Rs`` is centred at ``(n/2, ny/2)``; all sides periodic.
+    The dimensionless curvature is ``kappa = R0 / Rs`` as in Sec. 4.3.
+    """
+    nx = n
+    ny = n if ny is None else ny
+    x, y = _grid2(nx, ny)
+    xc, yc = nx / 2.0, ny / 2.0
+    phi0 = diffuse(Rs - np.hypot(x - xc, y - yc), W)
+    phi1 = (1.0 - phi0) * diffuse(R0 - np.hypot(x - xc, y - (yc + Rs)), W)
+    return Geometry(phi0, phi1, (True, True), probe_origin=(xc, yc), probe_axis=1,
+                    disk_center=(xc, yc), disk_radius=Rs, droplet_radius=R0, kappa=R0 / Rs,
+                    note=f"disk Rs={Rs}, droplet R0={R0}, {nx}x{ny}, W={W}")
+
+
+def free_drop(nx=96, ny=96, R=24.0, W=4.0):
+    """Circular drop of fluid 1 in fluid 2, no solid, all periodic (Laplace test)."""
+    x, y = _grid2(nx, ny)
+    phi0 = np.zeros((ny, nx))
+    phi1 = diffuse(R - np.hypot(x - nx / 2.0, y - ny / 2.0), W)
+    return Geometry(phi0, phi1, (True, True), probe_origin=(nx / 2.0, ny / 2.0), probe_axis=1,
+                    droplet_radius=R, note=f"free drop R={R}, {nx}x{ny}, W={W}")
+
+
+def flat_layer(nx=4, ny=128, W=4.0, y_lo=None, y_hi=None):
+    """Slab of fluid 1 between two flat interfaces, no solid, all periodic."""
+    x, y = _grid2(nx, ny)
+    y_lo = ny / 4.0 if y_lo is None else y_lo
+    y_hi = 3.0 * ny / 4.0 if y_hi is None else y_hi
+    phi0 = np.zeros((ny, nx))
+    # slab [y_lo, y_hi] as the intersection of two half-planes
+    phi1 = diffuse(y - y_lo, W) * diffuse(y_hi - y, W)
+    return Geometry(phi0, phi1, (True, True), probe_origin=(0.0, 0.0), probe_axis=1,
+                    note=f"flat slab {nx}x{ny}, interfaces at {y_lo},{y_hi}, W={W}")
+
+
+# --- seeded random geometry ---------------------------------------------------
+
+def splitmix64(seed):
+    """A tiny seeded uniform generator (SplitMix64), returned as a closure on [0, 1)."""
+    state = [seed & 0xFFFFFFFFFFFFFFFF]
+
+    def nxt():
+        state[0] = (state[0] + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+        z = state[0]
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+        z ^= z >> 31
+        return (z >> 11) / float(1 << 53)
+
+    return nxt
+
+
+def random_disks_droplet(n=256, seed=0, W=4.0, ny=None):
+    """1-6 non-overlapping solid disks (radii 8-40) plus one droplet (radius 10-60).
+
+    The droplet is placed on top of the largest disk; kappa = R0 / max(Rs)
+    (minimum curvature of the solid is that of its largest disk).  All sides
+    periodic.  Returns the geometry and the drawn contact angle in degrees
+    (uniform in 30-150).
+    """
+    u = splitmix64(seed * 7919 + 17)
+    nx = n
+    ny = n if ny is None else ny
+    ndisk = 1 + int(u() * 6)
+    disks = []
+    tries = 0
+    while len(disks) < ndisk and tries < 10000:
+        tries += 1
+        r = 8.0 + 32.0 * u()
+        r = min(r, 0.2 * min(nx, ny))
+        cx, cy = nx * u(), ny * u()
+        ok = True
+        for (qx, qy, qr) in disks:
+            dx = min(abs(cx - qx), nx - abs(cx - qx))
+            dy = min(abs(cy - qy), ny - abs(cy - qy))
+            if math.hypot(dx, dy) < r + qr + 2.0 * W:
+                ok = False
+                break
+        if ok:
+            disks.append((cx, cy, r))
+    x, y = _grid2(nx, ny)
+    phi0 = np.zeros((ny, nx))
+    for (cx, cy, r) in disks:
+        dx = np.abs(x - cx)
+        dx = np.minimum(dx, nx - dx)
+        dy = np.abs(y - cy)
+        dy = np.minimum(dy, ny - dy)
+        phi0 = np.maximum(phi0, diffuse(r - np.hypot(dx, dy), W))
+    big = max(disks, key=lambda d: d[2])
+    R0 = 10.0 + 50.0 * u()
+    R0 = min(R0, 0.2 * min(nx, ny))
+    cx, cy = big[0], big[1] + big[2]
+    dx = np.abs(x - cx)
+    dx = np.minimum(dx, nx - dx)
+    dy = np.abs(y - cy)
+    dy = np.minimum(dy, ny - dy)
+    phi1 = (1.0 - phi0) * diffuse(R0 - np.hypot(dx, dy), W)
+    theta = 30.0 + 120.0 * u()
+    g = Geometry(phi0, phi1, (True, True), probe_origin=(big[0], big[1]), probe_axis=1,
+                 disk_center=(big[0], big[1]), disk_radius=big[2], droplet_radius=R0,
+                 kappa=R0 / big[2], note=f"{len(disks)} disks, seed {seed}")
+    return g, theta
+
+
+def rsa_spheres(n=256, seed=0, rmin=10.0, rmax=20.0, target_solid=0.4, max_fail=1_000_000):
+    """Random sequential addition of non-overlapping spheres with periodic images.
+
+    Radii uniform in ``[rmin, rmax]``; stops when the sharp solid fraction
+    reaches ``target_solid`` or after ``max_fail`` consecutive rejections.
+    Returns the list ``[(cx, cy, cz, r), ...]``.
+    """
+    u = splitmix64(seed * 104729 + 3)
+    L = float(n)
+    spheres = []
+    vol = 0.0
+    fails = 0
+    while vol / L ** 3 < target_solid and fails < max_fail:
+        r = rmin + (rmax - rmin) * u()
+        c = (L * u(), L * u(), L * u())
+        ok = True
+        for (qx, qy, qz, qr) in spheres:
+            d2 = 0.0
+            for a, b in zip(c, (qx, qy, qz)):
+                d = abs(a - b)
+                d = min(d, L - d)
+                d2 += d * d
+            if d2 < (r + qr) ** 2:
+                ok = False
+                break
+        if ok:
+            spheres.append((c[0], c[1], c[2], r))
+            vol += 4.0 / 3.0 * math.pi * r ** 3
+            fails = 0
+        else:
+            fails += 1
+    return spheres
+
+
+def porous_inlet_slab(n=256, seed=0, W=4.0, slab=32.0, rmin=10.0, rmax=20.0, target_solid=0.4,
+                      spheres=None):
+    """3D porous workload: RSA spheres (tanh phi0) with fluid 1 filling the slab x < ``slab``.
+
+    All sides periodic.  Returns the geometry; ``note`` records the achieved
+    diffuse porosity ``1 - mean(phi0)``.
+    """
+    if spheres is None:
+        spheres = rsa_spheres(n, seed, rmin, rmax, target_solid)
+    ax = np.arange(n, dtype=np.float64)
+    phi0 = np.zeros((n, n, n))
+    for (cx, cy, cz, r) in spheres:
+        lo = [int(math.floor(c - r - 2 * W)) for c in (cz, cy, cx)]
+        hi = [int(math.ceil(c + r + 2 * W)) + 1 for c in (cz, cy, cx)]
+        iz = np.arange(lo[0], hi[0]) % n
+        iy = np.arange(lo[1], hi[1]) % n
+        ix = np.arange(lo[2], hi[2]) % n
+        dz = np.arange(lo[0], hi[0]) - cz
+        dy = np.arange(lo[1], hi[1]) - cy
+        dx = np.arange(lo[2], hi[2]) - cx
+        d = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
+        blk = diffuse(r - d, W)
+        sub = phi0[np.ix_(iz, iy, ix)]
+        phi0[np.ix_(iz, iy, ix)] = np.maximum(sub, blk)
+    del ax
+    x = np.arange(n, dtype=np.float64)[None, None, :]
+    phi1 = (1.0 - phi0) * diffuse(slab - x, W)
+    phi1 = np.broadcast_to(phi1, phi0.shape).copy()
+    poro = 1.0 - phi0.mean()
+    return Geometry(phi0, phi1, (True, True, True), probe_origin=(0.0, 0.0, 0.0), probe_axis=0,
+                    note=f"{len(spheres)} RSA spheres r in [{rmin},{rmax}], seed {seed}, porosity {poro:.4f}")

@@ -1,0 +1,22 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
+
+
+@pytest.fixture(scope="session")
+def lbm_lib():
+    """The built CUDA library (built in-tree on first use)."""
+    from paper_2311_05091_gb300.build import build
+    build()
+    from paper_2311_05091_gb300 import _lbm
+    _lbm.library()
+    return _lbm

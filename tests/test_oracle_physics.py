@@ -1,0 +1,142 @@
+"""Physics pins of the FP64 oracle: what the paper and the mathematics fix.
+
+* exact conservation of sum phi1 (zeroth moments of f^eq and R, Sec. 3);
+* the flat-interface profile 1/2 + 1/2 tanh(2x/D) (equilibrium of the free energy of Sec. 2.1);
+* the Laplace law dp = sigma / R of a free 2D drop;
+* Young's law on a flat wall (Sec. 4.2) with the k closure of Eq. kk;
+* the viscosity relation of Sec. 3 (shear-wave decay along an axis and a diagonal);
+* independence from the constant rho_0 inside lambda_0;
+* linear stability at rest of the NS rate reading (s0 = s4 = s2a).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lbm, model
+from oracle import observables as ob
+from synthetic import free_drop, wall_cap, wall_droplet
+from synthetic.geometry import Geometry
+
+
+def _run(geo, prm, steps, lattice="D2Q9"):
+    st = lbm.init_state(lattice, geo.phi0, geo.phi1, prm, geo.periodic)
+    lbm.step(st, nsteps=steps)
+    return st
+
+
+def test_mass_conservation_flat_wall_128x64():
+    geo = wall_droplet(128, 64, 8, 25.0, 4.0)
+    prm = model.Params(theta_deg=60.0, sigma=0.01, d0=0.5)
+    st = lbm.init_state("D2Q9", geo.phi0, geo.phi1, prm, geo.periodic)
+    m0 = st.f.sum()
+    lbm.step(st, nsteps=1000)
+    assert abs(st.f.sum() - m0) / m0 < 1e-12
+    assert abs(st.macro["phi1"].sum() - m0) / m0 < 1e-12
+
+
+def test_flat_interface_tanh_profile():
+    ny, W = 64, 4.0
+    y = np.arange(ny, dtype=float)
+    phi1 = (0.5 + 0.5 * np.tanh(2 * (y - 16) / W)) * (0.5 + 0.5 * np.tanh(2 * (48 - y) / W))
+    geo = Geometry(np.zeros((ny, 1)), phi1[:, None], (True, True))
+    st = _run(geo, model.Params(W=W, sigma=0.01, mu=(0.1, 0.1, 0.1)), 600)
+    prof = 0.5 + 0.5 * np.tanh(2 * (y - 16) / W)
+    lower = slice(4, 32)
+    assert np.abs(st.macro["phi1"][lower, 0] - prof[lower]).max() < 1e-2
+    # a visibly different width fails: the profile really is of width W
+    wrong = 0.5 + 0.5 * np.tanh(2 * (y - 16) / (1.3 * W))
+    assert np.abs(st.macro["phi1"][lower, 0] - wrong[lower]).max() > 3e-2
+
+
+def test_laplace_law_free_drop():
+    geo = free_drop(64, 64, 16.0, 4.0)
+    prm = model.Params(sigma=0.01, mu=(0.3, 0.3, 0.3))
+    st = _run(geo, prm, 3000)
+    R = math.sqrt(st.macro["phi1"].sum() / math.pi)
+    dp = ob.laplace_dp(geo.phi0, st.macro["phi1"], st.macro["p"])
+    assert abs(dp * R / prm.sigma - 1.0) < 0.02, dp * R / prm.sigma
+
+
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+def test_young_law_flat_wall(theta):
+    # a cap placed at the prescribed angle keeps it (R0 = 25 lu, D = 4 lu)
+    geo = wall_cap(96, 48, 8, 25.0, theta, 4.0)
+    prm = model.Params(theta_deg=theta, sigma=0.02, mu=(0.1, 0.1, 0.1))
+    st = _run(geo, prm, 2000)
+    th = ob.flat_wall_angle(geo.phi0, st.macro["phi1"], 48)[0]
+    assert abs(th - theta) < 1.0, th
+
+
+def _shear_rate(d0, diagonal, nu=0.02, t1=100, t2=500):
+    """Measured decay rate of a small shear wave, against nu k^2."""
+    n = 48
+    y, x = np.meshgrid(np.arange(n, dtype=float), np.arange(n if diagonal else 2, dtype=float), indexing="ij")
+    kx = 2 * math.pi / n
+    prm = model.Params(d0=d0, mu=(nu, nu, nu))
+    geo = Geometry(np.zeros(y.shape), np.zeros(y.shape), (True, True))
+    st = lbm.init_state("D2Q9", geo.phi0, geo.phi1, prm, geo.periodic)
+    U = 1e-4
+    if diagonal:
+        arg = kx * (x + y)
+        ux, uy = U * np.sin(arg), -U * np.sin(arg)
+        k2 = 2 * kx * kx
+    else:
+        ux, uy = U * np.sin(kx * y), 0 * y
+        k2 = kx * kx
+    # first-order velocity perturbation: g_i += w_i c_i . (rho u) / cs2
+    for i, ci in enumerate(st.lat.c):
+        st.g[i] += st.lat.w[i] * (ci[0] * ux + ci[1] * uy) / st.lat.cs2
+    st.hist_u = np.stack([ux, uy])
+    amps = []
+    for t in (t1, t2 - t1):
+        lbm.step(st, nsteps=t)
+        u = st.macro["u"]
+        amps.append(np.sum(u[0] * ux) / np.sum(ux * ux))
+    return -math.log(amps[1] / amps[0]) / (t2 - t1), nu * k2
+
+
+@pytest.mark.parametrize("d0", [1.0 / 3.0, 0.5])
+@pytest.mark.parametrize("diagonal", [False, True])
+def test_viscosity_relation_shear_wave(d0, diagonal):
+    # mu/(rho(1-phi0)) = (1/s2a - 1/2)(c^2 - cs2)/2 = (1/s2b - 1/2) cs2: both the axis-aligned
+    # (s2b) and the diagonal (s2a) shear wave decay at nu k^2 (to the O(k^2) lattice error)
+    rate, expect = _shear_rate(d0, diagonal)
+    assert abs(rate / expect - 1.0) < 1e-2, (rate, expect)
+
+
+def test_pressure_reference_constant_is_inert():
+    geo = wall_droplet(48, 32, 6, 10.0, 4.0)
+    base = dict(theta_deg=70.0, sigma=0.01, rho=(2.0, 3.0, 1.0), mu=(0.03, 0.05, 0.02))
+    a = _run(geo, model.Params(**base), 60)
+    b = _run(geo, model.Params(**base, rho_ref=17.0), 60)
+    for k in ("phi1", "u", "p"):
+        assert np.abs(a.macro[k] - b.macro[k]).max() < 1e-12 * max(1.0, np.abs(a.macro[k]).max()) + 1e-15
+
+
+def _spectral_radius(d0, mu, n=8):
+    prm = model.Params(d0=d0, mu=(mu, mu, mu))
+    geo = Geometry(np.zeros((n, n)), np.zeros((n, n)), (True, True))
+    c = model.constants(prm)
+    st0 = lbm.init_state("D2Q9", geo.phi0, geo.phi1, prm, geo.periodic)
+    g0 = st0.g.copy()
+    eps = 1e-7
+
+    def one(g):
+        st = lbm.init_state("D2Q9", geo.phi0, geo.phi1, prm, geo.periodic)
+        st.g = g
+        lbm.step(st, c, 1)
+        return st.g
+
+    ref = one(g0.copy())
+    A = np.zeros((g0.size, g0.size))
+    for j in range(g0.size):
+        gp = g0.copy().ravel()
+        gp[j] += eps
+        A[:, j] = (one(gp.reshape(g0.shape)) - ref).ravel() / eps
+    return np.abs(np.linalg.eigvals(A)).max()
+
+
+@pytest.mark.parametrize("d0,mu", [(1.0 / 3.0, 0.01), (0.5, 0.01), (0.5, 0.2)])
+def test_ns_rate_reading_is_linearly_stable(d0, mu):
+    assert _spectral_radius(d0, mu) < 1.0 + 1e-6
