@@ -1,0 +1,224 @@
+/*
+ * lbm.h -- C ABI of the GB300 library for the ternary "2f1s" phase-field
+ * lattice Boltzmann method of Zhan, Chai and Shi, "A ternary phase-field model
+ * for two-phase flows in complex geometries" (arXiv 2311.05091).
+ *
+ * Model.  Phase 0 is a frozen, diffuse solid (indicator phi0), phase 1 the
+ * droplet / driving fluid (phi1, the only evolved order parameter), phase 2
+ * the other fluid, phi2 = 1 - phi0 - phi1 (Sec. 2.2, Remarks 1-3).  Each time
+ * step (Sec. 2 and Sec. 3):
+ *   1. phi1 = sum_i f_i over the Cahn-Hilliard (CH) populations;
+ *   2. isotropic central stencils give grad / Laplacian of phi0, phi1;
+ *   3. chemical potentials mu_p = df_b/dphi_p - (3D/4) gamma_p lap phi_p and
+ *      mubar_1 = gamma_T/3 sum_{q != 1} (mu_1 - mu_q)/gamma_q (Sec. 2.1);
+ *   4. grad mubar_1, degenerate mobility, mass flux S, surface-tension force
+ *      F_s = sum mu_p grad phi_p, correction force F_c = div(S u - u S)/2,
+ *      body force, solid penalisation force (Sec. 2.3, Sec. 3);
+ *   5. Hermite-moment collision of the CH populations f (Sec. 3, Sec. 4 intro);
+ *   6. Hermite-moment collision of the Navier-Stokes (NS) populations g with
+ *      the pressure formulation and second-order force moment M^2F;
+ *   7. streaming with half-way bounce-back on non-periodic axes.
+ * The spreading coefficients follow Young's law with s01 = k s12 and the
+ * closure k(theta, kappa) of Eq. kk (Sec. 2.2).
+ *
+ * Lattice units: dx = dt = c = 1, cs^2 = d0 (scale factor).
+ *
+ * Layout.  Every field is float32, structure of arrays, x fastest:
+ *   scalar field   [b][z][y][x]            (b = instance of a batch)
+ *   vector field   [b][a][z][y][x]         (a = x, y[, z] component)
+ *   populations    [b][i][z][y][x]         (i = lattice direction)
+ * 2D lattices have nz = 1.  D2Q9 directions follow the paper's printed M0:
+ *   0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1).
+ * D3Q19 directions: 0 rest; 1..6 (+x,-x,+y,-y,+z,-z); 7..18 edges
+ *   (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
+ *   (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1).
+ *
+ * Ownership.  A context owns all of its device memory (allocated in
+ * lbm_create*, freed in lbm_destroy).  Host pointers passed in are read or
+ * written during the call only and never kept.  Device pointers passed to
+ * the *_device calls must stay valid until the work enqueued by that call
+ * has completed on the context's stream.
+ *
+ * Streams.  Every device operation is enqueued on the context's stream
+ * (lbm_set_stream; by default a stream the context creates).  Calls that
+ * return host data synchronise that stream.
+ *
+ * Errors.  Every call returns an lbm_status and never aborts the process.
+ * Invalid arguments give LBM_EINVAL and leave the context unchanged.  A
+ * failed CUDA call gives LBM_ECUDA; the context is then marked failed and
+ * every later call except lbm_destroy and lbm_last_error returns LBM_ESTATE.
+ * Asynchronous failures and divergence (NaN or |u| > 0.5 found by the step
+ * that closes each lbm_step call) surface at the next synchronising call
+ * (lbm_sync, lbm_get_*, lbm_observables) as LBM_ECUDA / LBM_EDIVERGED.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,      /* invalid argument                                  */
+  LBM_ENOMEM = -2,      /* device or host allocation failed                  */
+  LBM_ECUDA = -3,       /* a CUDA runtime call failed                        */
+  LBM_EDIVERGED = -4,   /* NaN or |u| > 0.5 detected                          */
+  LBM_ETIMEOUT = -5,    /* a bounded device wait gave up                     */
+  LBM_ESTATE = -6,      /* context not initialised, or failed earlier        */
+  LBM_EUNSUPPORTED = -7 /* lattice / option not built                        */
+} lbm_status;
+
+typedef enum {
+  LBM_D2Q9 = 0,   /* 2D, Appendix A weights and matrices                     */
+  LBM_D3Q19 = 1   /* 3D, weights from the same moment conditions (d0 < 1/2)  */
+} lbm_lattice;
+
+/* Periodicity bit mask; a clear bit means half-way bounce-back walls (no-flux
+ * for phi1, no-slip for u) half a spacing outside the first and last node. */
+enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };
+
+/* Physical and numerical parameters of one instance (lattice units). */
+typedef struct {
+  double W;             /* interface thickness D (Sec. 2.1), > 0                     */
+  double M_deg;         /* degenerate mobility coefficient (Sec. 2.2), >= 0         */
+  double M_cst;         /* constant mobility part, >= 0, M_cst + M_deg > 0          */
+  double theta_deg;     /* contact angle of fluid 1 on the solid, in (0, 180)       */
+  double kappa;         /* minimum dimensionless solid curvature (Eq. kk), > -1      */
+  double sigma;         /* fluid-fluid tension sigma_12, > 0                        */
+  double rho[3];        /* densities of solid, fluid 1, fluid 2, > 0                */
+  double mu[3];         /* dynamic viscosities of solid, fluid 1, fluid 2, > 0      */
+  double d0;            /* scale factor cs^2 = d0: (0,1) for D2Q9, (0,1/2) D3Q19    */
+  double eta_hat;       /* CH parameter eta_1 = eta_hat / gamma_1, > 0 (0.1)        */
+  double s_free_ch;     /* CH rates s0, s2a, s2b, s3, s4, in (0,2) (1)              */
+  double s_free_ns;     /* NS rates s1, s3, in (0,2) (1)                            */
+  double body_force[3]; /* body-force density b; F_b = (1 - phi0) b                 */
+} lbm_params;
+
+/* Diagnostics of one instance, computed from the fields of the last step
+ * (time t-1 after t steps): sums in float64 (Sec. 4.2-4.3 diagnostics). */
+typedef struct {
+  double mass1;      /* sum of phi1                                          */
+  double mass0;      /* sum of phi0                                          */
+  double umax;       /* max |u|                                              */
+  double p_in;       /* mean pressure where phi1 >= 0.99                      */
+  double p_out;      /* mean pressure where phi2 >= 0.99                      */
+  double dp;         /* p_in - p_out (Laplace pressure)                      */
+  int64_t n_in;      /* nodes in the p_in set                                 */
+  int64_t n_out;     /* nodes in the p_out set                                */
+  int64_t step;      /* completed steps                                       */
+} lbm_obs;
+
+/* Fill *p with the defaults: W 4, M_deg 0.1, M_cst 0, theta 90, kappa 0,
+ * sigma 0.01, rho 1, mu 0.01, d0 0.5 (Appendix A), eta_hat 0.1, free rates 1,
+ * no body force.  Returns LBM_EINVAL if p is NULL. */
+int lbm_default_params(lbm_params* p);
+
+/* Create a context for one lattice of nx * ny * nz nodes (nz = 1 for D2Q9).
+ * Derives k, gamma_p, gamma_T, eta_1 and the CH rate s1 from *p (Sec. 2.2,
+ * Sec. 3) on the host in float64 and allocates the device state.  Axes
+ * without their LBM_PERIODIC_* bit need at least 2 nodes.  On success *out
+ * holds the context; the state is not initialised until lbm_set_phase. */
+int lbm_create(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask,
+               const lbm_params* p, lbm_ctx** out);
+
+/* Same, for nbatch independent instances of the same size advanced together
+ * by one launch per step; params points to nbatch parameter sets. */
+int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask,
+                     int nbatch, const lbm_params* params, lbm_ctx** out);
+
+/* Free all device memory of the context.  Safe on NULL. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Enqueue all later work on `stream` (a cudaStream_t, may be NULL for the
+ * legacy default stream, which disables CUDA-graph replay).  The caller keeps
+ * ownership of the stream and must keep it alive while the context uses it. */
+int lbm_set_stream(lbm_ctx* ctx, void* stream);
+
+/* Launch tuning; results do not depend on it.  strip >= 1: rows (D2Q9) or
+ * planes (D3Q19) swept by one CTA of the step kernel.  depth in 1..3: rows
+ * of asynchronous global-to-shared copies each CTA keeps in flight (0 keeps
+ * the current value). */
+int lbm_set_launch(lbm_ctx* ctx, int strip, int depth);
+
+/* Kernel timing.  While enabled, every step-kernel launch is bracketed by a
+ * pair of CUDA events recorded on the context's stream (CUDA-graph replay is
+ * off meanwhile).  lbm_kernel_time synchronises, returns the summed device
+ * duration (ms) and the number of launches timed since the last read, and
+ * starts a new count.  Outputs may be NULL. */
+int lbm_set_profiling(lbm_ctx* ctx, int enable);
+int lbm_kernel_time(lbm_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Copy the solid indicator phi0 (host, nbatch*nz*ny*nx floats) to the device. */
+int lbm_set_solid(lbm_ctx* ctx, const float* phi0_host);
+int lbm_set_solid_device(lbm_ctx* ctx, const float* phi0_dev);
+
+/* Copy the initial phi1 (host, same size), then initialise every node at
+ * equilibrium: f = f^eq(phi1, mubar_1(phi1), u = 0), g = g^eq(p = 0, u = 0),
+ * history (phi1, u = 0, S = 0); resets the step count.  Requires lbm_set_solid. */
+int lbm_set_phase(lbm_ctx* ctx, const float* phi1_host);
+int lbm_set_phase_device(lbm_ctx* ctx, const float* phi1_dev);
+
+/* Enqueue n >= 0 coupled time steps (one fused kernel per step for D2Q9;
+ * replayed from a captured CUDA graph where the stream allows).  Returns once
+ * the work is enqueued.  The last step also writes the pressure field and
+ * checks for divergence. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Wait for the context's stream; report deferred errors. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Macroscopic fields of the last step (time t-1): phi1 (scalar), u (vector,
+ * d components), p (scalar); host buffers, any may be NULL.  Synchronous. */
+int lbm_get_fields(lbm_ctx* ctx, float* phi1, float* u, float* p);
+
+/* Current populations f (CH) and g (NS), host buffers of nbatch*Q*nodes
+ * floats.  The rest population g_0 is stored minus the constant rho_0 of the
+ * pressure equilibrium (lambda_0, Sec. 3), which the dynamics do not depend
+ * on.  Either pointer may be NULL.  Synchronous. */
+int lbm_get_populations(lbm_ctx* ctx, float* f, float* g);
+
+/* Checkpoint: the whole evolving state (populations, history, step count) as
+ * a byte image: a 64-byte header (uint32 magic "LBM1", int32 lattice, nx, ny,
+ * nz, nbatch, q, d, int64 step, int64 nodes, 16 bytes padding) followed by
+ * float32 f [b][i][nodes], g [b][i][nodes] (g_0 minus rho_0) and the history
+ * [b][k][nodes] with k = phi1, u (d components), S (d components) of the last
+ * step.  With buf == NULL, *bytes receives the size.  lbm_set_state restores
+ * an image taken from a context of the same shape; a run continued after
+ * restore is bitwise identical. */
+int lbm_get_state(lbm_ctx* ctx, void* buf, size_t* bytes);
+int lbm_set_state(lbm_ctx* ctx, const void* buf, size_t bytes);
+
+/* Reductions of instance `instance` (float64 accumulation, deterministic
+ * two-pass tree over warp-shuffle partials).  Synchronous. */
+int lbm_observables(lbm_ctx* ctx, int instance, lbm_obs* out);
+
+/* Contact angle of instance `instance` from the droplet height on the
+ * vertical grid column x = column (2D).  mode 0: flat bottom wall, H measured
+ * from the phi0 = 1/2 level on that column, R0 = sqrt(2 A / pi) from the area
+ * A = sum phi1, theta solves H/R0 = (1 - cos t) sqrt((pi/2)/(t - sin t cos t))
+ * (Sec. 4.2).  mode 1: disk of radius disk_radius centred at (column, y_c):
+ * H_max above the centre and the drop area solve the two-circle relation of
+ * Sec. 4.3.  Outputs may be NULL.  Synchronous. */
+int lbm_contact_angle(lbm_ctx* ctx, int instance, int mode, int column, double y_c,
+                      double disk_radius, double* theta_deg, double* height);
+
+/* Sizes. */
+int lbm_get_shape(const lbm_ctx* ctx, int* nx, int* ny, int* nz, int* nbatch, int* q);
+
+/* Message for a status code (static string). */
+const char* lbm_strerror(int status);
+
+/* Text of the last error raised on this context (static per context). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H_ */

@@ -1,0 +1,309 @@
+"""ctypes binding of ``liblbm_gb300.so``: argument marshalling only.
+
+Every function carries the name of the C entry point it calls (see
+``include/lbm.h`` for argument meaning, layout, ownership and errors) and
+raises :class:`LbmError` on a non-zero status.  All arithmetic of the method
+runs inside the CUDA library; nothing here computes on the fields.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+c_float_p = ctypes.POINTER(ctypes.c_float)
+
+LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_PERIODIC_X, LBM_PERIODIC_Y, LBM_PERIODIC_Z = 1, 2, 4
+STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_EDIVERGED",
+          -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE", -7: "LBM_EUNSUPPORTED"}
+
+# every symbol include/lbm.h declares
+EXPORTS = [
+    "lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy", "lbm_set_stream",
+    "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
+    "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
+    "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time",
+]
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("W", c_double), ("M_deg", c_double), ("M_cst", c_double), ("theta_deg", c_double),
+                ("kappa", c_double), ("sigma", c_double), ("rho", c_double * 3), ("mu", c_double * 3),
+                ("d0", c_double), ("eta_hat", c_double), ("s_free_ch", c_double), ("s_free_ns", c_double),
+                ("body_force", c_double * 3)]
+
+
+class lbm_obs(ctypes.Structure):
+    _fields_ = [("mass1", c_double), ("mass0", c_double), ("umax", c_double), ("p_in", c_double),
+                ("p_out", c_double), ("dp", c_double), ("n_in", ctypes.c_int64), ("n_out", ctypes.c_int64),
+                ("step", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({detail})")
+
+
+_LIB = None
+
+
+def library():
+    """Load the shared library; raise if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"{LIB} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is the only implementation)")
+    lib = ctypes.CDLL(LIB)
+    P = c_void_p
+    sig = {
+        "lbm_default_params": (c_int, [ctypes.POINTER(lbm_params)]),
+        "lbm_create": (c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(lbm_params), ctypes.POINTER(P)]),
+        "lbm_create_batch": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(lbm_params),
+                                     ctypes.POINTER(P)]),
+        "lbm_destroy": (None, [P]),
+        "lbm_set_stream": (c_int, [P, P]),
+        "lbm_set_launch": (c_int, [P, c_int, c_int]),
+        "lbm_set_solid": (c_int, [P, c_float_p]),
+        "lbm_set_solid_device": (c_int, [P, P]),
+        "lbm_set_phase": (c_int, [P, c_float_p]),
+        "lbm_set_phase_device": (c_int, [P, P]),
+        "lbm_step": (c_int, [P, c_int]),
+        "lbm_sync": (c_int, [P]),
+        "lbm_get_fields": (c_int, [P, c_float_p, c_float_p, c_float_p]),
+        "lbm_get_populations": (c_int, [P, c_float_p, c_float_p]),
+        "lbm_get_state": (c_int, [P, P, ctypes.POINTER(c_size_t)]),
+        "lbm_set_state": (c_int, [P, P, c_size_t]),
+        "lbm_observables": (c_int, [P, c_int, ctypes.POINTER(lbm_obs)]),
+        "lbm_contact_angle": (c_int, [P, c_int, c_int, c_int, c_double, c_double, ctypes.POINTER(c_double),
+                                      ctypes.POINTER(c_double)]),
+        "lbm_get_shape": (c_int, [P] + [ctypes.POINTER(c_int)] * 5),
+        "lbm_strerror": (ctypes.c_char_p, [c_int]),
+        "lbm_set_profiling": (c_int, [P, c_int]),
+        "lbm_kernel_time": (c_int, [P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_int64)]),
+        "lbm_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status, where, ctx=None):
+    if status != 0:
+        detail = library().lbm_last_error(ctx)
+        raise LbmError(status, where, detail.decode() if detail else "")
+
+
+def _fptr(a):
+    return a.ctypes.data_as(c_float_p)
+
+
+def _f32(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def lbm_default_params(**overrides) -> lbm_params:
+    p = lbm_params()
+    _check(library().lbm_default_params(ctypes.byref(p)), "lbm_default_params")
+    for k, v in overrides.items():
+        if k in ("rho", "mu", "body_force"):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def lbm_create(lattice, nx, ny, nz, periodic_mask, params: lbm_params):
+    out = c_void_p()
+    _check(library().lbm_create(lattice, nx, ny, nz, periodic_mask, ctypes.byref(params), ctypes.byref(out)),
+           "lbm_create")
+    return out
+
+
+def lbm_create_batch(lattice, nx, ny, nz, periodic_mask, params_list):
+    arr = (lbm_params * len(params_list))(*params_list)
+    out = c_void_p()
+    _check(library().lbm_create_batch(lattice, nx, ny, nz, periodic_mask, len(params_list), arr,
+                                      ctypes.byref(out)), "lbm_create_batch")
+    return out
+
+
+def lbm_destroy(ctx):
+    library().lbm_destroy(ctx)
+
+
+def lbm_set_stream(ctx, stream_handle):
+    _check(library().lbm_set_stream(ctx, c_void_p(stream_handle)), "lbm_set_stream", ctx)
+
+
+def lbm_set_launch(ctx, strip, depth=0):
+    _check(library().lbm_set_launch(ctx, strip, depth), "lbm_set_launch", ctx)
+
+
+def lbm_get_shape(ctx):
+    v = [c_int() for _ in range(5)]
+    _check(library().lbm_get_shape(ctx, *[ctypes.byref(x) for x in v]), "lbm_get_shape", ctx)
+    return tuple(x.value for x in v)   # nx, ny, nz, nbatch, q
+
+
+def _nodes(ctx):
+    nx, ny, nz, nb, q = lbm_get_shape(ctx)
+    return nx * ny * nz, nb, q
+
+
+def lbm_set_solid(ctx, phi0):
+    n, nb, _ = _nodes(ctx)
+    a = _f32(phi0, n * nb)
+    _check(library().lbm_set_solid(ctx, _fptr(a)), "lbm_set_solid", ctx)
+
+
+def lbm_set_solid_device(ctx, dev_ptr):
+    _check(library().lbm_set_solid_device(ctx, c_void_p(dev_ptr)), "lbm_set_solid_device", ctx)
+
+
+def lbm_set_phase(ctx, phi1):
+    n, nb, _ = _nodes(ctx)
+    a = _f32(phi1, n * nb)
+    _check(library().lbm_set_phase(ctx, _fptr(a)), "lbm_set_phase", ctx)
+
+
+def lbm_set_phase_device(ctx, dev_ptr):
+    _check(library().lbm_set_phase_device(ctx, c_void_p(dev_ptr)), "lbm_set_phase_device", ctx)
+
+
+def lbm_step(ctx, n):
+    _check(library().lbm_step(ctx, n), "lbm_step", ctx)
+
+
+def lbm_sync(ctx):
+    _check(library().lbm_sync(ctx), "lbm_sync", ctx)
+
+
+def lbm_get_fields(ctx, phi1=None, u=None, p=None):
+    """Fill (or allocate) float32 arrays phi1 [b, nodes], u [b, d, nodes], p [b, nodes]."""
+    n, nb, q = _nodes(ctx)
+    d = 2 if q == 9 else 3
+    phi1 = np.empty((nb, n), np.float32) if phi1 is None else phi1
+    u = np.empty((nb, d, n), np.float32) if u is None else u
+    p = np.empty((nb, n), np.float32) if p is None else p
+    for a, size in ((phi1, nb * n), (u, nb * d * n), (p, nb * n)):
+        if a.dtype != np.float32 or not a.flags.c_contiguous or a.size != size:
+            raise ValueError("output arrays must be C-contiguous float32 of the right size")
+    _check(library().lbm_get_fields(ctx, _fptr(phi1), _fptr(u), _fptr(p)), "lbm_get_fields", ctx)
+    return phi1, u, p
+
+
+def lbm_get_populations(ctx):
+    n, nb, q = _nodes(ctx)
+    f = np.empty((nb, q, n), np.float32)
+    g = np.empty((nb, q, n), np.float32)
+    _check(library().lbm_get_populations(ctx, _fptr(f), _fptr(g)), "lbm_get_populations", ctx)
+    return f, g
+
+
+def lbm_get_state(ctx) -> bytes:
+    size = c_size_t(0)
+    _check(library().lbm_get_state(ctx, None, ctypes.byref(size)), "lbm_get_state", ctx)
+    buf = ctypes.create_string_buffer(size.value)
+    _check(library().lbm_get_state(ctx, buf, ctypes.byref(size)), "lbm_get_state", ctx)
+    return buf.raw
+
+
+def lbm_set_state(ctx, image: bytes):
+    buf = ctypes.create_string_buffer(image, len(image))
+    _check(library().lbm_set_state(ctx, buf, len(image)), "lbm_set_state", ctx)
+
+
+def lbm_observables(ctx, instance=0) -> dict:
+    o = lbm_obs()
+    _check(library().lbm_observables(ctx, instance, ctypes.byref(o)), "lbm_observables", ctx)
+    return o.as_dict()
+
+
+def lbm_contact_angle(ctx, instance, mode, column, y_c=0.0, disk_radius=0.0):
+    th, h = c_double(), c_double()
+    _check(library().lbm_contact_angle(ctx, instance, mode, column, y_c, disk_radius, ctypes.byref(th),
+                                       ctypes.byref(h)), "lbm_contact_angle", ctx)
+    return th.value, h.value
+
+
+def lbm_set_profiling(ctx, enable):
+    _check(library().lbm_set_profiling(ctx, 1 if enable else 0), "lbm_set_profiling", ctx)
+
+
+def lbm_kernel_time(ctx):
+    """(summed device milliseconds, launches) of the step kernels timed since the last read."""
+    ms, n = c_double(), ctypes.c_int64()
+    _check(library().lbm_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(n)), "lbm_kernel_time", ctx)
+    return ms.value, n.value
+
+
+def lbm_strerror(status) -> str:
+    return library().lbm_strerror(status).decode()
+
+
+class Context:
+    """Owns one lbm_ctx; each method forwards to the C call of the same name."""
+
+    def __init__(self, lattice, nx, ny, nz=1, periodic=(True, True, True), params=None, batch=None):
+        mask = sum(bit for bit, on in zip((1, 2, 4), periodic) if on)
+        self.shape = (nx, ny, nz)
+        if batch is not None:
+            self.ctx = lbm_create_batch(lattice, nx, ny, nz, mask, batch)
+        else:
+            self.ctx = lbm_create(lattice, nx, ny, nz, mask, params if params is not None else lbm_default_params())
+        self.q = 9 if lattice == LBM_D2Q9 else 19
+        self.d = 2 if lattice == LBM_D2Q9 else 3
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, handle): lbm_set_stream(self.ctx, handle)
+    def set_launch(self, strip, depth=0): lbm_set_launch(self.ctx, strip, depth)
+    def set_solid(self, phi0): lbm_set_solid(self.ctx, phi0)
+    def set_phase(self, phi1): lbm_set_phase(self.ctx, phi1)
+    def set_solid_device(self, ptr): lbm_set_solid_device(self.ctx, ptr)
+    def set_phase_device(self, ptr): lbm_set_phase_device(self.ctx, ptr)
+    def step(self, n=1): lbm_step(self.ctx, n)
+    def sync(self): lbm_sync(self.ctx)
+    def get_fields(self, *a): return lbm_get_fields(self.ctx, *a)
+    def get_populations(self): return lbm_get_populations(self.ctx)
+    def get_state(self): return lbm_get_state(self.ctx)
+    def set_state(self, image): lbm_set_state(self.ctx, image)
+    def observables(self, instance=0): return lbm_observables(self.ctx, instance)
+    def set_profiling(self, enable): lbm_set_profiling(self.ctx, enable)
+    def kernel_time(self): return lbm_kernel_time(self.ctx)
+    def contact_angle(self, instance, mode, column, y_c=0.0, disk_radius=0.0):
+        return lbm_contact_angle(self.ctx, instance, mode, column, y_c, disk_radius)

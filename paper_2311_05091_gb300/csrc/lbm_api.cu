@@ -1,0 +1,753 @@
+// Host implementation of the C ABI declared in include/lbm.h.
+//
+// Parameter derivation follows the paper (arXiv 2311.05091) in float64 on
+// the host; the device receives one float32 InstanceConsts record per batch
+// instance.  All device work goes to the context's stream; graphs of
+// kGraphSteps steps are captured once per starting buffer and replayed.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+using lbm::InstanceConsts;
+using lbm::StepArgs;
+
+namespace {
+
+constexpr int kGraphSteps = 16;     // even: a replay returns to the same buffer
+constexpr uint32_t kStateMagic = 0x314d424cu;   // "LBM1"
+
+thread_local char g_last_error[256] = "";
+
+struct StateHeader {
+  uint32_t magic;
+  int32_t lattice, nx, ny, nz, nbatch, q, d;
+  int64_t step;
+  int64_t nodes;
+  int32_t pad[4];
+};
+
+}  // namespace
+
+struct lbm_ctx {
+  int lattice = 0;
+  int nx = 0, ny = 0, nz = 1, nbatch = 1, q = 9, d = 2;
+  int per[3] = {0, 0, 0};
+  long long nodes = 0;        // per instance
+  int strip = 32;
+  int depth = 1;
+  std::vector<InstanceConsts> hconsts;
+  InstanceConsts* dconsts = nullptr;
+  float* f[2] = {nullptr, nullptr};
+  float* g[2] = {nullptr, nullptr};
+  float* hist[2] = {nullptr, nullptr};
+  float* phi0 = nullptr;
+  float* p = nullptr;
+  unsigned int* dflag = nullptr;
+  double* dpart = nullptr;
+  double* dobs = nullptr;
+  int cur = 0;
+  long long step = 0;
+  bool solid_set = false, phase_set = false, failed = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;     // pairs: [2k] before, [2k+1] after launch k
+  size_t ev_used = 0;
+  char err[256] = "";
+};
+
+namespace {
+
+int set_err(lbm_ctx* c, int code, const char* fmt, const char* a = "", const char* b = "") {
+  char* dst = c ? c->err : g_last_error;
+  snprintf(dst, 256, fmt, a, b);
+  if (c) snprintf(g_last_error, 256, "%s", c->err);
+  return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+  if (c) c->failed = true;
+  return set_err(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBM_CK(c, call)                                       \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((c), e_, #call);  \
+  } while (0)
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+// Model constants of one instance (Sec. 2.2 Eq. kk and gamma_p; Sec. 3
+// relations for s1, the viscosity relation and the pressure constants).
+int derive(const lbm_params& p, int lattice, InstanceConsts& k, char* why) {
+  const bool is3d = lattice == LBM_D3Q19;
+  const double d0 = p.d0;
+  if (!finite_pos(p.W)) return snprintf(why, 128, "W must be > 0"), LBM_EINVAL;
+  if (!(p.M_deg >= 0.0) || !(p.M_cst >= 0.0) || !finite_pos(p.M_deg + p.M_cst))
+    return snprintf(why, 128, "mobility must be >= 0 with M_cst + M_deg > 0"), LBM_EINVAL;
+  if (!(p.theta_deg > 0.0 && p.theta_deg < 180.0))
+    return snprintf(why, 128, "theta_deg must lie in (0, 180)"), LBM_EINVAL;
+  if (!(p.kappa > -1.0) || !isfinite(p.kappa)) return snprintf(why, 128, "kappa must be > -1"), LBM_EINVAL;
+  if (!finite_pos(p.sigma)) return snprintf(why, 128, "sigma must be > 0"), LBM_EINVAL;
+  for (int i = 0; i < 3; ++i)
+    if (!finite_pos(p.rho[i]) || !finite_pos(p.mu[i]))
+      return snprintf(why, 128, "densities and viscosities must be > 0"), LBM_EINVAL;
+  const double d0max = is3d ? 0.5 : 1.0;
+  if (!(d0 > 0.0 && d0 < d0max)) return snprintf(why, 128, "d0 out of range for the lattice"), LBM_EINVAL;
+  if (!finite_pos(p.eta_hat)) return snprintf(why, 128, "eta_hat must be > 0"), LBM_EINVAL;
+  if (!(p.s_free_ch > 0.0 && p.s_free_ch < 2.0) || !(p.s_free_ns > 0.0 && p.s_free_ns < 2.0))
+    return snprintf(why, 128, "free relaxation rates must lie in (0, 2)"), LBM_EINVAL;
+  for (int i = 0; i < 3; ++i)
+    if (!isfinite(p.body_force[i])) return snprintf(why, 128, "body force must be finite"), LBM_EINVAL;
+
+  const double th = p.theta_deg * M_PI / 180.0;
+  const double sgn = p.theta_deg > 90.0 ? 1.0 : (p.theta_deg < 90.0 ? -1.0 : 0.0);
+  const double s = sin(M_PI / 4.0 * cos(th));
+  const double kk = 9.0 / (1.0 + p.kappa) * (1.0 + 2.0 * sgn * s * s);
+  const double s12 = p.sigma, s01 = kk * s12, s02 = s01 + s12 * cos(th);
+  const double g0 = s01 + s02 - s12, g1 = s01 + s12 - s02, g2 = s02 + s12 - s01;
+  if (!(g0 > 0.0 && g1 > 0.0 && g2 > 0.0))
+    return snprintf(why, 128, "spreading coefficients must be positive (check kappa, theta)"), LBM_EINVAL;
+  const double gT = 3.0 / (1.0 / g0 + 1.0 / g1 + 1.0 / g2);
+  // The kernels compute in float32 with cs2 = float(d0).  Every lattice
+  // constant below is derived from that rounded value, so identities such as
+  // w0 = (1 - cs2)^2 and cs2 / (1 - w0) = 1 / (2 - cs2) hold to one rounding
+  // instead of mixing two different scale factors.
+  const double df = (double)(float)d0;
+  const double cs2 = df;
+  const double eta = p.eta_hat / g1;
+  const double s1c = 1.0 / (0.5 + (p.M_cst + p.M_deg) / (g1 * eta * cs2));
+  double w0, wa, we;
+  if (is3d) {
+    w0 = 1.0 - 3.0 * df + 3.0 * df * df;
+    wa = (df - 2.0 * df * df) / 2.0;
+    we = df * df / 4.0;
+  } else {
+    w0 = (1.0 - df) * (1.0 - df);
+    wa = (df - df * df) / 2.0;
+    we = df * df / 4.0;
+  }
+  memset(&k, 0, sizeof(k));
+  k.cs2 = (float)cs2;
+  k.cs4 = (float)(cs2 * cs2);
+  k.w0 = (float)w0;
+  k.wa = (float)wa;
+  k.we = (float)we;
+  k.c12_W = (float)(12.0 / p.W);
+  k.c34_W = (float)(0.75 * p.W);
+  k.gam0 = (float)g0;
+  k.gam1 = (float)g1;
+  k.gam2 = (float)g2;
+  k.gT3 = (float)(gT / 3.0);
+  k.inv_gam0 = (float)(1.0 / g0);
+  k.inv_gam1 = (float)(1.0 / g1);
+  k.inv_gam2 = (float)(1.0 / g2);
+  k.eta = (float)eta;
+  k.M_cst = (float)p.M_cst;
+  k.M_deg = (float)p.M_deg;
+  k.corr_scale = (float)(p.M_deg / (p.M_cst + p.M_deg));
+  k.s1c = (float)s1c;
+  k.s0c = k.s2ac = k.s2bc = k.s3c = k.s4c = (float)p.s_free_ch;
+  k.ch_fast = p.s_free_ch == 1.0 ? 1.0f : 0.0f;
+  k.s1n = k.s3n = (float)p.s_free_ns;
+  k.rho0 = (float)p.rho[0];
+  k.rho1 = (float)p.rho[1];
+  k.rho2 = (float)p.rho[2];
+  k.mu0 = (float)p.mu[0];
+  k.mu1 = (float)p.mu[1];
+  k.mu2 = (float)p.mu[2];
+  k.bx = (float)p.body_force[0];
+  k.by = (float)p.body_force[1];
+  k.bz = (float)p.body_force[2];
+  k.a2a = (float)((1.0 - df) / 2.0);
+  k.a2b = (float)df;
+  // pressure: pf = cs2 / (1 - w0), wq = w0 / (c^2 - cs2)
+  k.pf = (float)(cs2 / (1.0 - w0));
+  k.wq = (float)(w0 / (1.0 - cs2));
+  if (is3d) {
+    k.Kp = (float)(1.0 - 2.0 * df);
+    k.h0 = (float)(1.0 - df);
+    k.h2 = (float)(3.0 - 7.0 * df);
+    k.h3 = (float)(1.0 - 3.0 * df);
+  } else {
+    k.Kp = (float)(1.0 - df);
+    k.h0 = (float)(1.0 - df);
+    k.h2 = (float)(2.0 - 4.0 * df);
+    k.h3 = (float)((1.0 - 3.0 * df) / 2.0);
+  }
+  return LBM_OK;
+}
+
+int default_strip(const lbm_ctx* c) {
+  // 32 rows per CTA measured best for the D2Q9 kernel on GB300 (prologue of
+  // two halo rows amortised, enough CTAs for 152 SMs at 3 CTAs each)
+  const long long rows = c->lattice == LBM_D2Q9 ? c->ny : c->nz;
+  long long strip = 32;
+  if (strip > rows) strip = rows;
+  return (int)std::max(1LL, strip);
+}
+
+StepArgs step_args(lbm_ctx* c, int from) {
+  StepArgs a;
+  a.f_in = c->f[from];
+  a.f_out = c->f[1 - from];
+  a.g_in = c->g[from];
+  a.g_out = c->g[1 - from];
+  a.phi0 = c->phi0;
+  a.hist_in = c->hist[from];
+  a.hist_out = c->hist[1 - from];
+  a.p_out = c->p;
+  a.consts = c->dconsts;
+  a.flag = c->dflag;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.per_x = c->per[0];
+  a.per_y = c->per[1];
+  a.per_z = c->per[2];
+  a.strip = c->strip;
+  a.depth = c->depth;
+  a.nodes = c->nodes;
+  return a;
+}
+
+cudaError_t launch_step(lbm_ctx* c, int from, bool observe, cudaStream_t s) {
+  const StepArgs a = step_args(c, from);
+  if (c->lattice == LBM_D2Q9) return lbm::launch_d2q9_step(a, c->nbatch, observe, s);
+  return lbm::launch_d3q19_step(a, c->nbatch, observe, s);
+}
+
+int ensure_graph(lbm_ctx* c, int from) {
+  if (c->graph[from]) return LBM_OK;
+  cudaStream_t cs = nullptr;
+  LBM_CK(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int b = from;
+  for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) {
+    e = launch_step(c, b, false, cs);
+    b = 1 - b;
+  }
+  cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[from], gr, 0);
+  if (gr) cudaGraphDestroy(gr);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_fail(c, e, "capture of the step graph");
+  return LBM_OK;
+}
+
+int check_ready(lbm_ctx* c, bool need_state) {
+  if (!c) return set_err(nullptr, LBM_EINVAL, "null context");
+  if (c->failed) return LBM_ESTATE;   // c->err keeps the first failure
+  if (need_state && !c->phase_set) return set_err(c, LBM_ESTATE, "state not initialised (call lbm_set_phase)");
+  return LBM_OK;
+}
+
+int check_flag(lbm_ctx* c) {
+  unsigned int flag = 0;
+  LBM_CK(c, cudaMemcpyAsync(&flag, c->dflag, sizeof(flag), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  if (flag) {
+    LBM_CK(c, cudaMemsetAsync(c->dflag, 0, sizeof(unsigned int), c->stream));
+    return set_err(c, LBM_EDIVERGED, "divergence: NaN or |u| > 0.5 at the last observed step");
+  }
+  return LBM_OK;
+}
+
+void free_all(lbm_ctx* c) {
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+  for (int i = 0; i < 2; ++i) {
+    if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+    cudaFree(c->f[i]);
+    cudaFree(c->g[i]);
+    cudaFree(c->hist[i]);
+  }
+  cudaFree(c->phi0);
+  cudaFree(c->p);
+  cudaFree(c->dflag);
+  cudaFree(c->dpart);
+  cudaFree(c->dobs);
+  cudaFree(c->dconsts);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+// --- host-side geometry of the droplet diagnostics ---------------------------
+
+double crossing_from_top(const std::vector<float>& v, double level) {
+  for (int k = (int)v.size() - 2; k >= 0; --k)
+    if (v[k] >= level && level > v[k + 1]) return k + (v[k] - level) / ((double)v[k] - v[k + 1]);
+  return NAN;
+}
+
+double crossing_from_bottom(const std::vector<float>& v, double level) {
+  for (int k = 0; k + 1 < (int)v.size(); ++k)
+    if (v[k] >= level && level > v[k + 1]) return k + (v[k] - level) / ((double)v[k] - v[k + 1]);
+  return NAN;
+}
+
+template <class F>
+double bisect(F fn, double lo, double hi, double target) {
+  double flo = fn(lo) - target;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double fm = fn(mid) - target;
+    if ((fm > 0) == (flo > 0)) {
+      lo = mid;
+      flo = fm;
+    } else {
+      hi = mid;
+    }
+  }
+  return 0.5 * (lo + hi);
+}
+
+// H / R0 of a 2D cap of contact angle t holding the area of a half disk R0.
+double flat_ratio(double t) { return (1.0 - cos(t)) * sqrt((M_PI / 2.0) / (t - sin(t) * cos(t))); }
+
+// Area of a circle (radius r, centre at distance k from the disk centre) outside the disk Rs.
+double area_outside(double r, double Rs, double k) {
+  const double a = (k * k - r * r + Rs * Rs) / (2.0 * k);
+  const double h2 = std::max(Rs * Rs - a * a, 0.0);
+  const double c1 = std::min(1.0, std::max(-1.0, (k * k + r * r - Rs * Rs) / (2.0 * k * r)));
+  const double c2 = std::min(1.0, std::max(-1.0, (k * k - r * r + Rs * Rs) / (2.0 * k * Rs)));
+  return M_PI * r * r - r * r * acos(c1) - Rs * Rs * acos(c2) + k * sqrt(h2);
+}
+
+double disk_hmax(double t, double Rs, double S0) {
+  auto area = [&](double r) { return area_outside(r, Rs, sqrt(r * r + Rs * Rs - 2.0 * r * Rs * cos(t))); };
+  const double r = bisect(area, 1e-6, 10.0 * (Rs + sqrt(S0)), S0);
+  return r + sqrt(r * r + Rs * Rs - 2.0 * r * Rs * cos(t));
+}
+
+// launch one step, bracketed by an event pair when profiling
+int timed_step(lbm_ctx* c, bool observe) {
+  if (c->profiling) {
+    while (c->ev.size() < 2 * (c->ev_used + 1)) {
+      cudaEvent_t e;
+      LBM_CK(c, cudaEventCreate(&e));
+      c->ev.push_back(e);
+    }
+    LBM_CK(c, cudaEventRecord(c->ev[2 * c->ev_used], c->stream));
+  }
+  cudaError_t e = launch_step(c, c->cur, observe, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+  if (c->profiling) {
+    LBM_CK(c, cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream));
+    ++c->ev_used;
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_default_params(lbm_params* p) {
+  if (!p) return LBM_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->W = 4.0;
+  p->M_deg = 0.1;
+  p->M_cst = 0.0;
+  p->theta_deg = 90.0;
+  p->kappa = 0.0;
+  p->sigma = 0.01;
+  for (int i = 0; i < 3; ++i) {
+    p->rho[i] = 1.0;
+    p->mu[i] = 0.01;
+  }
+  p->d0 = 0.5;
+  p->eta_hat = 0.1;
+  p->s_free_ch = 1.0;
+  p->s_free_ns = 1.0;
+  return LBM_OK;
+}
+
+int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, int nbatch,
+                     const lbm_params* params, lbm_ctx** out) {
+  if (!out) return set_err(nullptr, LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return set_err(nullptr, LBM_EINVAL, "unknown lattice");
+  if (!params || nbatch < 1) return set_err(nullptr, LBM_EINVAL, "need nbatch >= 1 parameter sets");
+  const bool is3d = lattice == LBM_D3Q19;
+  if (!is3d && nz != 1) return set_err(nullptr, LBM_EINVAL, "D2Q9 needs nz = 1");
+  if (nx < 1 || ny < 1 || nz < 1) return set_err(nullptr, LBM_EINVAL, "sizes must be positive");
+  const int per[3] = {(periodic_mask & LBM_PERIODIC_X) ? 1 : 0, (periodic_mask & LBM_PERIODIC_Y) ? 1 : 0,
+                      (periodic_mask & LBM_PERIODIC_Z) ? 1 : 0};
+  const int dims[3] = {nx, ny, nz};
+  for (int a = 0; a < (is3d ? 3 : 2); ++a)
+    if (!per[a] && dims[a] < 2) return set_err(nullptr, LBM_EINVAL, "a wall axis needs at least 2 nodes");
+  const long long nodes = (long long)nx * ny * nz;
+  if (nodes > (1LL << 40) / nbatch) return set_err(nullptr, LBM_EINVAL, "lattice too large");
+
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return set_err(nullptr, LBM_ENOMEM, "host allocation failed");
+  c->lattice = lattice;
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = nz;
+  c->nbatch = nbatch;
+  c->q = is3d ? 19 : 9;
+  c->d = is3d ? 3 : 2;
+  for (int a = 0; a < 3; ++a) c->per[a] = per[a];
+  c->nodes = nodes;
+  c->hconsts.resize(nbatch);
+  for (int b = 0; b < nbatch; ++b) {
+    char why[128] = "";
+    if (derive(params[b], lattice, c->hconsts[b], why) != LBM_OK) {
+      char msg[200];
+      snprintf(msg, sizeof msg, "instance %d: %s", b, why);
+      set_err(nullptr, LBM_EINVAL, "%s", msg);
+      delete c;
+      return LBM_EINVAL;
+    }
+  }
+  c->strip = default_strip(c);
+  const size_t pop = sizeof(float) * (size_t)c->q * nodes * nbatch;
+  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * nodes * nbatch;
+  const size_t fld = sizeof(float) * (size_t)nodes * nbatch;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaMalloc(&c->f[i], pop);
+    if (e == cudaSuccess) e = cudaMalloc(&c->g[i], pop);
+    if (e == cudaSuccess) e = cudaMalloc(&c->hist[i], his);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&c->phi0, fld);
+  if (e == cudaSuccess) e = cudaMalloc(&c->p, fld);
+  if (e == cudaSuccess) e = cudaMalloc(&c->dflag, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->dpart, sizeof(double) * lbm::obs_partials_len(nodes));
+  if (e == cudaSuccess) e = cudaMalloc(&c->dobs, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&c->dconsts, sizeof(InstanceConsts) * nbatch);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) c->own_stream = true;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->dconsts, c->hconsts.data(), sizeof(InstanceConsts) * nbatch, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->dflag, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(c->p, 0, fld);
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? LBM_ENOMEM : LBM_ECUDA;
+    set_err(nullptr, code, "device set-up failed: %s", cudaGetErrorString(e));
+    free_all(c);
+    delete c;
+    return code;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_create(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, const lbm_params* p,
+               lbm_ctx** out) {
+  return lbm_create_batch(lattice, nx, ny, nz, periodic_mask, 1, p, out);
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+int lbm_set_stream(lbm_ctx* c, void* stream) {
+  if (!c) return set_err(nullptr, LBM_EINVAL, "null context");
+  if (c->failed) return check_ready(c, false);
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  if (c->own_stream) {
+    cudaStreamDestroy(c->stream);
+    c->own_stream = false;
+  }
+  c->stream = (cudaStream_t)stream;
+  return LBM_OK;
+}
+
+int lbm_set_launch(lbm_ctx* c, int strip, int depth) {
+  if (int s = check_ready(c, false)) return s;
+  if (strip < 1) return set_err(c, LBM_EINVAL, "strip must be >= 1");
+  if (depth < 0 || depth > 3) return set_err(c, LBM_EINVAL, "depth must lie in 0..3 (0 keeps the current)");
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->strip = strip;
+  if (depth > 0) c->depth = depth;
+  for (int i = 0; i < 2; ++i)
+    if (c->graph[i]) {
+      cudaGraphExecDestroy(c->graph[i]);
+      c->graph[i] = nullptr;
+    }
+  return LBM_OK;
+}
+
+static int set_solid_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
+  if (int s = check_ready(c, false)) return s;
+  if (!src) return set_err(c, LBM_EINVAL, "phi0 is NULL");
+  LBM_CK(c, cudaMemcpyAsync(c->phi0, src, sizeof(float) * c->nodes * c->nbatch, kind, c->stream));
+  if (kind == cudaMemcpyHostToDevice) LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->solid_set = true;
+  return LBM_OK;
+}
+
+int lbm_set_solid(lbm_ctx* c, const float* phi0_host) { return set_solid_impl(c, phi0_host, cudaMemcpyHostToDevice); }
+int lbm_set_solid_device(lbm_ctx* c, const float* phi0_dev) {
+  return set_solid_impl(c, phi0_dev, cudaMemcpyDeviceToDevice);
+}
+
+static int set_phase_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
+  if (int s = check_ready(c, false)) return s;
+  if (!src) return set_err(c, LBM_EINVAL, "phi1 is NULL");
+  if (!c->solid_set) return set_err(c, LBM_ESTATE, "call lbm_set_solid before lbm_set_phase");
+  const int nh = 1 + 2 * c->d;
+  const size_t row = sizeof(float) * c->nodes;
+  // stage phi1 in plane 0 of the spare history buffer, then initialise the current one
+  float* stage = c->hist[1 - c->cur];
+  LBM_CK(c, cudaMemcpy2DAsync(stage, row * nh, src, row, row, c->nbatch, kind, c->stream));
+  cudaError_t e;
+  if (c->lattice == LBM_D2Q9)
+    e = lbm::launch_d2q9_init(c->phi0, stage, c->f[c->cur], c->g[c->cur], c->hist[c->cur], c->dconsts, c->nx,
+                              c->ny, c->per[0], c->per[1], c->nbatch, c->stream);
+  else
+    e = lbm::launch_d3q19_init(c->phi0, stage, c->f[c->cur], c->g[c->cur], c->hist[c->cur], c->dconsts, c->nx,
+                               c->ny, c->nz, c->per[0], c->per[1], c->per[2], c->nbatch, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  LBM_CK(c, cudaMemsetAsync(c->p, 0, sizeof(float) * c->nodes * c->nbatch, c->stream));
+  if (kind == cudaMemcpyHostToDevice) LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->phase_set = true;
+  c->step = 0;
+  return LBM_OK;
+}
+
+int lbm_set_phase(lbm_ctx* c, const float* phi1_host) { return set_phase_impl(c, phi1_host, cudaMemcpyHostToDevice); }
+int lbm_set_phase_device(lbm_ctx* c, const float* phi1_dev) {
+  return set_phase_impl(c, phi1_dev, cudaMemcpyDeviceToDevice);
+}
+
+int lbm_set_profiling(lbm_ctx* c, int enable) {
+  if (int s = check_ready(c, false)) return s;
+  c->profiling = enable != 0;
+  c->ev_used = 0;
+  return LBM_OK;
+}
+
+int lbm_kernel_time(lbm_ctx* c, double* total_ms, int64_t* launches) {
+  if (int s = check_ready(c, false)) return s;
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  for (size_t k = 0; k < c->ev_used; ++k) {
+    float ms = 0.f;
+    LBM_CK(c, cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = (int64_t)c->ev_used;
+  c->ev_used = 0;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+  if (int s = check_ready(c, true)) return s;
+  if (n < 0) return set_err(c, LBM_EINVAL, "n must be >= 0");
+  const bool graphs = c->stream != nullptr && !c->profiling;
+  while (n > 0) {
+    if (n > kGraphSteps && graphs) {
+      if (int s = ensure_graph(c, c->cur)) return s;
+      LBM_CK(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+      n -= kGraphSteps;
+      c->step += kGraphSteps;
+      continue;
+    }
+    const bool observe = (n == 1);
+    if (int s = timed_step(c, observe)) return s;
+    c->cur = 1 - c->cur;
+    c->step += 1;
+    --n;
+  }
+  return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c) {
+  if (int s = check_ready(c, false)) return s;
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  return check_flag(c);
+}
+
+int lbm_get_fields(lbm_ctx* c, float* phi1, float* u, float* p) {
+  if (int s = check_ready(c, true)) return s;
+  const int nh = 1 + 2 * c->d;
+  const size_t row = sizeof(float) * c->nodes;
+  const float* h = c->hist[c->cur];
+  if (phi1) LBM_CK(c, cudaMemcpy2DAsync(phi1, row, h, row * nh, row, c->nbatch, cudaMemcpyDeviceToHost, c->stream));
+  if (u)
+    LBM_CK(c, cudaMemcpy2DAsync(u, row * c->d, h + c->nodes, row * nh, row * c->d, c->nbatch,
+                                cudaMemcpyDeviceToHost, c->stream));
+  if (p) LBM_CK(c, cudaMemcpyAsync(p, c->p, row * c->nbatch, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  return check_flag(c);
+}
+
+int lbm_get_populations(lbm_ctx* c, float* f, float* g) {
+  if (int s = check_ready(c, true)) return s;
+  const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
+  if (f) LBM_CK(c, cudaMemcpyAsync(f, c->f[c->cur], pop, cudaMemcpyDeviceToHost, c->stream));
+  if (g) LBM_CK(c, cudaMemcpyAsync(g, c->g[c->cur], pop, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+static size_t state_bytes(const lbm_ctx* c) {
+  const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
+  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->nodes * c->nbatch;
+  return sizeof(StateHeader) + 2 * pop + his;
+}
+
+int lbm_get_state(lbm_ctx* c, void* buf, size_t* bytes) {
+  if (int s = check_ready(c, true)) return s;
+  if (!bytes) return set_err(c, LBM_EINVAL, "bytes is NULL");
+  const size_t need = state_bytes(c);
+  if (!buf) {
+    *bytes = need;
+    return LBM_OK;
+  }
+  if (*bytes < need) return set_err(c, LBM_EINVAL, "state buffer too small");
+  StateHeader hd;
+  memset(&hd, 0, sizeof hd);
+  hd.magic = kStateMagic;
+  hd.lattice = c->lattice;
+  hd.nx = c->nx;
+  hd.ny = c->ny;
+  hd.nz = c->nz;
+  hd.nbatch = c->nbatch;
+  hd.q = c->q;
+  hd.d = c->d;
+  hd.step = c->step;
+  hd.nodes = c->nodes;
+  char* o = static_cast<char*>(buf);
+  memcpy(o, &hd, sizeof hd);
+  o += sizeof hd;
+  const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
+  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->nodes * c->nbatch;
+  LBM_CK(c, cudaMemcpyAsync(o, c->f[c->cur], pop, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(o + pop, c->g[c->cur], pop, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(o + 2 * pop, c->hist[c->cur], his, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  *bytes = need;
+  return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx* c, const void* buf, size_t bytes) {
+  if (int s = check_ready(c, false)) return s;
+  if (!buf || bytes < sizeof(StateHeader)) return set_err(c, LBM_EINVAL, "state image too small");
+  StateHeader hd;
+  memcpy(&hd, buf, sizeof hd);
+  if (hd.magic != kStateMagic || hd.lattice != c->lattice || hd.nx != c->nx || hd.ny != c->ny ||
+      hd.nz != c->nz || hd.nbatch != c->nbatch || hd.q != c->q || hd.d != c->d || bytes != state_bytes(c))
+    return set_err(c, LBM_EINVAL, "state image does not match this context");
+  if (!c->solid_set) return set_err(c, LBM_ESTATE, "call lbm_set_solid before lbm_set_state");
+  const char* o = static_cast<const char*>(buf) + sizeof hd;
+  const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
+  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->nodes * c->nbatch;
+  LBM_CK(c, cudaMemcpyAsync(c->f[c->cur], o, pop, cudaMemcpyHostToDevice, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(c->g[c->cur], o + pop, pop, cudaMemcpyHostToDevice, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(c->hist[c->cur], o + 2 * pop, his, cudaMemcpyHostToDevice, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->step = hd.step;
+  c->phase_set = true;
+  return LBM_OK;
+}
+
+int lbm_observables(lbm_ctx* c, int instance, lbm_obs* out) {
+  if (int s = check_ready(c, true)) return s;
+  if (!out || instance < 0 || instance >= c->nbatch) return set_err(c, LBM_EINVAL, "bad instance or output");
+  const int nh = 1 + 2 * c->d;
+  const float* h = c->hist[c->cur] + (size_t)instance * nh * c->nodes;
+  cudaError_t e = lbm::launch_observables(c->phi0 + (size_t)instance * c->nodes, h, h + c->nodes, c->d,
+                                          c->p + (size_t)instance * c->nodes, c->nodes, c->dpart, c->dobs,
+                                          c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "observables kernel");
+  double r[8];
+  LBM_CK(c, cudaMemcpyAsync(r, c->dobs, sizeof r, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  out->mass1 = r[0];
+  out->mass0 = r[1];
+  out->umax = r[2];
+  out->n_in = (int64_t)r[4];
+  out->n_out = (int64_t)r[6];
+  out->p_in = r[4] > 0 ? r[3] / r[4] : NAN;
+  out->p_out = r[6] > 0 ? r[5] / r[6] : NAN;
+  out->dp = out->p_in - out->p_out;
+  out->step = c->step;
+  if (r[7] > 0) return set_err(c, LBM_EDIVERGED, "non-finite values in the fields");
+  return check_flag(c);
+}
+
+int lbm_contact_angle(lbm_ctx* c, int instance, int mode, int column, double y_c, double disk_radius,
+                      double* theta_deg, double* height) {
+  if (int s = check_ready(c, true)) return s;
+  if (c->lattice != LBM_D2Q9) return set_err(c, LBM_EUNSUPPORTED, "contact angle is measured on 2D lattices");
+  if (instance < 0 || instance >= c->nbatch || column < 0 || column >= c->nx || (mode != 0 && mode != 1))
+    return set_err(c, LBM_EINVAL, "bad instance, column or mode");
+  if (mode == 1 && !(disk_radius > 0)) return set_err(c, LBM_EINVAL, "disk radius must be > 0");
+  lbm_obs ob;
+  if (int s = lbm_observables(c, instance, &ob)) return s;
+  const int nh = 1 + 2 * c->d;
+  std::vector<float> col1(c->ny), col0(c->ny);
+  const float* h = c->hist[c->cur] + (size_t)instance * nh * c->nodes + column;
+  const float* s0 = c->phi0 + (size_t)instance * c->nodes + column;
+  LBM_CK(c, cudaMemcpy2DAsync(col1.data(), sizeof(float), h, sizeof(float) * c->nx, sizeof(float), c->ny,
+                              cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaMemcpy2DAsync(col0.data(), sizeof(float), s0, sizeof(float) * c->nx, sizeof(float), c->ny,
+                              cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  const double ytop = crossing_from_top(col1, 0.5);
+  double H, th;
+  if (mode == 0) {
+    const double ywall = crossing_from_bottom(col0, 0.5);
+    H = ytop - ywall;
+    const double R0 = sqrt(2.0 * ob.mass1 / M_PI);
+    th = bisect(flat_ratio, 1e-6, M_PI - 1e-6, H / R0);
+  } else {
+    H = ytop - y_c;
+    const double S0 = ob.mass1;
+    th = bisect([&](double t) { return disk_hmax(t, disk_radius, S0); }, 1e-3, M_PI - 1e-3, H);
+  }
+  if (theta_deg) *theta_deg = th * 180.0 / M_PI;
+  if (height) *height = H;
+  if (!isfinite(H)) return set_err(c, LBM_EINVAL, "no phi1 = 1/2 crossing on that column");
+  return LBM_OK;
+}
+
+int lbm_get_shape(const lbm_ctx* c, int* nx, int* ny, int* nz, int* nbatch, int* q) {
+  if (!c) return LBM_EINVAL;
+  if (nx) *nx = c->nx;
+  if (ny) *ny = c->ny;
+  if (nz) *nz = c->nz;
+  if (nbatch) *nbatch = c->nbatch;
+  if (q) *q = c->q;
+  return LBM_OK;
+}
+
+const char* lbm_strerror(int s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EDIVERGED: return "simulation diverged";
+    case LBM_ETIMEOUT: return "device wait timed out";
+    case LBM_ESTATE: return "invalid context state";
+    case LBM_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : g_last_error; }
+
+}  // extern "C"

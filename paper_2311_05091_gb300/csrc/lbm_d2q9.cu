@@ -1,0 +1,610 @@
+// D2Q9 kernels of the coupled CH + NS step (Zhan, Chai, Shi, arXiv 2311.05091).
+//
+// One fused kernel per time step.  Each CTA owns a strip of BX columns and
+// `strip` rows and sweeps it from bottom to top with shared-memory rings:
+//
+//   stage 1, row y+2: phi1 = sum_i f_i (push-streamed populations at rest in
+//            HBM) for the CTA's columns plus two halo columns each side, and
+//            phi0; the owned populations are kept for the collision.
+//   stage 2, row y+1: mubar_1 from the isotropic stencil of phi0 / phi1
+//            (Sec. 2.1, Eq. CHmodel) on BX + 2 columns; history (u, S) of the
+//            previous step for the correction-force stencil.
+//   stage 3, row y:   gradients, forces, velocity, pressure, both Hermite
+//            collisions in closed form (Sec. 3, Sec. 4 intro, Appendix A) and
+//            the push-streaming store with half-way bounce-back.
+//
+// HBM traffic per node and step: f and g read and written (144 B), phi0 read
+// (4 B), history phi1/u/S read and written (40 B): 188 B.  Halo rows and
+// columns are re-read from L2.
+//
+// Layouts: see include/lbm.h.  The NS rest population is stored minus the
+// constant rho_0 of lambda_0, so every stored g is O(p/cs2) and float32 keeps
+// its relative precision; the dynamics do not depend on that constant.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int BX = 128;   // columns (threads) per CTA
+constexpr int RP = 5;     // ring depth of phi0 / phi1 rows
+constexpr int RM = 3;     // ring depth of mubar / history rows
+constexpr float kOneMinusPhi0Floor = 5.9604644775390625e-8f;  // 2^-24
+
+__device__ __forceinline__ int wrap_or_mirror(int i, int n, int per) {
+  if (per) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  if (i < 0) return -1 - i;          // mirror ghost across the half-way wall
+  if (i >= n) return 2 * n - 1 - i;
+  return i;
+}
+
+__device__ __forceinline__ int ring(int r, int n) { return ((r % n) + n) % n; }
+
+// 3x3 neighbourhood: centre, axis (e, n, w, s) and diagonal (ne, nw, sw, se).
+struct P9 {
+  float c, e, n, w, s, ne, nw, sw, se;
+};
+
+// Isotropic central gradient with the D2Q9 weights of d0 = 1/3:
+// grad v = sum_i w_i c_i v(x + c_i) / (1/3), w = 1/9 (axis), 1/36 (diagonal).
+__device__ __forceinline__ void iso_grad(const P9& v, float& gx, float& gy) {
+  gx = (v.e - v.w) * (1.f / 3.f) + ((v.ne + v.se) - (v.nw + v.sw)) * (1.f / 12.f);
+  gy = (v.n - v.s) * (1.f / 3.f) + ((v.ne + v.nw) - (v.se + v.sw)) * (1.f / 12.f);
+}
+
+// Isotropic Laplacian: sum_i 2 w_i (v(x + c_i) - v(x)) / (1/3).
+__device__ __forceinline__ float iso_lap(const P9& v) {
+  const float a = (v.e - v.c) + (v.w - v.c) + (v.n - v.c) + (v.s - v.c);
+  const float d = (v.ne - v.c) + (v.nw - v.c) + (v.sw - v.c) + (v.se - v.c);
+  return a * (2.f / 3.f) + d * (1.f / 6.f);
+}
+
+// mu_p = gamma_p psi_p, psi_p = (12/D) phi_p (1 - phi_p)(1 - 2 phi_p) - (3D/4) lap phi_p.
+__device__ __forceinline__ void chem_pot(const InstanceConsts& k, float ph0, float ph1, float lap0,
+                                         float lap1, float& mu0, float& mu1, float& mu2) {
+  const float ph2 = 1.f - ph0 - ph1;
+  const float lap2 = -lap0 - lap1;
+  const float psi0 = k.c12_W * ph0 * (1.f - ph0) * (1.f - 2.f * ph0) - k.c34_W * lap0;
+  const float psi1 = k.c12_W * ph1 * (1.f - ph1) * (1.f - 2.f * ph1) - k.c34_W * lap1;
+  const float psi2 = k.c12_W * ph2 * (1.f - ph2) * (1.f - 2.f * ph2) - k.c34_W * lap2;
+  mu0 = k.gam0 * psi0;
+  mu1 = k.gam1 * psi1;
+  mu2 = k.gam2 * psi2;
+}
+
+// mubar_1 = gamma_T/3 [ (mu1 - mu0)/gamma_0 + (mu1 - mu2)/gamma_2 ].
+__device__ __forceinline__ float mubar1_of(const InstanceConsts& k, float mu0, float mu1, float mu2) {
+  return k.gT3 * ((mu1 - mu0) * k.inv_gam0 + (mu1 - mu2) * k.inv_gam2);
+}
+
+// Natural moments (rows of M0, Appendix A) of nine populations.
+struct Nat {
+  float m0, mx, my, mxx, myy, mxy, mxyy, mxxy, mxxyy;
+};
+
+__device__ __forceinline__ Nat natural(const float* v) {
+  Nat m;
+  const float d5678 = v[5] + v[6] + v[7] + v[8];
+  m.m0 = ((v[0] + v[1]) + (v[2] + v[3])) + (v[4] + d5678);
+  m.mx = (v[1] - v[3]) + (v[5] - v[6]) - (v[7] - v[8]);
+  m.my = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+  m.mxx = (v[1] + v[3]) + d5678;
+  m.myy = (v[2] + v[4]) + d5678;
+  m.mxy = (v[5] - v[6]) + (v[7] - v[8]);
+  m.mxyy = (v[5] - v[6]) - (v[7] - v[8]);
+  m.mxxy = (v[5] + v[6]) - (v[7] + v[8]);
+  m.mxxyy = d5678;
+  return m;
+}
+
+// Populations from natural moments (M0^-1 in closed form).
+__device__ __forceinline__ void from_natural(const Nat& m, float* v) {
+  v[0] = m.m0 - m.mxx - m.myy + m.mxxyy;
+  v[1] = 0.5f * (m.mx + m.mxx - m.mxyy - m.mxxyy);
+  v[2] = 0.5f * (m.my + m.myy - m.mxxy - m.mxxyy);
+  v[3] = 0.5f * (-m.mx + m.mxx + m.mxyy - m.mxxyy);
+  v[4] = 0.5f * (-m.my + m.myy + m.mxxy - m.mxxyy);
+  v[5] = 0.25f * (m.mxy + m.mxyy + m.mxxy + m.mxxyy);
+  v[6] = 0.25f * (-m.mxy - m.mxyy + m.mxxy + m.mxxyy);
+  v[7] = 0.25f * (m.mxy - m.mxyy - m.mxxy + m.mxxyy);
+  v[8] = 0.25f * (-m.mxy + m.mxyy - m.mxxy + m.mxxyy);
+}
+
+// Hermite moments H = N M0 v with the printed N (Appendix A) and back.
+struct Her {
+  float h0, hx, hy, hxx, hyy, hxy, hxyy, hxxy, h4;
+};
+
+__device__ __forceinline__ Her hermite(const Nat& m, float cs2, float cs4) {
+  Her h;
+  h.h0 = m.m0;
+  h.hx = m.mx;
+  h.hy = m.my;
+  h.hxx = m.mxx - cs2 * m.m0;
+  h.hyy = m.myy - cs2 * m.m0;
+  h.hxy = m.mxy;
+  h.hxyy = m.mxyy - cs2 * m.mx;
+  h.hxxy = m.mxxy - cs2 * m.my;
+  h.h4 = m.mxxyy - cs2 * (m.mxx + m.myy) + cs4 * m.m0;
+  return h;
+}
+
+__device__ __forceinline__ Nat natural_of(const Her& h, float cs2, float cs4) {
+  Nat m;
+  m.m0 = h.h0;
+  m.mx = h.hx;
+  m.my = h.hy;
+  m.mxx = h.hxx + cs2 * h.h0;
+  m.myy = h.hyy + cs2 * h.h0;
+  m.mxy = h.hxy;
+  m.mxyy = h.hxyy + cs2 * h.hx;
+  m.mxxy = h.hxxy + cs2 * h.hy;
+  m.mxxyy = h.h4 + cs2 * (h.hxx + h.hyy) + cs4 * h.h0;
+  return m;
+}
+
+
+
+
+// Push-stream v (direction i, opposite io) from (x, y); half-way bounce-back
+// sends a population that would leave through a wall back into slot io.
+__device__ __forceinline__ void push(float* __restrict__ out, long long plane, int i, int io, int cx, int cy,
+                                     int x, int y, int nx, int ny, int per_x, int per_y, float v) {
+  int xd = x + cx, yd = y + cy;
+  bool bb = false;
+  if (xd < 0 || xd >= nx) {
+    if (per_x) xd = xd < 0 ? xd + nx : xd - nx;
+    else bb = true;
+  }
+  if (yd < 0 || yd >= ny) {
+    if (per_y) yd = yd < 0 ? yd + ny : yd - ny;
+    else bb = true;
+  }
+  const long long dst = bb ? (long long)io * plane + (long long)y * nx + x
+                           : (long long)i * plane + (long long)yd * nx + xd;
+  out[dst] = v;
+}
+
+// ---------------------------------------------------------------------------
+// initial state: f = f^eq(phi1, mubar_1, u = 0), g = g^eq(p = 0, u = 0) - rho_0 e_0 = 0,
+// history = (phi1, 0, 0, 0, 0)
+// ---------------------------------------------------------------------------
+__global__ void d2q9_init(const float* __restrict__ phi0_all, const float* __restrict__ phi1_all,
+                          float* __restrict__ f_all, float* __restrict__ g_all, float* __restrict__ hist_all,
+                          const InstanceConsts* __restrict__ consts, int nx, int ny, int per_x, int per_y) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int b = blockIdx.z;
+  if (x >= nx) return;
+  const InstanceConsts& k = consts[b];
+  const long long plane = (long long)nx * ny;
+  const float* phi0 = phi0_all + (long long)b * plane;
+  const float* phi1 = phi1_all + (long long)b * 5 * plane;   // staged in a history plane
+  auto at = [&](const float* a, int dx, int dy) {
+    const int xx = wrap_or_mirror(x + dx, nx, per_x), yy = wrap_or_mirror(y + dy, ny, per_y);
+    return a[(long long)yy * nx + xx];
+  };
+  P9 v0{at(phi0, 0, 0), at(phi0, 1, 0), at(phi0, 0, 1), at(phi0, -1, 0), at(phi0, 0, -1),
+        at(phi0, 1, 1), at(phi0, -1, 1), at(phi0, -1, -1), at(phi0, 1, -1)};
+  P9 v1{at(phi1, 0, 0), at(phi1, 1, 0), at(phi1, 0, 1), at(phi1, -1, 0), at(phi1, 0, -1),
+        at(phi1, 1, 1), at(phi1, -1, 1), at(phi1, -1, -1), at(phi1, 1, -1)};
+  float mu0, mu1, mu2;
+  chem_pot(k, v0.c, v1.c, iso_lap(v0), iso_lap(v1), mu0, mu1, mu2);
+  const float emb = k.eta * mubar1_of(k, mu0, mu1, mu2);
+  const long long node = (long long)y * nx + x;
+  float* f = f_all + (long long)b * 9 * plane;
+  float* g = g_all + (long long)b * 9 * plane;
+  float* h = hist_all + (long long)b * 5 * plane;
+  f[node] = v1.c + (k.w0 - 1.f) * emb;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) f[(long long)i * plane + node] = (i < 5 ? k.wa : k.we) * emb;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) g[(long long)i * plane + node] = 0.f;
+  h[node] = v1.c;
+#pragma unroll
+  for (int q = 1; q < 5; ++q) h[(long long)q * plane + node] = 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// fused step, software-pipelined: every thread streams its own column (and the
+// halo threads their halo columns) of row y+2+D into a shared-memory slot with
+// asynchronous copies while rows y+2 .. y are being processed, so D rows of
+// loads stay in flight across the compute.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// one row of every array the step reads: populations f with two halo columns
+// each side, phi0 likewise, history (phi1, u, S) with one halo column, g own
+struct RowSlot {
+  float f[9][BX + 4];
+  float p0[BX + 4];
+  float h[5][BX + 2];
+  float g[9][BX];
+};
+
+template <int D>
+struct StepSmem {
+  RowSlot slot[D + 3];
+  float phi1[RP][BX + 4];
+  float phi0[RP][BX + 4];
+  float mub[RM][BX + 2];
+  float h[RM][4][BX + 2];
+  InstanceConsts k;
+};
+
+template <int D>
+constexpr size_t step_smem_bytes() { return sizeof(StepSmem<D>); }
+
+template <bool OBS, int D>
+__global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem<D>& S = *reinterpret_cast<StepSmem<D>*>(smem_raw);
+  constexpr int R = D + 3;
+
+  const int t = threadIdx.x;
+  const int x0 = blockIdx.x * BX;
+  const int nx = a.nx, ny = a.ny, per_x = a.per_x, per_y = a.per_y;
+  const int ys = blockIdx.y * a.strip;
+  const int ye = min(ys + a.strip, ny);
+  const int b = blockIdx.z;
+  const long long plane = a.nodes;
+  static_assert(sizeof(InstanceConsts) / 4 <= BX, "constants copied one word per thread");
+  if (t < (int)(sizeof(InstanceConsts) / 4))
+    reinterpret_cast<float*>(&S.k)[t] = reinterpret_cast<const float*>(a.consts + b)[t];
+  const float* __restrict__ f_in = a.f_in + (long long)b * 9 * plane;
+  const float* __restrict__ g_in = a.g_in + (long long)b * 9 * plane;
+  float* __restrict__ f_out = a.f_out + (long long)b * 9 * plane;
+  float* __restrict__ g_out = a.g_out + (long long)b * 9 * plane;
+  const float* __restrict__ phi0 = a.phi0 + (long long)b * plane;
+  const float* __restrict__ h_in = a.hist_in + (long long)b * 5 * plane;
+  float* __restrict__ h_out = a.hist_out + (long long)b * 5 * plane;
+
+  // columns this thread stages: its own, plus halo columns for threads 0..3
+  const int x_own = x0 + t;
+  const int c_halo = t < 2 ? t : BX + t;             // f / phi0 slot of the halo column (t < 4)
+  const int x_halo = x0 - 2 + c_halo;
+  const int s_halo = t == 0 ? 0 : BX + 1;            // history slot of the halo column (t < 2)
+  const int xh_halo = x0 - 1 + s_halo;
+  const int px_own = wrap_or_mirror(x_own, nx, per_x);
+  const int px_halo = wrap_or_mirror(x_halo, nx, per_x);
+  const int pxh_halo = wrap_or_mirror(xh_halo, nx, per_x);
+
+  // issue the asynchronous copies of logical row r into its slot
+  auto issue = [&](int r) {
+    if (r <= ye + 1) {
+      RowSlot& sl = S.slot[(r - (ys - 2)) % R];
+      const long long rowb = (long long)wrap_or_mirror(r, ny, per_y) * nx;
+      if (x_own <= nx + 1) {
+        const long long idx = rowb + px_own;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cp_async4(&sl.f[i][t + 2], f_in + (long long)i * plane + idx);
+        cp_async4(&sl.p0[t + 2], phi0 + idx);
+        if (x_own <= nx) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q) cp_async4(&sl.h[q][t + 1], h_in + (long long)q * plane + idx);
+        }
+        if (x_own < nx && r >= ys && r < ye) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) cp_async4(&sl.g[i][t], g_in + (long long)i * plane + idx);
+        }
+      }
+      if (t < 4 && x_halo <= nx + 1) {
+        const long long idx = rowb + px_halo;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cp_async4(&sl.f[i][c_halo], f_in + (long long)i * plane + idx);
+        cp_async4(&sl.p0[c_halo], phi0 + idx);
+      }
+      if (t < 2 && xh_halo <= nx) {
+        const long long idx = rowb + pxh_halo;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) cp_async4(&sl.h[q][s_halo], h_in + (long long)q * plane + idx);
+      }
+    }
+    cp_commit();   // empty groups keep the group count uniform
+  };
+
+  // stage 1: phi1 = sum f and phi0 of row r into the rings (each thread reads
+  // only the columns it copied itself, so no barrier is needed before it)
+  auto stage1 = [&](int r) {
+    const RowSlot& sl = S.slot[(r - (ys - 2)) % R];
+    const int sp = ring(r, RP);
+    if (x_own <= nx + 1) {
+      float sum = sl.f[0][t + 2];
+#pragma unroll
+      for (int i = 1; i < 9; ++i) sum += sl.f[i][t + 2];
+      S.phi1[sp][t + 2] = sum;
+      S.phi0[sp][t + 2] = sl.p0[t + 2];
+    }
+    if (t < 4 && x_halo <= nx + 1) {
+      float sum = sl.f[0][c_halo];
+#pragma unroll
+      for (int i = 1; i < 9; ++i) sum += sl.f[i][c_halo];
+      S.phi1[sp][c_halo] = sum;
+      S.phi0[sp][c_halo] = sl.p0[c_halo];
+    }
+  };
+
+  const InstanceConsts& k = S.k;
+
+  // stage 2: mubar_1 of row r and the previous-step (u, S) into the rings
+  auto stage2 = [&](int r) {
+    const RowSlot& sl = S.slot[(r - (ys - 2)) % R];
+    const int sm = ring(r, RM);
+    const int p0 = ring(r, RP), pm = ring(r - 1, RP), pp = ring(r + 1, RP);
+    auto one = [&](int s) {
+      const int xl = x0 - 1 + s;
+      if (xl > nx) return;
+      const int c = s + 1;
+      const P9 v1{S.phi1[p0][c], S.phi1[p0][c + 1], S.phi1[pp][c], S.phi1[p0][c - 1], S.phi1[pm][c],
+                  S.phi1[pp][c + 1], S.phi1[pp][c - 1], S.phi1[pm][c - 1], S.phi1[pm][c + 1]};
+      const P9 v0{S.phi0[p0][c], S.phi0[p0][c + 1], S.phi0[pp][c], S.phi0[p0][c - 1], S.phi0[pm][c],
+                  S.phi0[pp][c + 1], S.phi0[pp][c - 1], S.phi0[pm][c - 1], S.phi0[pm][c + 1]};
+      float mu0, mu1, mu2;
+      chem_pot(k, v0.c, v1.c, iso_lap(v0), iso_lap(v1), mu0, mu1, mu2);
+      S.mub[sm][s] = mubar1_of(k, mu0, mu1, mu2);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) S.h[sm][q][s] = sl.h[q + 1][s];
+    };
+    one(t + 1);
+    if (t == 0) one(0);
+    if (t == 1) one(BX + 1);
+  };
+
+  // stage 3: collide and stream row y
+  auto stage3 = [&](int y) {
+    const int x = x0 + t;
+    if (x >= nx) return;
+    const RowSlot& sl = S.slot[(y - (ys - 2)) % R];
+    const int c = t + 2, s = t + 1;
+    const int p0 = ring(y, RP), pm = ring(y - 1, RP), pp = ring(y + 1, RP);
+    const int m0 = ring(y, RM), mm = ring(y - 1, RM), mp = ring(y + 1, RM);
+    const long long node = (long long)y * nx + x;
+    const float cs2 = k.cs2, cs4 = k.cs4;
+    float g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = sl.g[i][t];
+    const float php = sl.h[0][s];
+
+    const P9 v1{S.phi1[p0][c], S.phi1[p0][c + 1], S.phi1[pp][c], S.phi1[p0][c - 1], S.phi1[pm][c],
+                S.phi1[pp][c + 1], S.phi1[pp][c - 1], S.phi1[pm][c - 1], S.phi1[pm][c + 1]};
+    const P9 v0{S.phi0[p0][c], S.phi0[p0][c + 1], S.phi0[pp][c], S.phi0[p0][c - 1], S.phi0[pm][c],
+                S.phi0[pp][c + 1], S.phi0[pp][c - 1], S.phi0[pm][c - 1], S.phi0[pm][c + 1]};
+    const P9 vm{S.mub[m0][s], S.mub[m0][s + 1], S.mub[mp][s], S.mub[m0][s - 1], S.mub[mm][s],
+                S.mub[mp][s + 1], S.mub[mp][s - 1], S.mub[mm][s - 1], S.mub[mm][s + 1]};
+    // A = S_x u_y - u_x S_y of the previous step at the eight neighbours
+    auto A = [&](int row, int col) {
+      return S.h[row][2][col] * S.h[row][1][col] - S.h[row][0][col] * S.h[row][3][col];
+    };
+    const P9 va{0.f, A(m0, s + 1), A(mp, s), A(m0, s - 1), A(mm, s), A(mp, s + 1), A(mp, s - 1),
+                A(mm, s - 1), A(mm, s + 1)};
+    const float ph1 = v1.c, ph0 = v0.c, ph2 = 1.f - ph0 - ph1;
+    float g1x, g1y, g0x, g0y, gmx, gmy, dAx, dAy;
+    iso_grad(v1, g1x, g1y);
+    iso_grad(v0, g0x, g0y);
+    iso_grad(vm, gmx, gmy);
+    iso_grad(va, dAx, dAy);
+    float mu0, mu1, mu2;
+    chem_pot(k, ph0, ph1, iso_lap(v0), iso_lap(v1), mu0, mu1, mu2);
+    const float mub = vm.c;
+
+    // degenerate mobility, mass flux S (frozen phi0), mixture properties
+    const float fdeg = ph1 * (1.f - ph1) * (1.f - ph0);
+    const float mob = k.M_cst + k.M_deg * fdeg;
+    const float sfac = (k.rho1 - k.rho2) * mob * k.inv_gam1;
+    const float Sx = sfac * gmx, Sy = sfac * gmy;
+    const float rho = k.rho0 * ph0 + k.rho1 * ph1 + k.rho2 * ph2;
+    const float grx = (k.rho0 - k.rho2) * g0x + (k.rho1 - k.rho2) * g1x;
+    const float gry = (k.rho0 - k.rho2) * g0y + (k.rho1 - k.rho2) * g1y;
+    const float muv = k.mu0 * ph0 + k.mu1 * ph1 + k.mu2 * ph2;
+
+    // F = F_s + F_b + F_c
+    const float one_m0 = 1.f - ph0;
+    const float Fx = (mu0 - mu2) * g0x + (mu1 - mu2) * g1x + one_m0 * k.bx - 0.5f * dAy;
+    const float Fy = (mu0 - mu2) * g0y + (mu1 - mu2) * g1y + one_m0 * k.by + 0.5f * dAx;
+
+    // NS moments, velocity with the solid penalisation force
+    const Nat ng = natural(g);
+    const float inv_rho = 1.f / rho;
+    const float usx = (ng.mx + 0.5f * Fx) * inv_rho;
+    const float usy = (ng.my + 0.5f * Fy) * inv_rho;
+    const float damp = 1.f - 0.5f * ph0;
+    const float ux = usx * damp, uy = usy * damp;
+    const float Ftx = Fx - ph0 * rho * usx, Fty = Fy - ph0 * rho * usy;
+
+    // local viscous rates (s0 = s4 = s2a)
+    const float om = fmaxf(one_m0, kOneMinusPhi0Floor);
+    const float ra = rho * om * k.a2a, rb = rho * om * k.a2b;
+    const float s2a = ra / (0.5f * ra + muv);
+    const float s2b = rb / (0.5f * rb + muv);
+    const float inv_s2a = 0.5f + muv / ra;
+
+    // pressure
+    const float uxp = S.h[m0][0][s], uyp = S.h[m0][1][s], Sxp = S.h[m0][2][s], Syp = S.h[m0][3][s];
+    const float udg = ux * grx + uy * gry;
+    const float q = (rho * ux - Sx) * ux + (rho * uy - Sy) * uy;
+    const float rhop = k.rho0 * ph0 + k.rho1 * php + k.rho2 * (1.f - ph0 - php);
+    const float qp = (rhop * uxp - Sxp) * uxp + (rhop * uyp - Syp) * uyp;
+    const float H = k.Kp * ((k.h0 - k.h2) * inv_s2a + k.h3);
+    const float sum_nz = ng.m0 - g[0];
+    const float p = k.pf * (sum_nz + (0.5f + H) * udg - k.wq * q + 0.5f * k.Kp * (q - qp));
+
+    // ---- NS collision in Hermite space ----
+    {
+      const Her h = hermite(ng, cs2, cs4);
+      const float exx = p + rho * ux * ux - Sx * ux;
+      const float eyy = p + rho * uy * uy - Sy * uy;
+      const float exy = rho * ux * uy - 0.5f * (Sx * uy + ux * Sy);
+      const float e4 = -cs2 * p;
+      const float dSxx = Sx * ux - Sxp * uxp;
+      const float dSyy = Sy * uy - Syp * uyp;
+      const float dSxy = 0.5f * (Sx * uy + ux * Sy) - 0.5f * (Sxp * uyp + uxp * Syp);
+      const float iso = (1.f - 3.f * cs2) * udg;
+      const float Mxx = 2.f * ux * Fx - dSxx + 2.f * cs2 * ux * grx + iso;
+      const float Myy = 2.f * uy * Fy - dSyy + 2.f * cs2 * uy * gry + iso;
+      const float Mxy = ux * Fy + Fx * uy - dSxy + cs2 * (ux * gry + grx * uy);
+      Her o;
+      o.h0 = h.h0 - s2a * h.h0 + (1.f - 0.5f * s2a) * udg;
+      o.hx = h.hx - k.s1n * (h.hx - rho * ux) + (1.f - 0.5f * k.s1n) * Ftx;
+      o.hy = h.hy - k.s1n * (h.hy - rho * uy) + (1.f - 0.5f * k.s1n) * Fty;
+      o.hxx = h.hxx - s2a * (h.hxx - exx) + (1.f - 0.5f * s2a) * Mxx;
+      o.hyy = h.hyy - s2a * (h.hyy - eyy) + (1.f - 0.5f * s2a) * Myy;
+      o.hxy = h.hxy - s2b * (h.hxy - exy) + (1.f - 0.5f * s2b) * Mxy;
+      o.hxyy = h.hxyy * (1.f - k.s3n);
+      o.hxxy = h.hxxy * (1.f - k.s3n);
+      o.h4 = h.h4 - s2a * (h.h4 - e4);
+      float go[9];
+      from_natural(natural_of(o, cs2, cs4), go);
+      push(g_out, plane, 0, 0, 0, 0, x, y, nx, ny, per_x, per_y, go[0]);
+      push(g_out, plane, 1, 3, 1, 0, x, y, nx, ny, per_x, per_y, go[1]);
+      push(g_out, plane, 2, 4, 0, 1, x, y, nx, ny, per_x, per_y, go[2]);
+      push(g_out, plane, 3, 1, -1, 0, x, y, nx, ny, per_x, per_y, go[3]);
+      push(g_out, plane, 4, 2, 0, -1, x, y, nx, ny, per_x, per_y, go[4]);
+      push(g_out, plane, 5, 7, 1, 1, x, y, nx, ny, per_x, per_y, go[5]);
+      push(g_out, plane, 6, 8, -1, 1, x, y, nx, ny, per_x, per_y, go[6]);
+      push(g_out, plane, 7, 5, -1, -1, x, y, nx, ny, per_x, per_y, go[7]);
+      push(g_out, plane, 8, 6, 1, -1, x, y, nx, ny, per_x, per_y, go[8]);
+    }
+
+    // ---- CH collision ----
+    {
+      float fv[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fv[i] = sl.f[i][c];
+      Nat nf = natural(fv);
+      nf.m0 = ph1;   // zeroth moment is the phase field itself
+      const float emb = k.eta * mub;
+      const float corr = k.corr_scale * (1.f - fdeg);
+      // R first moment: d_t(phi1 u) + cs2 * corr * eta grad mubar
+      const float Rx = (ph1 * ux - php * uxp) + cs2 * corr * k.eta * gmx;
+      const float Ry = (ph1 * uy - php * uyp) + cs2 * corr * k.eta * gmy;
+      float fo[9];
+      if (k.ch_fast != 0.f) {
+        // every moment but the first relaxes at rate 1, so f* = f^eq + w_i c_i . dj / cs2 with
+        // the post-collision first moment o = phi u + (1 - s1)(j - phi u) + (1 - s1/2) R
+        const float ox = ph1 * ux + (1.f - k.s1c) * (nf.mx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx;
+        const float oy = ph1 * uy + (1.f - k.s1c) * (nf.my - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry;
+        const float ic = 1.f / cs2;
+        const float ax = ox * ic, ay = oy * ic;
+        fo[1] = k.wa * (emb + ax);
+        fo[3] = k.wa * (emb - ax);
+        fo[2] = k.wa * (emb + ay);
+        fo[4] = k.wa * (emb - ay);
+        fo[5] = k.we * (emb + ax + ay);
+        fo[6] = k.we * (emb - ax + ay);
+        fo[7] = k.we * (emb - ax - ay);
+        fo[8] = k.we * (emb + ax - ay);
+        // rest population closes the zeroth moment exactly
+        fo[0] = ph1 - (((fo[1] + fo[3]) + (fo[2] + fo[4])) + ((fo[5] + fo[7]) + (fo[6] + fo[8])));
+      } else {
+        const Her h = hermite(nf, cs2, cs4);
+        const float exx = cs2 * (emb - ph1);
+        Her o;
+        o.h0 = ph1;
+        o.hx = h.hx - k.s1c * (h.hx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx;
+        o.hy = h.hy - k.s1c * (h.hy - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry;
+        o.hxx = h.hxx - k.s2ac * (h.hxx - exx);
+        o.hyy = h.hyy - k.s2ac * (h.hyy - exx);
+        o.hxy = h.hxy * (1.f - k.s2bc);
+        o.hxyy = h.hxyy * (1.f - k.s3c);
+        o.hxxy = h.hxxy * (1.f - k.s3c);
+        o.h4 = h.h4 - k.s4c * (h.h4 - cs4 * (ph1 - emb));
+        from_natural(natural_of(o, cs2, cs4), fo);
+      }
+      push(f_out, plane, 0, 0, 0, 0, x, y, nx, ny, per_x, per_y, fo[0]);
+      push(f_out, plane, 1, 3, 1, 0, x, y, nx, ny, per_x, per_y, fo[1]);
+      push(f_out, plane, 2, 4, 0, 1, x, y, nx, ny, per_x, per_y, fo[2]);
+      push(f_out, plane, 3, 1, -1, 0, x, y, nx, ny, per_x, per_y, fo[3]);
+      push(f_out, plane, 4, 2, 0, -1, x, y, nx, ny, per_x, per_y, fo[4]);
+      push(f_out, plane, 5, 7, 1, 1, x, y, nx, ny, per_x, per_y, fo[5]);
+      push(f_out, plane, 6, 8, -1, 1, x, y, nx, ny, per_x, per_y, fo[6]);
+      push(f_out, plane, 7, 5, -1, -1, x, y, nx, ny, per_x, per_y, fo[7]);
+      push(f_out, plane, 8, 6, 1, -1, x, y, nx, ny, per_x, per_y, fo[8]);
+    }
+
+    // history of this step
+    h_out[node] = ph1;
+    h_out[plane + node] = ux;
+    h_out[2 * plane + node] = uy;
+    h_out[3 * plane + node] = Sx;
+    h_out[4 * plane + node] = Sy;
+    if (OBS) {
+      a.p_out[(long long)b * plane + node] = p;
+      const float u2 = ux * ux + uy * uy;
+      if (!(u2 <= 0.25f) || !(fabsf(ph1) < 1e30f)) atomicOr(a.flag, 1u);
+    }
+  };
+
+  // prologue: copies of rows ys-2 .. ys+D, phi rows ys-2 .. ys+1, mubar / history rows ys-1, ys
+  for (int r = ys - 2; r <= ys + D; ++r) issue(r);
+  __syncthreads();   // constants visible
+  cp_wait<R - 1>();
+  stage1(ys - 2);
+  issue(ys + 1 + D);   // reuses the slot of row ys-2, read above by this thread only
+  cp_wait<R - 1>();
+  stage1(ys - 1);
+  cp_wait<R - 2>();
+  stage1(ys);
+  cp_wait<R - 3>();
+  stage1(ys + 1);
+  __syncthreads();
+  stage2(ys - 1);
+  stage2(ys);
+  __syncthreads();
+  for (int y = ys; y < ye; ++y) {
+    // the slot of row y+2+D last held row y-1, whose final reader was this
+    // thread's own stage 3 of the previous iteration
+    issue(y + 2 + D);
+    cp_wait<D>();
+    stage1(y + 2);
+    __syncthreads();
+    stage2(y + 1);
+    __syncthreads();
+    stage3(y);
+  }
+  cp_wait<0>();
+}
+
+}  // namespace
+
+cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, float* g, float* hist,
+                             const InstanceConsts* consts, int nx, int ny, int per_x, int per_y,
+                             int nbatch, cudaStream_t s) {
+  dim3 block(128), grid((nx + 127) / 128, ny, nbatch);
+  d2q9_init<<<grid, block, 0, s>>>(phi0, phi1, f, g, hist, consts, nx, ny, per_x, per_y);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_depth(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+  const size_t smem = step_smem_bytes<D>();
+  static bool configured = false;   // attribute set once per process (both variants)
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(d2q9_step<true, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(d2q9_step<false, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 block(BX), grid((a.nx + BX - 1) / BX, (a.ny + a.strip - 1) / a.strip, nbatch);
+  if (observe) d2q9_step<true, D><<<grid, block, smem, s>>>(a);
+  else d2q9_step<false, D><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+  switch (a.depth) {
+    case 1: return launch_depth<1>(a, nbatch, observe, s);
+    case 3: return launch_depth<3>(a, nbatch, observe, s);
+    default: return launch_depth<2>(a, nbatch, observe, s);
+  }
+}
+
+}  // namespace lbm

@@ -1,0 +1,81 @@
+// Internal declarations shared by the library's translation units.
+//
+// Per-instance constants are derived on the host in double precision (model
+// parameters of Sec. 2.2 and Sec. 3 of the paper) and stored on the device as
+// float32 in one `InstanceConsts` record per batch instance.  Kernels read the
+// record of their instance once (uniform address, broadcast) into registers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+struct InstanceConsts {
+  // lattice (cs2 = d0, weights of the scale-factor lattice)
+  float cs2, cs4, w0, wa, we;      // D2Q9: wa = axis weight, we = diagonal weight
+                                   // D3Q19: wa = axis weight, we = edge weight
+  // free energy (Sec. 2.1): 12/D and 3D/4
+  float c12_W, c34_W;
+  // spreading coefficients gamma_p, gamma_T/3, their inverses
+  float gam0, gam1, gam2, gT3, inv_gam0, inv_gam1, inv_gam2;
+  // CH: eta_1, mobility, rates (s1 from Sec. 3 relation, free rates)
+  float eta, M_cst, M_deg, corr_scale;   // corr_scale = M_deg / (M_cst + M_deg)
+  float s1c, s0c, s2ac, s2bc, s3c, s4c;
+  // NS: free rates s1, s3 (s0 and s4 follow the local s2a)
+  float s1n, s3n;
+  // densities and dynamic viscosities of solid, fluid 1, fluid 2
+  float rho0, rho1, rho2, mu0, mu1, mu2;
+  // body force density
+  float bx, by, bz;
+  // viscosity relation: s2a uses (c^2 - cs2)/2, s2b uses cs2
+  float a2a, a2b;
+  // pressure formula (Sec. 3): p = pf * [sum_{i!=0} g_i + (1/2 + H) u.grad rho
+  //   - wq * (rho u - S).u + K/2 * d_t((rho u - S).u)],
+  // H = K * (h0 * inv_s0 - h2 * inv_s2a + h3), pf = cs2/(1-w0), wq = w0/(1-cs2)
+  float pf, wq, Kp, h0, h2, h3;
+  float ch_fast;   // 1 when every free CH rate is 1: closed form f* = f^eq + first-moment part
+  float pad;
+};
+
+// Launch arguments of the fused step kernel (both lattices).
+struct StepArgs {
+  const float* f_in;
+  float* f_out;
+  const float* g_in;
+  float* g_out;
+  const float* phi0;
+  const float* hist_in;   // [b][k][nodes]: phi1, u (d), S (d) at the previous step
+  float* hist_out;
+  float* p_out;           // written only by the observing variant
+  const InstanceConsts* consts;
+  unsigned int* flag;     // divergence flag (observing variant)
+  int nx, ny, nz;
+  int per_x, per_y, per_z;
+  int strip;              // rows (2D) or planes (3D) per CTA
+  int depth;              // rows of asynchronous copies kept in flight (1..3)
+  long long nodes;        // nodes per instance
+};
+
+// Kernel launchers (return cudaGetLastError of the launch).
+cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, float* g,
+                             float* hist, const InstanceConsts* consts, int nx, int ny,
+                             int per_x, int per_y, int nbatch, cudaStream_t s);
+cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s);
+
+cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, float* g,
+                              float* hist, const InstanceConsts* consts, int nx, int ny, int nz,
+                              int per_x, int per_y, int per_z, int nbatch, cudaStream_t s);
+cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s);
+
+// Observables: deterministic two-pass reduction of one instance.
+//   phi0, phi1, u (d planes), p: device fields of one instance, n nodes.
+//   partials: scratch of obs_partials_len(n) doubles.  out: 8 doubles
+//   [sum phi1, sum phi0, max|u|, sum p_in, n_in, sum p_out, n_out, nonfinite].
+int obs_partials_blocks(long long n);
+long long obs_partials_len(long long n);
+cudaError_t launch_observables(const float* phi0, const float* phi1, const float* u, int d,
+                               const float* p, long long n, double* partials, double* out,
+                               cudaStream_t s);
+
+}  // namespace lbm
