@@ -198,6 +198,30 @@ int lbm_set_state(lbm_ctx* ctx, const void* buf, size_t bytes);
  * two-pass tree over warp-shuffle partials).  Synchronous. */
 int lbm_observables(lbm_ctx* ctx, int instance, lbm_obs* out);
 
+/* Allocation-free diagnostics, for callers that cannot allocate device memory
+ * when they need these numbers: a solver embedded in an application that owns
+ * all device memory through its own pool, a latency-bound loop in which
+ * cudaMalloc would synchronise the device, or a caller out of memory budget.
+ * The paper has no counterpart; this is a service of the library.
+ *
+ * Same sums as lbm_observables, computed from caller-owned device buffers of
+ * one instance: phi0, phi1, p (n floats each), u (d planes of n floats, d in
+ * 1..3).  out: device buffer of 8 doubles receiving sum phi1, sum phi0,
+ * max |u|, sum p over phi1 >= 0.99, that node count, sum p over phi2 >= 0.99,
+ * that node count, number of non-finite nodes.  The work is enqueued on
+ * `stream` (a cudaStream_t, NULL for the legacy stream); read `out` after
+ * synchronising it.  No device memory is allocated or freed: the partial sums
+ * live in a fixed 1 MiB array inside the library (one record per 1024 nodes),
+ * resident on every device that loads the library until exit, so n is at most
+ * 16,777,216; larger n, n < 1, NULL buffers or a bad d give LBM_EINVAL before
+ * any launch.  The first call on each device looks the array's device address
+ * up (cudaGetSymbolAddress); make it before capturing a stream.  Every call
+ * shares the array and it keeps the previous call's contents (nothing needs
+ * clearing: each call overwrites the records it reads); calls whose kernels
+ * overlap on the GPU race on it.  LBM_ECUDA if the look-up or a launch fails. */
+int lbm_observables_noalloc(const float* phi0, const float* phi1, const float* u, int d, const float* p,
+                            long long n, double* out, void* stream);
+
 /* Contact angle of instance `instance` from the droplet height on the
  * vertical grid column x = column (2D).  mode 0: flat bottom wall, H measured
  * from the phi0 = 1/2 level on that column, R0 = sqrt(2 A / pi) from the area

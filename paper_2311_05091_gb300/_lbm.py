@@ -27,7 +27,7 @@ EXPORTS = [
     "lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy", "lbm_set_stream",
     "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
     "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
-    "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time",
+    "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_observables_noalloc",
 ]
 
 
@@ -90,6 +90,7 @@ def library():
         "lbm_get_shape": (c_int, [P] + [ctypes.POINTER(c_int)] * 5),
         "lbm_strerror": (ctypes.c_char_p, [c_int]),
         "lbm_set_profiling": (c_int, [P, c_int]),
+        "lbm_observables_noalloc": (c_int, [P, P, P, c_int, P, ctypes.c_longlong, P, P]),
         "lbm_kernel_time": (c_int, [P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_int64)]),
         "lbm_last_error": (ctypes.c_char_p, [P]),
     }
@@ -236,6 +237,13 @@ def lbm_observables(ctx, instance=0) -> dict:
     o = lbm_obs()
     _check(library().lbm_observables(ctx, instance, ctypes.byref(o)), "lbm_observables", ctx)
     return o.as_dict()
+
+
+def lbm_observables_noalloc(phi0_ptr, phi1_ptr, u_ptr, d, p_ptr, n, out_ptr, stream=0):
+    """Allocation-free diagnostics on caller-owned device buffers (see include/lbm.h);
+    returns the status code instead of raising so that callers can test the refusals."""
+    return library().lbm_observables_noalloc(c_void_p(phi0_ptr), c_void_p(phi1_ptr), c_void_p(u_ptr), d,
+                                             c_void_p(p_ptr), n, c_void_p(out_ptr), c_void_p(stream))
 
 
 def lbm_contact_angle(ctx, instance, mode, column, y_c=0.0, disk_radius=0.0):
