@@ -191,10 +191,11 @@ int derive(const lbm_params& p, int lattice, InstanceConsts& k, char* why) {
 }
 
 int default_strip(const lbm_ctx* c) {
-  // 32 rows per CTA measured best for the D2Q9 kernel on GB300 (prologue of
-  // two halo rows amortised, enough CTAs for 152 SMs at 3 CTAs each)
+  // 16 rows per CTA measured best for the D2Q9 kernel on GB300 (sweep over
+  // 16..64 rows on the 1024^2 x 5 workload: shorter strips balance the
+  // 152 SMs better than the two-row prologue of each strip costs)
   const long long rows = c->lattice == LBM_D2Q9 ? c->ny : c->nz;
-  long long strip = 32;
+  long long strip = 16;
   if (strip > rows) strip = rows;
   return (int)std::max(1LL, strip);
 }

@@ -208,26 +208,33 @@ __global__ void d2q9_init(const float* __restrict__ phi0_all, const float* __res
 }
 
 // ---------------------------------------------------------------------------
-// fused step, software-pipelined: every thread streams its own column (and the
-// halo threads their halo columns) of row y+2+D into a shared-memory slot with
-// asynchronous copies while rows y+2 .. y are being processed, so D rows of
-// loads stay in flight across the compute.
+// fused step, software-pipelined: the CTA streams row y+2+D of every array it
+// reads into a shared-memory slot with asynchronous copies while rows y+2 ..
+// y are processed, so D rows of loads stay in flight across the compute.
+// Own columns travel in 16-byte copies when the row length allows it; halo
+// columns (two each side for f and phi0, one for the history) in 4-byte
+// copies with periodic wrap or mirror ghosts.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// one row of every array the step reads: populations f with two halo columns
-// each side, phi0 likewise, history (phi1, u, S) with one halo column, g own
+constexpr int PAD = 4;          // own columns start 16 bytes into each slot row
+constexpr int W = BX + 2 * PAD; // slot row width
+constexpr int NARR = 24;        // f (9), phi0, history (5), g (9)
+
+// one row of every array the step reads; array a of the slot is rows[a]:
+// 0-8 f, 9 phi0, 10-14 history (phi1, ux, uy, Sx, Sy), 15-23 g
 struct RowSlot {
-  float f[9][BX + 4];
-  float p0[BX + 4];
-  float h[5][BX + 2];
-  float g[9][BX];
+  float rows[NARR][W];
 };
 
 template <int D>
@@ -236,12 +243,14 @@ struct StepSmem {
   float phi1[RP][BX + 4];
   float phi0[RP][BX + 4];
   float mub[RM][BX + 2];
-  float h[RM][4][BX + 2];
+  float acorr[RM][BX + 2];   // S_x u_y - u_x S_y of the previous step
   InstanceConsts k;
 };
 
 template <int D>
 constexpr size_t step_smem_bytes() { return sizeof(StepSmem<D>); }
+
+__device__ __forceinline__ int inc_mod(int v, int n) { return v + 1 == n ? 0 : v + 1; }
 
 template <bool OBS, int D>
 __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
@@ -259,315 +268,348 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
   static_assert(sizeof(InstanceConsts) / 4 <= BX, "constants copied one word per thread");
   if (t < (int)(sizeof(InstanceConsts) / 4))
     reinterpret_cast<float*>(&S.k)[t] = reinterpret_cast<const float*>(a.consts + b)[t];
+
+  // base pointers of the 24 source planes: f 0-8, phi0 9, history 10-14, g 15-23
   const float* __restrict__ f_in = a.f_in + (long long)b * 9 * plane;
   const float* __restrict__ g_in = a.g_in + (long long)b * 9 * plane;
+  const float* __restrict__ p0_in = a.phi0 + (long long)b * plane;
+  const float* __restrict__ h_in = a.hist_in + (long long)b * 5 * plane;
   float* __restrict__ f_out = a.f_out + (long long)b * 9 * plane;
   float* __restrict__ g_out = a.g_out + (long long)b * 9 * plane;
-  const float* __restrict__ phi0 = a.phi0 + (long long)b * plane;
-  const float* __restrict__ h_in = a.hist_in + (long long)b * 5 * plane;
   float* __restrict__ h_out = a.hist_out + (long long)b * 5 * plane;
+  auto src_plane = [&](int arr) -> const float* {
+    return arr < 9 ? f_in + arr * plane
+                   : (arr == 9 ? p0_in : (arr < 15 ? h_in + (arr - 10) * plane : g_in + (arr - 15) * plane));
+  };
 
-  // columns this thread stages: its own, plus halo columns for threads 0..3
-  const int x_own = x0 + t;
-  const int c_halo = t < 2 ? t : BX + t;             // f / phi0 slot of the halo column (t < 4)
-  const int x_halo = x0 - 2 + c_halo;
-  const int s_halo = t == 0 ? 0 : BX + 1;            // history slot of the halo column (t < 2)
-  const int xh_halo = x0 - 1 + s_halo;
-  const int px_own = wrap_or_mirror(x_own, nx, per_x);
-  const int px_halo = wrap_or_mirror(x_halo, nx, per_x);
-  const int pxh_halo = wrap_or_mirror(xh_halo, nx, per_x);
+  const bool vec16 = (nx & 3) == 0;
+  const int x = x0 + t;
 
-  // issue the asynchronous copies of logical row r into its slot
-  auto issue = [&](int r) {
+  // halo copy assignment: 40 copies of f / phi0 (two columns each side), 10 of the
+  // history (one column each side).  The right halo starts at xr, the first
+  // column after the CTA's last real column, so a ragged last CTA stages the
+  // wrapped / mirrored columns nx, nx+1 right after its real ones.
+  const int xr = min(x0 + BX, nx);
+  int h_arr = -1, h_col = 0, h_xl = 0;
+  if (t < 40) {
+    const int side = t / 10, arr = t % 10;
+    h_arr = arr;
+    h_col = side < 2 ? PAD - 2 + side : PAD + (xr - x0) + (side - 2);
+    h_xl = side < 2 ? x0 - 2 + side : xr + (side - 2);
+  } else if (t < 50) {
+    const int side = (t - 40) / 5, arr = 10 + (t - 40) % 5;
+    h_arr = arr;
+    h_col = side == 0 ? PAD - 1 : PAD + (xr - x0);
+    h_xl = side == 0 ? x0 - 1 : xr;
+  }
+  const bool h_active = h_arr >= 0 && h_xl <= nx + (h_arr < 10 ? 1 : 0);
+  const int h_px = wrap_or_mirror(h_xl, nx, per_x);
+  const float* __restrict__ h_src = h_arr >= 0 ? src_plane(h_arr) : f_in;
+
+  // issue the asynchronous copies of logical row r into slot sl
+  auto issue = [&](int r, int sl) {
     if (r <= ye + 1) {
-      RowSlot& sl = S.slot[(r - (ys - 2)) % R];
+      RowSlot& slot = S.slot[sl];
       const long long rowb = (long long)wrap_or_mirror(r, ny, per_y) * nx;
-      if (x_own <= nx + 1) {
-        const long long idx = rowb + px_own;
+      const bool own_row = r >= ys && r < ye;
+      if (vec16) {
+        // chunk m of this thread: array (t >> 5) + 4 m, columns x0 + 4 (t & 31) .. + 3
+        const int j = t & 31;
+        const int xc = x0 + 4 * j;
+        if (xc < nx) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) cp_async4(&sl.f[i][t + 2], f_in + (long long)i * plane + idx);
-        cp_async4(&sl.p0[t + 2], phi0 + idx);
-        if (x_own <= nx) {
-#pragma unroll
-          for (int q = 0; q < 5; ++q) cp_async4(&sl.h[q][t + 1], h_in + (long long)q * plane + idx);
+          for (int m = 0; m < 6; ++m) {
+            const int arr = (t >> 5) + 4 * m;
+            if (arr < 15 || own_row) cp_async16(&slot.rows[arr][PAD + 4 * j], src_plane(arr) + rowb + xc);
+          }
         }
-        if (x_own < nx && r >= ys && r < ye) {
+      } else if (x < nx) {
 #pragma unroll
-          for (int i = 0; i < 9; ++i) cp_async4(&sl.g[i][t], g_in + (long long)i * plane + idx);
-        }
+        for (int arr = 0; arr < NARR; ++arr)
+          if (arr < 15 || own_row) cp_async4(&slot.rows[arr][PAD + t], src_plane(arr) + rowb + x);
       }
-      if (t < 4 && x_halo <= nx + 1) {
-        const long long idx = rowb + px_halo;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) cp_async4(&sl.f[i][c_halo], f_in + (long long)i * plane + idx);
-        cp_async4(&sl.p0[c_halo], phi0 + idx);
-      }
-      if (t < 2 && xh_halo <= nx) {
-        const long long idx = rowb + pxh_halo;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) cp_async4(&sl.h[q][s_halo], h_in + (long long)q * plane + idx);
-      }
+      if (h_active) cp_async4(&slot.rows[h_arr][h_col], h_src + rowb + h_px);
     }
     cp_commit();   // empty groups keep the group count uniform
   };
 
-  // stage 1: phi1 = sum f and phi0 of row r into the rings (each thread reads
-  // only the columns it copied itself, so no barrier is needed before it)
-  auto stage1 = [&](int r) {
-    const RowSlot& sl = S.slot[(r - (ys - 2)) % R];
-    const int sp = ring(r, RP);
-    if (x_own <= nx + 1) {
-      float sum = sl.f[0][t + 2];
+  const InstanceConsts& k = S.k;
+  // rotating ring indices of rows y-1, y, y+1, y+2 (phi rings) and y-1, y, y+1 (mubar rings)
+  int pm = ring(ys - 1, RP), p0 = ring(ys, RP), pp = ring(ys + 1, RP), pq = ring(ys + 2, RP);
+  int mm = ring(ys - 1, RM), m0 = ring(ys, RM), mp = ring(ys + 1, RM);
+  // slot of rows ys-2 + q is q mod R
+
+  // stage 1: phi1 = sum f and phi0 of the row in slot sl into phi ring row sp.
+  // After the wait and a barrier every thread sees the whole slot.
+  auto stage1 = [&](int sl, int sp) {
+    const RowSlot& slot = S.slot[sl];
+    for (int c = t; c < BX + 4; c += BX) {
+      const int xl = x0 - 2 + c;
+      if (xl > nx + 1) continue;
+      const int col = c + PAD - 2;
+      float sum = slot.rows[0][col];
 #pragma unroll
-      for (int i = 1; i < 9; ++i) sum += sl.f[i][t + 2];
-      S.phi1[sp][t + 2] = sum;
-      S.phi0[sp][t + 2] = sl.p0[t + 2];
-    }
-    if (t < 4 && x_halo <= nx + 1) {
-      float sum = sl.f[0][c_halo];
-#pragma unroll
-      for (int i = 1; i < 9; ++i) sum += sl.f[i][c_halo];
-      S.phi1[sp][c_halo] = sum;
-      S.phi0[sp][c_halo] = sl.p0[c_halo];
+      for (int i = 1; i < 9; ++i) sum += slot.rows[i][col];
+      S.phi1[sp][c] = sum;
+      S.phi0[sp][c] = slot.rows[9][col];
     }
   };
 
-  const InstanceConsts& k = S.k;
-
-  // stage 2: mubar_1 of row r and the previous-step (u, S) into the rings
-  auto stage2 = [&](int r) {
-    const RowSlot& sl = S.slot[(r - (ys - 2)) % R];
-    const int sm = ring(r, RM);
-    const int p0 = ring(r, RP), pm = ring(r - 1, RP), pp = ring(r + 1, RP);
-    auto one = [&](int s) {
+  // stage 2: mubar_1 and the correction-force product of the row in slot sl;
+  // returns mu0 - mu2 and mu1 - mu2 of this thread's own column
+  auto stage2 = [&](int sl, int cm, int cp, int cq, int sm, float& d02, float& d12) {
+    const RowSlot& slot = S.slot[sl];
+    auto one = [&](int s, bool own) {
       const int xl = x0 - 1 + s;
       if (xl > nx) return;
       const int c = s + 1;
+      const P9 v1{S.phi1[cp][c], S.phi1[cp][c + 1], S.phi1[cq][c], S.phi1[cp][c - 1], S.phi1[cm][c],
+                  S.phi1[cq][c + 1], S.phi1[cq][c - 1], S.phi1[cm][c - 1], S.phi1[cm][c + 1]};
+      const P9 v0{S.phi0[cp][c], S.phi0[cp][c + 1], S.phi0[cq][c], S.phi0[cp][c - 1], S.phi0[cm][c],
+                  S.phi0[cq][c + 1], S.phi0[cq][c - 1], S.phi0[cm][c - 1], S.phi0[cm][c + 1]};
+      float mu0, mu1, mu2;
+      chem_pot(k, v0.c, v1.c, iso_lap(v0), iso_lap(v1), mu0, mu1, mu2);
+      S.mub[sm][s] = mubar1_of(k, mu0, mu1, mu2);
+      const int col = s + PAD - 1;
+      S.acorr[sm][s] = slot.rows[13][col] * slot.rows[12][col] - slot.rows[11][col] * slot.rows[14][col];
+      if (own) {
+        d02 = mu0 - mu2;
+        d12 = mu1 - mu2;
+      }
+    };
+    one(t + 1, true);              // this thread's own column
+    if (t == 0) one(0, false);     // halo columns
+    if (t == 1) one(BX + 1, false);
+  };
+
+  // prologue: copies of rows ys-2 .. ys+D, phi rows ys-2 .. ys+1, mubar rows ys-1, ys
+  for (int q = 0; q < R; ++q) issue(ys - 2 + q, q);
+  __syncthreads();   // constants visible
+  cp_wait<R - 1>();
+  __syncthreads();
+  stage1(0, ring(ys - 2, RP));
+  __syncthreads();   // slot 0 read by all threads before it is refilled
+  issue(ys + 1 + D, 0);
+  cp_wait<R - 1>();
+  __syncthreads();
+  stage1(1, pm);
+  cp_wait<R - 2>();
+  __syncthreads();
+  stage1(2, p0);
+  cp_wait<R - 3>();
+  __syncthreads();
+  stage1(3 % R, pp);
+  __syncthreads();
+  float d02 = 0.f, d12 = 0.f;       // mu differences of this thread's column, row y
+  {
+    float u02, u12;
+    stage2(1, ring(ys - 2, RP), pm, p0, mm, u02, u12);
+    stage2(2, pm, p0, pp, m0, d02, d12);
+  }
+  __syncthreads();
+
+  int sl_y = 2 % R;            // slot of row y
+  int sl_q = 4 % R;            // slot of row y+2
+  int sl_n = (4 + D) % R;      // slot that receives row y+2+D (it held row y-1)
+  for (int y = ys; y < ye; ++y) {
+    cp_wait<D - 1>();          // row y+2 has landed
+    __syncthreads();           // ... for every thread, and row y-1 is no longer read
+    issue(y + 2 + D, sl_n);
+    stage1(sl_q, pq);
+    __syncthreads();
+    float n02 = 0.f, n12 = 0.f;
+    stage2((sl_y + 1) % R, p0, pp, pq, mp, n02, n12);
+    __syncthreads();
+
+    // ---------------- stage 3: collide and stream row y ----------------
+    if (x < nx) {
+      const RowSlot& sl = S.slot[sl_y];
+      const int c = t + 2, s = t + 1, col = t + PAD;
+      const long long node = (long long)y * nx + x;
+      const float cs2 = k.cs2, cs4 = k.cs4;
+      float g[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[i] = sl.rows[15 + i][col];
+      const float php = sl.rows[10][col], uxp = sl.rows[11][col], uyp = sl.rows[12][col];
+      const float Sxp = sl.rows[13][col], Syp = sl.rows[14][col];
+
       const P9 v1{S.phi1[p0][c], S.phi1[p0][c + 1], S.phi1[pp][c], S.phi1[p0][c - 1], S.phi1[pm][c],
                   S.phi1[pp][c + 1], S.phi1[pp][c - 1], S.phi1[pm][c - 1], S.phi1[pm][c + 1]};
       const P9 v0{S.phi0[p0][c], S.phi0[p0][c + 1], S.phi0[pp][c], S.phi0[p0][c - 1], S.phi0[pm][c],
                   S.phi0[pp][c + 1], S.phi0[pp][c - 1], S.phi0[pm][c - 1], S.phi0[pm][c + 1]};
-      float mu0, mu1, mu2;
-      chem_pot(k, v0.c, v1.c, iso_lap(v0), iso_lap(v1), mu0, mu1, mu2);
-      S.mub[sm][s] = mubar1_of(k, mu0, mu1, mu2);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) S.h[sm][q][s] = sl.h[q + 1][s];
-    };
-    one(t + 1);
-    if (t == 0) one(0);
-    if (t == 1) one(BX + 1);
-  };
+      const P9 vm{S.mub[m0][s], S.mub[m0][s + 1], S.mub[mp][s], S.mub[m0][s - 1], S.mub[mm][s],
+                  S.mub[mp][s + 1], S.mub[mp][s - 1], S.mub[mm][s - 1], S.mub[mm][s + 1]};
+      const P9 va{0.f, S.acorr[m0][s + 1], S.acorr[mp][s], S.acorr[m0][s - 1], S.acorr[mm][s],
+                  S.acorr[mp][s + 1], S.acorr[mp][s - 1], S.acorr[mm][s - 1], S.acorr[mm][s + 1]};
 
-  // stage 3: collide and stream row y
-  auto stage3 = [&](int y) {
-    const int x = x0 + t;
-    if (x >= nx) return;
-    const RowSlot& sl = S.slot[(y - (ys - 2)) % R];
-    const int c = t + 2, s = t + 1;
-    const int p0 = ring(y, RP), pm = ring(y - 1, RP), pp = ring(y + 1, RP);
-    const int m0 = ring(y, RM), mm = ring(y - 1, RM), mp = ring(y + 1, RM);
-    const long long node = (long long)y * nx + x;
-    const float cs2 = k.cs2, cs4 = k.cs4;
-    float g[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = sl.g[i][t];
-    const float php = sl.h[0][s];
+      const float ph1 = v1.c, ph0 = v0.c, ph2 = 1.f - ph0 - ph1;
+      float g1x, g1y, g0x, g0y, gmx, gmy, dAx, dAy;
+      iso_grad(v1, g1x, g1y);
+      iso_grad(v0, g0x, g0y);
+      iso_grad(vm, gmx, gmy);
+      iso_grad(va, dAx, dAy);
+      const float mub = vm.c;
 
-    const P9 v1{S.phi1[p0][c], S.phi1[p0][c + 1], S.phi1[pp][c], S.phi1[p0][c - 1], S.phi1[pm][c],
-                S.phi1[pp][c + 1], S.phi1[pp][c - 1], S.phi1[pm][c - 1], S.phi1[pm][c + 1]};
-    const P9 v0{S.phi0[p0][c], S.phi0[p0][c + 1], S.phi0[pp][c], S.phi0[p0][c - 1], S.phi0[pm][c],
-                S.phi0[pp][c + 1], S.phi0[pp][c - 1], S.phi0[pm][c - 1], S.phi0[pm][c + 1]};
-    const P9 vm{S.mub[m0][s], S.mub[m0][s + 1], S.mub[mp][s], S.mub[m0][s - 1], S.mub[mm][s],
-                S.mub[mp][s + 1], S.mub[mp][s - 1], S.mub[mm][s - 1], S.mub[mm][s + 1]};
-    // A = S_x u_y - u_x S_y of the previous step at the eight neighbours
-    auto A = [&](int row, int col) {
-      return S.h[row][2][col] * S.h[row][1][col] - S.h[row][0][col] * S.h[row][3][col];
-    };
-    const P9 va{0.f, A(m0, s + 1), A(mp, s), A(m0, s - 1), A(mm, s), A(mp, s + 1), A(mp, s - 1),
-                A(mm, s - 1), A(mm, s + 1)};
-    const float ph1 = v1.c, ph0 = v0.c, ph2 = 1.f - ph0 - ph1;
-    float g1x, g1y, g0x, g0y, gmx, gmy, dAx, dAy;
-    iso_grad(v1, g1x, g1y);
-    iso_grad(v0, g0x, g0y);
-    iso_grad(vm, gmx, gmy);
-    iso_grad(va, dAx, dAy);
-    float mu0, mu1, mu2;
-    chem_pot(k, ph0, ph1, iso_lap(v0), iso_lap(v1), mu0, mu1, mu2);
-    const float mub = vm.c;
+      // degenerate mobility, mass flux S (frozen phi0), mixture properties
+      const float fdeg = ph1 * (1.f - ph1) * (1.f - ph0);
+      const float mob = k.M_cst + k.M_deg * fdeg;
+      const float sfac = (k.rho1 - k.rho2) * mob * k.inv_gam1;
+      const float Sx = sfac * gmx, Sy = sfac * gmy;
+      const float rho = k.rho0 * ph0 + k.rho1 * ph1 + k.rho2 * ph2;
+      const float grx = (k.rho0 - k.rho2) * g0x + (k.rho1 - k.rho2) * g1x;
+      const float gry = (k.rho0 - k.rho2) * g0y + (k.rho1 - k.rho2) * g1y;
+      const float muv = k.mu0 * ph0 + k.mu1 * ph1 + k.mu2 * ph2;
 
-    // degenerate mobility, mass flux S (frozen phi0), mixture properties
-    const float fdeg = ph1 * (1.f - ph1) * (1.f - ph0);
-    const float mob = k.M_cst + k.M_deg * fdeg;
-    const float sfac = (k.rho1 - k.rho2) * mob * k.inv_gam1;
-    const float Sx = sfac * gmx, Sy = sfac * gmy;
-    const float rho = k.rho0 * ph0 + k.rho1 * ph1 + k.rho2 * ph2;
-    const float grx = (k.rho0 - k.rho2) * g0x + (k.rho1 - k.rho2) * g1x;
-    const float gry = (k.rho0 - k.rho2) * g0y + (k.rho1 - k.rho2) * g1y;
-    const float muv = k.mu0 * ph0 + k.mu1 * ph1 + k.mu2 * ph2;
+      // F = F_s + F_b + F_c, F_s = (mu0 - mu2) grad phi0 + (mu1 - mu2) grad phi1
+      const float one_m0 = 1.f - ph0;
+      const float Fx = d02 * g0x + d12 * g1x + one_m0 * k.bx - 0.5f * dAy;
+      const float Fy = d02 * g0y + d12 * g1y + one_m0 * k.by + 0.5f * dAx;
 
-    // F = F_s + F_b + F_c
-    const float one_m0 = 1.f - ph0;
-    const float Fx = (mu0 - mu2) * g0x + (mu1 - mu2) * g1x + one_m0 * k.bx - 0.5f * dAy;
-    const float Fy = (mu0 - mu2) * g0y + (mu1 - mu2) * g1y + one_m0 * k.by + 0.5f * dAx;
+      // NS moments, velocity with the solid penalisation force
+      const Nat ng = natural(g);
+      const float inv_rho = __frcp_rn(rho);
+      const float usx = (ng.mx + 0.5f * Fx) * inv_rho;
+      const float usy = (ng.my + 0.5f * Fy) * inv_rho;
+      const float damp = 1.f - 0.5f * ph0;
+      const float ux = usx * damp, uy = usy * damp;
+      const float Ftx = Fx - ph0 * rho * usx, Fty = Fy - ph0 * rho * usy;
 
-    // NS moments, velocity with the solid penalisation force
-    const Nat ng = natural(g);
-    const float inv_rho = 1.f / rho;
-    const float usx = (ng.mx + 0.5f * Fx) * inv_rho;
-    const float usy = (ng.my + 0.5f * Fy) * inv_rho;
-    const float damp = 1.f - 0.5f * ph0;
-    const float ux = usx * damp, uy = usy * damp;
-    const float Ftx = Fx - ph0 * rho * usx, Fty = Fy - ph0 * rho * usy;
+      // local viscous rates (s0 = s4 = s2a)
+      const float om = fmaxf(one_m0, kOneMinusPhi0Floor);
+      const float ra = rho * om * k.a2a, rb = rho * om * k.a2b;
+      const float s2a = __fdividef(ra, 0.5f * ra + muv);
+      const float s2b = __fdividef(rb, 0.5f * rb + muv);
+      const float inv_s2a = 0.5f + __fdividef(muv, ra);
 
-    // local viscous rates (s0 = s4 = s2a)
-    const float om = fmaxf(one_m0, kOneMinusPhi0Floor);
-    const float ra = rho * om * k.a2a, rb = rho * om * k.a2b;
-    const float s2a = ra / (0.5f * ra + muv);
-    const float s2b = rb / (0.5f * rb + muv);
-    const float inv_s2a = 0.5f + muv / ra;
+      // pressure
+      const float udg = ux * grx + uy * gry;
+      const float q = (rho * ux - Sx) * ux + (rho * uy - Sy) * uy;
+      const float rhop = k.rho0 * ph0 + k.rho1 * php + k.rho2 * (1.f - ph0 - php);
+      const float qp = (rhop * uxp - Sxp) * uxp + (rhop * uyp - Syp) * uyp;
+      const float H = k.Kp * ((k.h0 - k.h2) * inv_s2a + k.h3);
+      const float sum_nz = ng.m0 - g[0];
+      const float p = k.pf * (sum_nz + (0.5f + H) * udg - k.wq * q + 0.5f * k.Kp * (q - qp));
 
-    // pressure
-    const float uxp = S.h[m0][0][s], uyp = S.h[m0][1][s], Sxp = S.h[m0][2][s], Syp = S.h[m0][3][s];
-    const float udg = ux * grx + uy * gry;
-    const float q = (rho * ux - Sx) * ux + (rho * uy - Sy) * uy;
-    const float rhop = k.rho0 * ph0 + k.rho1 * php + k.rho2 * (1.f - ph0 - php);
-    const float qp = (rhop * uxp - Sxp) * uxp + (rhop * uyp - Syp) * uyp;
-    const float H = k.Kp * ((k.h0 - k.h2) * inv_s2a + k.h3);
-    const float sum_nz = ng.m0 - g[0];
-    const float p = k.pf * (sum_nz + (0.5f + H) * udg - k.wq * q + 0.5f * k.Kp * (q - qp));
+      // destinations of the nine pushes; interior nodes use fixed offsets
+      const bool edge = x == 0 || x == nx - 1 || y == 0 || y == ny - 1;
+      auto store = [&](float* __restrict__ out, int i, int io, int cx, int cy, float v) {
+        if (!edge) out[(long long)i * plane + node + (long long)cy * nx + cx] = v;
+        else push(out, plane, i, io, cx, cy, x, y, nx, ny, per_x, per_y, v);
+      };
 
-    // ---- NS collision in Hermite space ----
-    {
-      const Her h = hermite(ng, cs2, cs4);
-      const float exx = p + rho * ux * ux - Sx * ux;
-      const float eyy = p + rho * uy * uy - Sy * uy;
-      const float exy = rho * ux * uy - 0.5f * (Sx * uy + ux * Sy);
-      const float e4 = -cs2 * p;
-      const float dSxx = Sx * ux - Sxp * uxp;
-      const float dSyy = Sy * uy - Syp * uyp;
-      const float dSxy = 0.5f * (Sx * uy + ux * Sy) - 0.5f * (Sxp * uyp + uxp * Syp);
-      const float iso = (1.f - 3.f * cs2) * udg;
-      const float Mxx = 2.f * ux * Fx - dSxx + 2.f * cs2 * ux * grx + iso;
-      const float Myy = 2.f * uy * Fy - dSyy + 2.f * cs2 * uy * gry + iso;
-      const float Mxy = ux * Fy + Fx * uy - dSxy + cs2 * (ux * gry + grx * uy);
-      Her o;
-      o.h0 = h.h0 - s2a * h.h0 + (1.f - 0.5f * s2a) * udg;
-      o.hx = h.hx - k.s1n * (h.hx - rho * ux) + (1.f - 0.5f * k.s1n) * Ftx;
-      o.hy = h.hy - k.s1n * (h.hy - rho * uy) + (1.f - 0.5f * k.s1n) * Fty;
-      o.hxx = h.hxx - s2a * (h.hxx - exx) + (1.f - 0.5f * s2a) * Mxx;
-      o.hyy = h.hyy - s2a * (h.hyy - eyy) + (1.f - 0.5f * s2a) * Myy;
-      o.hxy = h.hxy - s2b * (h.hxy - exy) + (1.f - 0.5f * s2b) * Mxy;
-      o.hxyy = h.hxyy * (1.f - k.s3n);
-      o.hxxy = h.hxxy * (1.f - k.s3n);
-      o.h4 = h.h4 - s2a * (h.h4 - e4);
-      float go[9];
-      from_natural(natural_of(o, cs2, cs4), go);
-      push(g_out, plane, 0, 0, 0, 0, x, y, nx, ny, per_x, per_y, go[0]);
-      push(g_out, plane, 1, 3, 1, 0, x, y, nx, ny, per_x, per_y, go[1]);
-      push(g_out, plane, 2, 4, 0, 1, x, y, nx, ny, per_x, per_y, go[2]);
-      push(g_out, plane, 3, 1, -1, 0, x, y, nx, ny, per_x, per_y, go[3]);
-      push(g_out, plane, 4, 2, 0, -1, x, y, nx, ny, per_x, per_y, go[4]);
-      push(g_out, plane, 5, 7, 1, 1, x, y, nx, ny, per_x, per_y, go[5]);
-      push(g_out, plane, 6, 8, -1, 1, x, y, nx, ny, per_x, per_y, go[6]);
-      push(g_out, plane, 7, 5, -1, -1, x, y, nx, ny, per_x, per_y, go[7]);
-      push(g_out, plane, 8, 6, 1, -1, x, y, nx, ny, per_x, per_y, go[8]);
-    }
-
-    // ---- CH collision ----
-    {
-      float fv[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) fv[i] = sl.f[i][c];
-      Nat nf = natural(fv);
-      nf.m0 = ph1;   // zeroth moment is the phase field itself
-      const float emb = k.eta * mub;
-      const float corr = k.corr_scale * (1.f - fdeg);
-      // R first moment: d_t(phi1 u) + cs2 * corr * eta grad mubar
-      const float Rx = (ph1 * ux - php * uxp) + cs2 * corr * k.eta * gmx;
-      const float Ry = (ph1 * uy - php * uyp) + cs2 * corr * k.eta * gmy;
-      float fo[9];
-      if (k.ch_fast != 0.f) {
-        // every moment but the first relaxes at rate 1, so f* = f^eq + w_i c_i . dj / cs2 with
-        // the post-collision first moment o = phi u + (1 - s1)(j - phi u) + (1 - s1/2) R
-        const float ox = ph1 * ux + (1.f - k.s1c) * (nf.mx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx;
-        const float oy = ph1 * uy + (1.f - k.s1c) * (nf.my - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry;
-        const float ic = 1.f / cs2;
-        const float ax = ox * ic, ay = oy * ic;
-        fo[1] = k.wa * (emb + ax);
-        fo[3] = k.wa * (emb - ax);
-        fo[2] = k.wa * (emb + ay);
-        fo[4] = k.wa * (emb - ay);
-        fo[5] = k.we * (emb + ax + ay);
-        fo[6] = k.we * (emb - ax + ay);
-        fo[7] = k.we * (emb - ax - ay);
-        fo[8] = k.we * (emb + ax - ay);
-        // rest population closes the zeroth moment exactly
-        fo[0] = ph1 - (((fo[1] + fo[3]) + (fo[2] + fo[4])) + ((fo[5] + fo[7]) + (fo[6] + fo[8])));
-      } else {
-        const Her h = hermite(nf, cs2, cs4);
-        const float exx = cs2 * (emb - ph1);
+      // ---- NS collision in Hermite space ----
+      {
+        const Her h = hermite(ng, cs2, cs4);
+        const float exx = p + rho * ux * ux - Sx * ux;
+        const float eyy = p + rho * uy * uy - Sy * uy;
+        const float exy = rho * ux * uy - 0.5f * (Sx * uy + ux * Sy);
+        const float e4 = -cs2 * p;
+        const float dSxx = Sx * ux - Sxp * uxp;
+        const float dSyy = Sy * uy - Syp * uyp;
+        const float dSxy = 0.5f * (Sx * uy + ux * Sy) - 0.5f * (Sxp * uyp + uxp * Syp);
+        const float iso = (1.f - 3.f * cs2) * udg;
+        const float Mxx = 2.f * ux * Fx - dSxx + 2.f * cs2 * ux * grx + iso;
+        const float Myy = 2.f * uy * Fy - dSyy + 2.f * cs2 * uy * gry + iso;
+        const float Mxy = ux * Fy + Fx * uy - dSxy + cs2 * (ux * gry + grx * uy);
         Her o;
-        o.h0 = ph1;
-        o.hx = h.hx - k.s1c * (h.hx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx;
-        o.hy = h.hy - k.s1c * (h.hy - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry;
-        o.hxx = h.hxx - k.s2ac * (h.hxx - exx);
-        o.hyy = h.hyy - k.s2ac * (h.hyy - exx);
-        o.hxy = h.hxy * (1.f - k.s2bc);
-        o.hxyy = h.hxyy * (1.f - k.s3c);
-        o.hxxy = h.hxxy * (1.f - k.s3c);
-        o.h4 = h.h4 - k.s4c * (h.h4 - cs4 * (ph1 - emb));
-        from_natural(natural_of(o, cs2, cs4), fo);
+        o.h0 = h.h0 - s2a * h.h0 + (1.f - 0.5f * s2a) * udg;
+        o.hx = h.hx - k.s1n * (h.hx - rho * ux) + (1.f - 0.5f * k.s1n) * Ftx;
+        o.hy = h.hy - k.s1n * (h.hy - rho * uy) + (1.f - 0.5f * k.s1n) * Fty;
+        o.hxx = h.hxx - s2a * (h.hxx - exx) + (1.f - 0.5f * s2a) * Mxx;
+        o.hyy = h.hyy - s2a * (h.hyy - eyy) + (1.f - 0.5f * s2a) * Myy;
+        o.hxy = h.hxy - s2b * (h.hxy - exy) + (1.f - 0.5f * s2b) * Mxy;
+        o.hxyy = h.hxyy * (1.f - k.s3n);
+        o.hxxy = h.hxxy * (1.f - k.s3n);
+        o.h4 = h.h4 - s2a * (h.h4 - e4);
+        float go[9];
+        from_natural(natural_of(o, cs2, cs4), go);
+        store(g_out, 0, 0, 0, 0, go[0]);
+        store(g_out, 1, 3, 1, 0, go[1]);
+        store(g_out, 2, 4, 0, 1, go[2]);
+        store(g_out, 3, 1, -1, 0, go[3]);
+        store(g_out, 4, 2, 0, -1, go[4]);
+        store(g_out, 5, 7, 1, 1, go[5]);
+        store(g_out, 6, 8, -1, 1, go[6]);
+        store(g_out, 7, 5, -1, -1, go[7]);
+        store(g_out, 8, 6, 1, -1, go[8]);
       }
-      push(f_out, plane, 0, 0, 0, 0, x, y, nx, ny, per_x, per_y, fo[0]);
-      push(f_out, plane, 1, 3, 1, 0, x, y, nx, ny, per_x, per_y, fo[1]);
-      push(f_out, plane, 2, 4, 0, 1, x, y, nx, ny, per_x, per_y, fo[2]);
-      push(f_out, plane, 3, 1, -1, 0, x, y, nx, ny, per_x, per_y, fo[3]);
-      push(f_out, plane, 4, 2, 0, -1, x, y, nx, ny, per_x, per_y, fo[4]);
-      push(f_out, plane, 5, 7, 1, 1, x, y, nx, ny, per_x, per_y, fo[5]);
-      push(f_out, plane, 6, 8, -1, 1, x, y, nx, ny, per_x, per_y, fo[6]);
-      push(f_out, plane, 7, 5, -1, -1, x, y, nx, ny, per_x, per_y, fo[7]);
-      push(f_out, plane, 8, 6, 1, -1, x, y, nx, ny, per_x, per_y, fo[8]);
-    }
 
-    // history of this step
-    h_out[node] = ph1;
-    h_out[plane + node] = ux;
-    h_out[2 * plane + node] = uy;
-    h_out[3 * plane + node] = Sx;
-    h_out[4 * plane + node] = Sy;
-    if (OBS) {
-      a.p_out[(long long)b * plane + node] = p;
-      const float u2 = ux * ux + uy * uy;
-      if (!(u2 <= 0.25f) || !(fabsf(ph1) < 1e30f)) atomicOr(a.flag, 1u);
-    }
-  };
+      // ---- CH collision ----
+      {
+        float fv[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fv[i] = sl.rows[i][col];
+        Nat nf = natural(fv);
+        nf.m0 = ph1;   // zeroth moment is the phase field itself
+        const float emb = k.eta * mub;
+        const float corr = k.corr_scale * (1.f - fdeg);
+        // R first moment: d_t(phi1 u) + cs2 * corr * eta grad mubar
+        const float Rx = (ph1 * ux - php * uxp) + cs2 * corr * k.eta * gmx;
+        const float Ry = (ph1 * uy - php * uyp) + cs2 * corr * k.eta * gmy;
+        float fo[9];
+        if (k.ch_fast != 0.f) {
+          // every moment but the first relaxes at rate 1, so f* = f^eq + w_i c_i . dj / cs2 with
+          // the post-collision first moment o = phi u + (1 - s1)(j - phi u) + (1 - s1/2) R
+          const float ox = ph1 * ux + (1.f - k.s1c) * (nf.mx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx;
+          const float oy = ph1 * uy + (1.f - k.s1c) * (nf.my - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry;
+          const float ic = __frcp_rn(cs2);
+          const float ax = ox * ic, ay = oy * ic;
+          fo[1] = k.wa * (emb + ax);
+          fo[3] = k.wa * (emb - ax);
+          fo[2] = k.wa * (emb + ay);
+          fo[4] = k.wa * (emb - ay);
+          fo[5] = k.we * (emb + ax + ay);
+          fo[6] = k.we * (emb - ax + ay);
+          fo[7] = k.we * (emb - ax - ay);
+          fo[8] = k.we * (emb + ax - ay);
+          // rest population closes the zeroth moment exactly
+          fo[0] = ph1 - (((fo[1] + fo[3]) + (fo[2] + fo[4])) + ((fo[5] + fo[7]) + (fo[6] + fo[8])));
+        } else {
+          const Her h = hermite(nf, cs2, cs4);
+          const float exx = cs2 * (emb - ph1);
+          Her o;
+          o.h0 = ph1;
+          o.hx = h.hx - k.s1c * (h.hx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx;
+          o.hy = h.hy - k.s1c * (h.hy - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry;
+          o.hxx = h.hxx - k.s2ac * (h.hxx - exx);
+          o.hyy = h.hyy - k.s2ac * (h.hyy - exx);
+          o.hxy = h.hxy * (1.f - k.s2bc);
+          o.hxyy = h.hxyy * (1.f - k.s3c);
+          o.hxxy = h.hxxy * (1.f - k.s3c);
+          o.h4 = h.h4 - k.s4c * (h.h4 - cs4 * (ph1 - emb));
+          from_natural(natural_of(o, cs2, cs4), fo);
+        }
+        store(f_out, 0, 0, 0, 0, fo[0]);
+        store(f_out, 1, 3, 1, 0, fo[1]);
+        store(f_out, 2, 4, 0, 1, fo[2]);
+        store(f_out, 3, 1, -1, 0, fo[3]);
+        store(f_out, 4, 2, 0, -1, fo[4]);
+        store(f_out, 5, 7, 1, 1, fo[5]);
+        store(f_out, 6, 8, -1, 1, fo[6]);
+        store(f_out, 7, 5, -1, -1, fo[7]);
+        store(f_out, 8, 6, 1, -1, fo[8]);
+      }
 
-  // prologue: copies of rows ys-2 .. ys+D, phi rows ys-2 .. ys+1, mubar / history rows ys-1, ys
-  for (int r = ys - 2; r <= ys + D; ++r) issue(r);
-  __syncthreads();   // constants visible
-  cp_wait<R - 1>();
-  stage1(ys - 2);
-  issue(ys + 1 + D);   // reuses the slot of row ys-2, read above by this thread only
-  cp_wait<R - 1>();
-  stage1(ys - 1);
-  cp_wait<R - 2>();
-  stage1(ys);
-  cp_wait<R - 3>();
-  stage1(ys + 1);
-  __syncthreads();
-  stage2(ys - 1);
-  stage2(ys);
-  __syncthreads();
-  for (int y = ys; y < ye; ++y) {
-    // the slot of row y+2+D last held row y-1, whose final reader was this
-    // thread's own stage 3 of the previous iteration
-    issue(y + 2 + D);
-    cp_wait<D>();
-    stage1(y + 2);
-    __syncthreads();
-    stage2(y + 1);
-    __syncthreads();
-    stage3(y);
+      // history of this step
+      h_out[node] = ph1;
+      h_out[plane + node] = ux;
+      h_out[2 * plane + node] = uy;
+      h_out[3 * plane + node] = Sx;
+      h_out[4 * plane + node] = Sy;
+      if (OBS) {
+        a.p_out[(long long)b * plane + node] = p;
+        const float u2 = ux * ux + uy * uy;
+        if (!(u2 <= 0.25f) || !(fabsf(ph1) < 1e30f)) atomicOr(a.flag, 1u);
+      }
+    }
+    d02 = n02;
+    d12 = n12;
+    // rotate the rings to row y+1
+    pm = p0; p0 = pp; pp = pq; pq = inc_mod(pq, RP);
+    mm = m0; m0 = mp; mp = inc_mod(mp, RM);
+    sl_y = inc_mod(sl_y, R);
+    sl_q = inc_mod(sl_q, R);
+    sl_n = inc_mod(sl_n, R);
   }
   cp_wait<0>();
 }
