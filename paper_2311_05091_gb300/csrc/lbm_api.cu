@@ -392,6 +392,8 @@ int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_m
   for (int a = 0; a < (is3d ? 3 : 2); ++a)
     if (!per[a] && dims[a] < 2) return set_err(nullptr, LBM_EINVAL, "a wall axis needs at least 2 nodes");
   const long long nodes = (long long)nx * ny * nz;
+  // kernels index the planes of one instance with 32-bit offsets
+  if (nodes * (is3d ? 19 : 9) >= (1LL << 31)) return set_err(nullptr, LBM_EINVAL, "lattice too large for one instance");
   if (nodes > (1LL << 40) / nbatch) return set_err(nullptr, LBM_EINVAL, "lattice too large");
 
   lbm_ctx* c = new (std::nothrow) lbm_ctx();

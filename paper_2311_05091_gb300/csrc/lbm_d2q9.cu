@@ -290,14 +290,16 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
   // column after the CTA's last real column, so a ragged last CTA stages the
   // wrapped / mirrored columns nx, nx+1 right after its real ones.
   const int xr = min(x0 + BX, nx);
+  // the 50 halo copies are spread over the four warps (copy k on thread 32 (k % 4) + k / 4)
+  const int hk = (t & 31) * 4 + (t >> 5);
   int h_arr = -1, h_col = 0, h_xl = 0;
-  if (t < 40) {
-    const int side = t / 10, arr = t % 10;
+  if (hk < 40) {
+    const int side = hk / 10, arr = hk % 10;
     h_arr = arr;
     h_col = side < 2 ? PAD - 2 + side : PAD + (xr - x0) + (side - 2);
     h_xl = side < 2 ? x0 - 2 + side : xr + (side - 2);
-  } else if (t < 50) {
-    const int side = (t - 40) / 5, arr = 10 + (t - 40) % 5;
+  } else if (hk < 50) {
+    const int side = (hk - 40) / 5, arr = 10 + (hk - 40) % 5;
     h_arr = arr;
     h_col = side == 0 ? PAD - 1 : PAD + (xr - x0);
     h_xl = side == 0 ? x0 - 1 : xr;
@@ -343,30 +345,36 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
   // After the wait and a barrier every thread sees the whole slot.
   auto stage1 = [&](int sl, int sp) {
     const RowSlot& slot = S.slot[sl];
-    for (int c = t; c < BX + 4; c += BX) {
+    auto one = [&](int c) {
       const int xl = x0 - 2 + c;
-      if (xl > nx + 1) continue;
+      if (xl > nx + 1) return;
       const int col = c + PAD - 2;
       float sum = slot.rows[0][col];
 #pragma unroll
       for (int i = 1; i < 9; ++i) sum += slot.rows[i][col];
       S.phi1[sp][c] = sum;
       S.phi0[sp][c] = slot.rows[9][col];
-    }
+    };
+    one(t);
+    if ((t & 31) == 0) one(BX + (t >> 5));   // the four extra columns, one per warp
   };
 
   // stage 2: mubar_1 and the correction-force product of the row in slot sl;
   // returns mu0 - mu2 and mu1 - mu2 of this thread's own column
   auto stage2 = [&](int sl, int cm, int cp, int cq, int sm, float& d02, float& d12) {
     const RowSlot& slot = S.slot[sl];
+    const float* A1m = S.phi1[cm];
+    const float* A1p = S.phi1[cp];
+    const float* A1q = S.phi1[cq];
+    const float* A0m = S.phi0[cm];
+    const float* A0p = S.phi0[cp];
+    const float* A0q = S.phi0[cq];
     auto one = [&](int s, bool own) {
       const int xl = x0 - 1 + s;
       if (xl > nx) return;
       const int c = s + 1;
-      const P9 v1{S.phi1[cp][c], S.phi1[cp][c + 1], S.phi1[cq][c], S.phi1[cp][c - 1], S.phi1[cm][c],
-                  S.phi1[cq][c + 1], S.phi1[cq][c - 1], S.phi1[cm][c - 1], S.phi1[cm][c + 1]};
-      const P9 v0{S.phi0[cp][c], S.phi0[cp][c + 1], S.phi0[cq][c], S.phi0[cp][c - 1], S.phi0[cm][c],
-                  S.phi0[cq][c + 1], S.phi0[cq][c - 1], S.phi0[cm][c - 1], S.phi0[cm][c + 1]};
+      const P9 v1{A1p[c], A1p[c + 1], A1q[c], A1p[c - 1], A1m[c], A1q[c + 1], A1q[c - 1], A1m[c - 1], A1m[c + 1]};
+      const P9 v0{A0p[c], A0p[c + 1], A0q[c], A0p[c - 1], A0m[c], A0q[c + 1], A0q[c - 1], A0m[c - 1], A0m[c + 1]};
       float mu0, mu1, mu2;
       chem_pot(k, v0.c, v1.c, iso_lap(v0), iso_lap(v1), mu0, mu1, mu2);
       S.mub[sm][s] = mubar1_of(k, mu0, mu1, mu2);
@@ -377,9 +385,9 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
         d12 = mu1 - mu2;
       }
     };
-    one(t + 1, true);              // this thread's own column
-    if (t == 0) one(0, false);     // halo columns
-    if (t == 1) one(BX + 1, false);
+    one(t + 1, true);                 // this thread's own column
+    if (t == 64) one(0, false);       // halo columns, on warps 2 and 3
+    if (t == 96) one(BX + 1, false);
   };
 
   // prologue: copies of rows ys-2 .. ys+D, phi rows ys-2 .. ys+1, mubar rows ys-1, ys
@@ -425,7 +433,8 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
     if (x < nx) {
       const RowSlot& sl = S.slot[sl_y];
       const int c = t + 2, s = t + 1, col = t + PAD;
-      const long long node = (long long)y * nx + x;
+      const int node = y * nx + x;         // instance-relative, < 2^31 (checked at creation)
+      const int pl = (int)plane;
       const float cs2 = k.cs2, cs4 = k.cs4;
       float g[9];
 #pragma unroll
@@ -433,14 +442,22 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
       const float php = sl.rows[10][col], uxp = sl.rows[11][col], uyp = sl.rows[12][col];
       const float Sxp = sl.rows[13][col], Syp = sl.rows[14][col];
 
-      const P9 v1{S.phi1[p0][c], S.phi1[p0][c + 1], S.phi1[pp][c], S.phi1[p0][c - 1], S.phi1[pm][c],
-                  S.phi1[pp][c + 1], S.phi1[pp][c - 1], S.phi1[pm][c - 1], S.phi1[pm][c + 1]};
-      const P9 v0{S.phi0[p0][c], S.phi0[p0][c + 1], S.phi0[pp][c], S.phi0[p0][c - 1], S.phi0[pm][c],
-                  S.phi0[pp][c + 1], S.phi0[pp][c - 1], S.phi0[pm][c - 1], S.phi0[pm][c + 1]};
-      const P9 vm{S.mub[m0][s], S.mub[m0][s + 1], S.mub[mp][s], S.mub[m0][s - 1], S.mub[mm][s],
-                  S.mub[mp][s + 1], S.mub[mp][s - 1], S.mub[mm][s - 1], S.mub[mm][s + 1]};
-      const P9 va{0.f, S.acorr[m0][s + 1], S.acorr[mp][s], S.acorr[m0][s - 1], S.acorr[mm][s],
-                  S.acorr[mp][s + 1], S.acorr[mp][s - 1], S.acorr[mm][s - 1], S.acorr[mm][s + 1]};
+      const float* B1m = S.phi1[pm] + c;
+      const float* B10 = S.phi1[p0] + c;
+      const float* B1p = S.phi1[pp] + c;
+      const float* B0m = S.phi0[pm] + c;
+      const float* B00 = S.phi0[p0] + c;
+      const float* B0p = S.phi0[pp] + c;
+      const float* Mm = S.mub[mm] + s;
+      const float* M0 = S.mub[m0] + s;
+      const float* Mp = S.mub[mp] + s;
+      const float* Am = S.acorr[mm] + s;
+      const float* A0 = S.acorr[m0] + s;
+      const float* Ap = S.acorr[mp] + s;
+      const P9 v1{B10[0], B10[1], B1p[0], B10[-1], B1m[0], B1p[1], B1p[-1], B1m[-1], B1m[1]};
+      const P9 v0{B00[0], B00[1], B0p[0], B00[-1], B0m[0], B0p[1], B0p[-1], B0m[-1], B0m[1]};
+      const P9 vm{M0[0], M0[1], Mp[0], M0[-1], Mm[0], Mp[1], Mp[-1], Mm[-1], Mm[1]};
+      const P9 va{0.f, A0[1], Ap[0], A0[-1], Am[0], Ap[1], Ap[-1], Am[-1], Am[1]};
 
       const float ph1 = v1.c, ph0 = v0.c, ph2 = 1.f - ph0 - ph1;
       float g1x, g1y, g0x, g0y, gmx, gmy, dAx, dAy;
@@ -493,7 +510,7 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
       // destinations of the nine pushes; interior nodes use fixed offsets
       const bool edge = x == 0 || x == nx - 1 || y == 0 || y == ny - 1;
       auto store = [&](float* __restrict__ out, int i, int io, int cx, int cy, float v) {
-        if (!edge) out[(long long)i * plane + node + (long long)cy * nx + cx] = v;
+        if (!edge) out[i * pl + node + cy * nx + cx] = v;
         else push(out, plane, i, io, cx, cy, x, y, nx, ny, per_x, per_y, v);
       };
 
@@ -592,10 +609,10 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
 
       // history of this step
       h_out[node] = ph1;
-      h_out[plane + node] = ux;
-      h_out[2 * plane + node] = uy;
-      h_out[3 * plane + node] = Sx;
-      h_out[4 * plane + node] = Sy;
+      h_out[pl + node] = ux;
+      h_out[2 * pl + node] = uy;
+      h_out[3 * pl + node] = Sx;
+      h_out[4 * pl + node] = Sy;
       if (OBS) {
         a.p_out[(long long)b * plane + node] = p;
         const float u2 = ux * ux + uy * uy;
