@@ -140,10 +140,10 @@ void lbm_destroy(lbm_ctx* ctx);
  * ownership of the stream and must keep it alive while the context uses it. */
 int lbm_set_stream(lbm_ctx* ctx, void* stream);
 
-/* Launch tuning; results do not depend on it.  strip >= 1: rows (D2Q9) or
- * planes (D3Q19) swept by one CTA of the step kernel.  depth in 1..3: rows
- * of asynchronous global-to-shared copies each CTA keeps in flight (0 keeps
- * the current value). */
+/* Launch tuning; results do not depend on it (bitwise).  strip >= 1: rows
+ * (D2Q9) or z planes (D3Q19) swept by one CTA of the step kernel.  depth in
+ * 1..3: rows of asynchronous global-to-shared copies each D2Q9 CTA keeps in
+ * flight (0 keeps the current value; the D3Q19 kernel ignores it). */
 int lbm_set_launch(lbm_ctx* ctx, int strip, int depth);
 
 /* Kernel timing.  While enabled, every step-kernel launch is bracketed by a
@@ -164,7 +164,8 @@ int lbm_set_solid_device(lbm_ctx* ctx, const float* phi0_dev);
 int lbm_set_phase(lbm_ctx* ctx, const float* phi1_host);
 int lbm_set_phase_device(lbm_ctx* ctx, const float* phi1_dev);
 
-/* Enqueue n >= 0 coupled time steps (one fused kernel per step for D2Q9;
+/* Enqueue n >= 0 coupled time steps (D2Q9: one fused kernel per step;
+ * D3Q19: a moment pass, phi1 = sum f and j = sum c f, then one fused kernel;
  * replayed from a captured CUDA graph where the stream allows).  Returns once
  * the work is enqueued.  The last step also writes the pressure field and
  * checks for divergence. */

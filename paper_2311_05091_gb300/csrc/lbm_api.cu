@@ -52,6 +52,7 @@ struct lbm_ctx {
   float* hist[2] = {nullptr, nullptr};
   float* phi0 = nullptr;
   float* p = nullptr;
+  float* mom = nullptr;        // D3Q19 moment-pass scratch
   unsigned int* dflag = nullptr;
   double* dpart = nullptr;
   double* dobs = nullptr;
@@ -194,8 +195,9 @@ int default_strip(const lbm_ctx* c) {
   // 16 rows per CTA measured best for the D2Q9 kernel on GB300 (sweep over
   // 16..64 rows on the 1024^2 x 5 workload: shorter strips balance the
   // 152 SMs better than the two-row prologue of each strip costs)
+  // 32 planes per CTA for the D3Q19 sweep: 2048 CTAs on 256^3
   const long long rows = c->lattice == LBM_D2Q9 ? c->ny : c->nz;
-  long long strip = 16;
+  long long strip = c->lattice == LBM_D2Q9 ? 16 : 32;
   if (strip > rows) strip = rows;
   return (int)std::max(1LL, strip);
 }
@@ -210,6 +212,7 @@ StepArgs step_args(lbm_ctx* c, int from) {
   a.hist_in = c->hist[from];
   a.hist_out = c->hist[1 - from];
   a.p_out = c->p;
+  a.mom = c->mom;
   a.consts = c->dconsts;
   a.flag = c->dflag;
   a.nx = c->nx;
@@ -279,6 +282,7 @@ void free_all(lbm_ctx* c) {
   }
   cudaFree(c->phi0);
   cudaFree(c->p);
+  cudaFree(c->mom);
   cudaFree(c->dflag);
   cudaFree(c->dpart);
   cudaFree(c->dobs);
@@ -430,6 +434,7 @@ int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_m
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->phi0, fld);
   if (e == cudaSuccess) e = cudaMalloc(&c->p, fld);
+  if (e == cudaSuccess && is3d) e = cudaMalloc(&c->mom, 3 * fld);
   if (e == cudaSuccess) e = cudaMalloc(&c->dflag, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&c->dpart, sizeof(double) * lbm::obs_partials_len(nodes));
   if (e == cudaSuccess) e = cudaMalloc(&c->dobs, sizeof(double) * 8);

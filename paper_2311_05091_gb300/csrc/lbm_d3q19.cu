@@ -1,13 +1,724 @@
-// D3Q19 kernels of the coupled CH + NS step.
+// D3Q19 kernels of the coupled CH + NS step (Zhan, Chai, Shi, arXiv 2311.05091).
+//
+// Two launches per time step:
+//
+//   d3q19_moments  phi1 = sum_i f_i and the first moment j = sum_i c_i f_i of
+//                  the push-streamed CH populations (Sec. 3).  phi1 goes to
+//                  plane 0 of this step's history, j to a 3-plane scratch.
+//   d3q19_step     the fused rest of the step.  A CTA owns a TX x TY column
+//                  tile and sweeps a strip of z planes with shared-memory
+//                  rings: phi0 / phi1 with two halo columns (four planes),
+//                  mubar_1 and the antisymmetric products S_a u_b - u_a S_b of
+//                  the previous step with one halo column (three planes).
+//                  Per node it evaluates the stencils, forces, velocity and
+//                  pressure, both Hermite-moment collisions in closed form and
+//                  the push-streaming store with half-way bounce-back.
+//
+// Why the split: the CH populations enter the collision only through phi1,
+// j and, for the free rates of the Hermite basis, the higher moments.  With
+// every free CH rate equal to 1 (the default), f* = f^eq + R/2 - (s1 - 1) P1 v
+// needs phi1 and j alone, so the fused kernel never reads f and the moment
+// pass moves the f read off the stencil path.  With other free rates the
+// fused kernel reads f once more.
+//
+// Collision in closed form.  Lambda = T^-1 K T with T the w-orthogonal
+// Hermite basis (Sec. 4 intro, Appendix A) acts on each group of equal rate
+// through the w-orthogonal projector P_g onto that group's span, which does
+// not depend on the basis chosen inside the group:
+//     Lambda v = s4 v + sum_{g != 4} (s_g - s4) P_g v.
+// The fourth-order group therefore never has to be built.  The third-order
+// span is spanned, per axis a with the other two axes (b, c) in cyclic
+// order, by the w-orthogonal pair A_a = c_a (c_b^2 + c_c^2) - 2 cs2 c_a and
+// B_a = c_a (c_b^2 - c_c^2), of w-norms 2 cs2^2 (1 - 2 cs2) and 2 cs2^2.
+//
+// HBM traffic per node and step (algorithmic): f and g read and written
+// (304 B), phi0 read (4 B), history phi1 / u / S read and written (56 B):
+// 364 B.  The split adds the j scratch (12 B written, 12 B read) and the
+// second read of phi1 (4 B).
+//
+// The NS rest population is stored minus the constant rho_0 of lambda_0.
+#include <algorithm>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
+namespace {
 
-cudaError_t launch_d3q19_init(const float*, const float*, float*, float*, float*, const InstanceConsts*, int,
-                              int, int, int, int, int, int, cudaStream_t) {
-  return cudaErrorNotSupported;
+constexpr int Q = 19;
+constexpr int NH = 7;                        // history planes: phi1, u (3), S (3)
+constexpr int TX = 32, TY = 8, NT = TX * TY; // owned column tile, one thread per column
+constexpr int HX2 = TX + 4, HY2 = TY + 4, N2 = HX2 * HY2;   // tile with two halo columns
+constexpr int HX1 = TX + 2, HY1 = TY + 2, N1 = HX1 * HY1;   // tile with one halo column
+constexpr int RP = 4;                        // phi ring planes: z-1 .. z+2
+constexpr int RM = 3;                        // mubar / product ring planes: z-1 .. z+1
+constexpr float kOneMinusPhi0Floor = 5.9604644775390625e-8f;  // 2^-24
+
+// direction table (include/lbm.h): 0 rest, 1-6 axes, 7-18 edges
+__host__ __device__ constexpr int CX(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int CY(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int CZ(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int OPP(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr int CA(int i, int a) { return a == 0 ? CX(i) : (a == 1 ? CY(i) : CZ(i)); }
+
+__device__ __forceinline__ int wrap_or_mirror(int i, int n, int per) {
+  if (per) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  if (i < 0) return -1 - i;          // mirror ghost across the half-way wall
+  if (i >= n) return 2 * n - 1 - i;
+  return i;
 }
 
-cudaError_t launch_d3q19_step(const StepArgs&, int, bool, cudaStream_t) { return cudaErrorNotSupported; }
+__device__ __forceinline__ int ring(int r, int n) { return ((r % n) + n) % n; }
+
+// value of a ring-stored field at x + c_d: planes pm (z-1), p0 (z), pp (z+1), row stride sw
+__device__ __forceinline__ float nb(const float* pm, const float* p0, const float* pp, int i, int sw, int d) {
+  const float* pl = CZ(d) > 0 ? pp : (CZ(d) < 0 ? pm : p0);
+  return pl[i + CY(d) * sw + CX(d)];
+}
+
+// Isotropic central derivative along axis A with the D3Q19 weights of d0 = 1/3
+// (1/18 axis, 1/36 edge): d_A v = sum_i w_i c_iA v(x + c_i) / (1/3).
+template <int A>
+__device__ __forceinline__ float dgrad(const float* pm, const float* p0, const float* pp, int i, int sw) {
+  float axis = 0.f, edge = 0.f;
+#pragma unroll
+  for (int d = 1; d < Q; ++d) {
+    const int c = CA(d, A);
+    if (c == 0) continue;
+    const float v = nb(pm, p0, pp, i, sw, d);
+    if (d < 7) axis += c > 0 ? v : -v;
+    else edge += c > 0 ? v : -v;
+  }
+  return axis * (1.f / 6.f) + edge * (1.f / 12.f);
+}
+
+// Isotropic Laplacian: sum_i 2 w_i (v(x + c_i) - v(x)) / (1/3).
+__device__ __forceinline__ float lap3(const float* pm, const float* p0, const float* pp, int i, int sw) {
+  const float c = p0[i];
+  float axis = 0.f, edge = 0.f;
+#pragma unroll
+  for (int d = 1; d < Q; ++d) {
+    const float v = nb(pm, p0, pp, i, sw, d) - c;
+    if (d < 7) axis += v;
+    else edge += v;
+  }
+  return axis * (1.f / 3.f) + edge * (1.f / 6.f);
+}
+
+// mu_p = gamma_p psi_p, psi_p = (12/D) phi_p (1 - phi_p)(1 - 2 phi_p) - (3D/4) lap phi_p (Sec. 2.1).
+__device__ __forceinline__ void chem_pot(const InstanceConsts& k, float ph0, float ph1, float lap0,
+                                         float lap1, float& mu0, float& mu1, float& mu2) {
+  const float ph2 = 1.f - ph0 - ph1;
+  const float lap2 = -lap0 - lap1;
+  const float psi0 = k.c12_W * ph0 * (1.f - ph0) * (1.f - 2.f * ph0) - k.c34_W * lap0;
+  const float psi1 = k.c12_W * ph1 * (1.f - ph1) * (1.f - 2.f * ph1) - k.c34_W * lap1;
+  const float psi2 = k.c12_W * ph2 * (1.f - ph2) * (1.f - 2.f * ph2) - k.c34_W * lap2;
+  mu0 = k.gam0 * psi0;
+  mu1 = k.gam1 * psi1;
+  mu2 = k.gam2 * psi2;
+}
+
+// mubar_1 = gamma_T/3 [ (mu1 - mu0)/gamma_0 + (mu1 - mu2)/gamma_2 ] (Eq. CHmodel).
+__device__ __forceinline__ float mubar1_of(const InstanceConsts& k, float mu0, float mu1, float mu2) {
+  return k.gT3 * ((mu1 - mu0) * k.inv_gam0 + (mu1 - mu2) * k.inv_gam2);
+}
+
+__device__ __forceinline__ float weight(const InstanceConsts& k, int i) {
+  return i == 0 ? k.w0 : (i < 7 ? k.wa : k.we);
+}
+
+// ---------------------------------------------------------------------------
+// initial state: f = f^eq(phi1, mubar_1, u = 0), g = g^eq(p = 0, u = 0) - rho_0 e_0 = 0,
+// history = (phi1, 0, ..., 0).  phi1 arrives staged in plane 0 of a spare history buffer.
+// ---------------------------------------------------------------------------
+__global__ void d3q19_init(const float* __restrict__ phi0_all, const float* __restrict__ phi1_all,
+                           float* __restrict__ f_all, float* __restrict__ g_all, float* __restrict__ hist_all,
+                           const InstanceConsts* __restrict__ consts, int nx, int ny, int nz, int per_x,
+                           int per_y, int per_z, int nbatch) {
+  const long long nodes = (long long)nx * ny * nz;
+  const long long total = nodes * nbatch;
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < total;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(gi / nodes);
+    const long long node = gi - (long long)b * nodes;
+    const int x = (int)(node % nx), y = (int)((node / nx) % ny), z = (int)(node / ((long long)nx * ny));
+    const InstanceConsts& k = consts[b];
+    const float* phi0 = phi0_all + (long long)b * nodes;
+    const float* phi1 = phi1_all + (long long)b * NH * nodes;
+    auto at = [&](const float* a, int d) {
+      const int xx = wrap_or_mirror(x + CX(d), nx, per_x);
+      const int yy = wrap_or_mirror(y + CY(d), ny, per_y);
+      const int zz = wrap_or_mirror(z + CZ(d), nz, per_z);
+      return a[((long long)zz * ny + yy) * nx + xx];
+    };
+    const float c0 = phi0[node], c1 = phi1[node];
+    float a0 = 0.f, e0 = 0.f, a1 = 0.f, e1 = 0.f;
+#pragma unroll
+    for (int d = 1; d < Q; ++d) {
+      const float v0 = at(phi0, d) - c0, v1 = at(phi1, d) - c1;
+      if (d < 7) {
+        a0 += v0;
+        a1 += v1;
+      } else {
+        e0 += v0;
+        e1 += v1;
+      }
+    }
+    const float lap0 = a0 * (1.f / 3.f) + e0 * (1.f / 6.f);
+    const float lap1 = a1 * (1.f / 3.f) + e1 * (1.f / 6.f);
+    float mu0, mu1, mu2;
+    chem_pot(k, c0, c1, lap0, lap1, mu0, mu1, mu2);
+    const float emb = k.eta * mubar1_of(k, mu0, mu1, mu2);
+    float* f = f_all + (long long)b * Q * nodes;
+    float* g = g_all + (long long)b * Q * nodes;
+    float* h = hist_all + (long long)b * NH * nodes;
+    f[node] = c1 + (k.w0 - 1.f) * emb;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) f[(long long)i * nodes + node] = (i < 7 ? k.wa : k.we) * emb;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[(long long)i * nodes + node] = 0.f;
+    h[node] = c1;
+#pragma unroll
+    for (int q = 1; q < NH; ++q) h[(long long)q * nodes + node] = 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// moment pass: phi1 = sum_i f_i -> history plane 0, j = sum_i c_i f_i -> scratch
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void moments19(const float (&v)[Q], float& s, float& jx, float& jy, float& jz) {
+  s = v[0];
+  jx = 0.f;
+  jy = 0.f;
+  jz = 0.f;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    s += v[i];
+    if (CX(i)) jx += CX(i) > 0 ? v[i] : -v[i];
+    if (CY(i)) jy += CY(i) > 0 ? v[i] : -v[i];
+    if (CZ(i)) jz += CZ(i) > 0 ? v[i] : -v[i];
+  }
+}
+
+__global__ void __launch_bounds__(256) d3q19_moments(const float* __restrict__ f_all, float* __restrict__ hist_all,
+                                                     float* __restrict__ mom_all, int nodes, int vec4) {
+  const int b = blockIdx.y;
+  const float* f = f_all + (long long)b * Q * nodes;
+  float* h = hist_all + (long long)b * NH * nodes;
+  float* m = mom_all + (long long)b * 3 * nodes;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec4) {
+    const int n4 = nodes >> 2;
+    if (t >= n4) return;
+    float4 v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = __ldcs(reinterpret_cast<const float4*>(f + (long long)i * nodes) + t);
+    float4 s, jx, jy, jz;
+    {
+      float a[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a[i] = v[i].x;
+      moments19(a, s.x, jx.x, jy.x, jz.x);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a[i] = v[i].y;
+      moments19(a, s.y, jx.y, jy.y, jz.y);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a[i] = v[i].z;
+      moments19(a, s.z, jx.z, jy.z, jz.z);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a[i] = v[i].w;
+      moments19(a, s.w, jx.w, jy.w, jz.w);
+    }
+    reinterpret_cast<float4*>(h)[t] = s;
+    reinterpret_cast<float4*>(m)[t] = jx;
+    reinterpret_cast<float4*>(m + nodes)[t] = jy;
+    reinterpret_cast<float4*>(m + 2 * (long long)nodes)[t] = jz;
+  } else {
+    if (t >= nodes) return;
+    float a[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) a[i] = __ldcs(f + (long long)i * nodes + t);
+    float s, jx, jy, jz;
+    moments19(a, s, jx, jy, jz);
+    h[t] = s;
+    m[t] = jx;
+    m[nodes + t] = jy;
+    m[2 * (long long)nodes + t] = jz;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused step
+// ---------------------------------------------------------------------------
+struct StepSmem3 {
+  float phi1[RP][N2];
+  float phi0[RP][N2];
+  float mub[RM][N1];
+  float acor[RM][3][N1];   // S_x u_y - u_x S_y, S_x u_z - u_x S_z, S_y u_z - u_y S_z (previous step)
+  InstanceConsts k;
+};
+
+template <bool OBS>
+__global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem3& S = *reinterpret_cast<StepSmem3*>(smem_raw);
+
+  const int t = threadIdx.x;
+  const int tx = t % TX, ty = t / TX;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int per_x = a.per_x, per_y = a.per_y, per_z = a.per_z;
+  const int ntx = (nx + TX - 1) / TX;
+  const int x0 = (blockIdx.x % ntx) * TX;
+  const int zs = (blockIdx.x / ntx) * a.strip;
+  const int ze = min(zs + a.strip, nz);
+  const int y0 = blockIdx.y * TY;
+  const int b = blockIdx.z;
+  const int nodes = (int)a.nodes;   // < 2^31 / 19 (checked at creation)
+  const int plane = nx * ny;
+  static_assert(sizeof(InstanceConsts) / 4 <= NT, "constants copied one word per thread");
+  if (t < (int)(sizeof(InstanceConsts) / 4))
+    reinterpret_cast<float*>(&S.k)[t] = reinterpret_cast<const float*>(a.consts + b)[t];
+
+  const float* __restrict__ f_in = a.f_in + (long long)b * Q * nodes;
+  const float* __restrict__ g_in = a.g_in + (long long)b * Q * nodes;
+  const float* __restrict__ p0_in = a.phi0 + (long long)b * nodes;
+  const float* __restrict__ h_in = a.hist_in + (long long)b * NH * nodes;
+  float* __restrict__ f_out = a.f_out + (long long)b * Q * nodes;
+  float* __restrict__ g_out = a.g_out + (long long)b * Q * nodes;
+  float* __restrict__ h_out = a.hist_out + (long long)b * NH * nodes;
+  const float* __restrict__ phi1_now = h_out;   // written by the moment pass of this step
+  const float* __restrict__ j_in = a.mom + (long long)b * 3 * nodes;
+
+  // phi0 / phi1 of logical plane zl on the two-halo tile into ring slot sl
+  auto load_phi = [&](int zl, int sl) {
+    const int zo = wrap_or_mirror(zl, nz, per_z) * plane;
+    for (int p = t; p < N2; p += NT) {
+      const int px = p % HX2, py = p / HX2;
+      const int xl = x0 - 2 + px, yl = y0 - 2 + py;
+      if (xl > nx + 1 || yl > ny + 1) continue;   // beyond what the last real column needs
+      const int o = zo + wrap_or_mirror(yl, ny, per_y) * nx + wrap_or_mirror(xl, nx, per_x);
+      S.phi1[sl][p] = phi1_now[o];
+      S.phi0[sl][p] = p0_in[o];
+    }
+  };
+  // antisymmetric products of the previous step's S and u on the one-halo tile
+  auto load_hist = [&](int zl, int sl) {
+    const int zo = wrap_or_mirror(zl, nz, per_z) * plane;
+    for (int p = t; p < N1; p += NT) {
+      const int px = p % HX1, py = p / HX1;
+      const int xl = x0 - 1 + px, yl = y0 - 1 + py;
+      if (xl > nx || yl > ny) continue;
+      const int o = zo + wrap_or_mirror(yl, ny, per_y) * nx + wrap_or_mirror(xl, nx, per_x);
+      const float ux = h_in[nodes + o], uy = h_in[2 * nodes + o], uz = h_in[3 * nodes + o];
+      const float sx = h_in[4 * nodes + o], sy = h_in[5 * nodes + o], sz = h_in[6 * nodes + o];
+      S.acor[sl][0][p] = sx * uy - ux * sy;
+      S.acor[sl][1][p] = sx * uz - ux * sz;
+      S.acor[sl][2][p] = sy * uz - uy * sz;
+    }
+  };
+  const InstanceConsts& k = S.k;
+  // mubar_1 of logical plane zl on the one-halo tile; phi ring slots of zl-1, zl, zl+1
+  auto calc_mub = [&](int zl, int rm, int r0, int rp, int sl) {
+    for (int p = t; p < N1; p += NT) {
+      const int px = p % HX1, py = p / HX1;
+      if (x0 - 1 + px > nx || y0 - 1 + py > ny) continue;
+      const int i = (py + 1) * HX2 + (px + 1);
+      const float lap0 = lap3(S.phi0[rm], S.phi0[r0], S.phi0[rp], i, HX2);
+      const float lap1 = lap3(S.phi1[rm], S.phi1[r0], S.phi1[rp], i, HX2);
+      float mu0, mu1, mu2;
+      chem_pot(k, S.phi0[r0][i], S.phi1[r0][i], lap0, lap1, mu0, mu1, mu2);
+      S.mub[sl][p] = mubar1_of(k, mu0, mu1, mu2);
+    }
+  };
+
+  // prologue: phi planes zs-2 .. zs+1, products zs-1, zs, mubar zs-1, zs
+  __syncthreads();   // constants visible
+  for (int q = -2; q <= 1; ++q) load_phi(zs + q, ring(zs + q, RP));
+  load_hist(zs - 1, ring(zs - 1, RM));
+  load_hist(zs, ring(zs, RM));
+  __syncthreads();
+  calc_mub(zs - 1, ring(zs - 2, RP), ring(zs - 1, RP), ring(zs, RP), ring(zs - 1, RM));
+  calc_mub(zs, ring(zs - 1, RP), ring(zs, RP), ring(zs + 1, RP), ring(zs, RM));
+
+  const int x = x0 + tx, y = y0 + ty;
+  const bool own = x < nx && y < ny;
+  for (int z = zs; z < ze; ++z) {
+    __syncthreads();   // the rings of plane z-1 are no longer read
+    load_phi(z + 2, ring(z + 2, RP));
+    load_hist(z + 1, ring(z + 1, RM));
+    __syncthreads();
+    calc_mub(z + 1, ring(z, RP), ring(z + 1, RP), ring(z + 2, RP), ring(z + 1, RM));
+    __syncthreads();
+    if (!own) continue;
+
+    const int node = z * plane + y * nx + x;
+    const float cs2 = k.cs2, cs4 = k.cs4;
+    const int rpm = ring(z - 1, RP), rp0 = ring(z, RP), rpp = ring(z + 1, RP);
+    const int rmm = ring(z - 1, RM), rm0 = ring(z, RM), rmp = ring(z + 1, RM);
+    const int i2 = (ty + 2) * HX2 + (tx + 2);
+    const int i1 = (ty + 1) * HX1 + (tx + 1);
+
+    // stencils of phi0, phi1 (two-halo ring) and mubar_1, products (one-halo ring)
+    const float* A0m = S.phi0[rpm];
+    const float* A00 = S.phi0[rp0];
+    const float* A0p = S.phi0[rpp];
+    const float* A1m = S.phi1[rpm];
+    const float* A10 = S.phi1[rp0];
+    const float* A1p = S.phi1[rpp];
+    const float ph0 = A00[i2], ph1 = A10[i2], ph2 = 1.f - ph0 - ph1;
+    const float g0x = dgrad<0>(A0m, A00, A0p, i2, HX2), g0y = dgrad<1>(A0m, A00, A0p, i2, HX2),
+                g0z = dgrad<2>(A0m, A00, A0p, i2, HX2);
+    const float g1x = dgrad<0>(A1m, A10, A1p, i2, HX2), g1y = dgrad<1>(A1m, A10, A1p, i2, HX2),
+                g1z = dgrad<2>(A1m, A10, A1p, i2, HX2);
+    float mu0, mu1, mu2;
+    chem_pot(k, ph0, ph1, lap3(A0m, A00, A0p, i2, HX2), lap3(A1m, A10, A1p, i2, HX2), mu0, mu1, mu2);
+    const float d02 = mu0 - mu2, d12 = mu1 - mu2;
+    const float* Mm = S.mub[rmm];
+    const float* M0 = S.mub[rm0];
+    const float* Mp = S.mub[rmp];
+    const float mub = M0[i1];
+    const float gmx = dgrad<0>(Mm, M0, Mp, i1, HX1), gmy = dgrad<1>(Mm, M0, Mp, i1, HX1),
+                gmz = dgrad<2>(Mm, M0, Mp, i1, HX1);
+    // correction force F_c,b = 1/2 sum_a d_a (S_a u_b - u_a S_b), products A_xy, A_xz, A_yz
+    const float dAxy_x = dgrad<0>(S.acor[rmm][0], S.acor[rm0][0], S.acor[rmp][0], i1, HX1);
+    const float dAxy_y = dgrad<1>(S.acor[rmm][0], S.acor[rm0][0], S.acor[rmp][0], i1, HX1);
+    const float dAxz_x = dgrad<0>(S.acor[rmm][1], S.acor[rm0][1], S.acor[rmp][1], i1, HX1);
+    const float dAxz_z = dgrad<2>(S.acor[rmm][1], S.acor[rm0][1], S.acor[rmp][1], i1, HX1);
+    const float dAyz_y = dgrad<1>(S.acor[rmm][2], S.acor[rm0][2], S.acor[rmp][2], i1, HX1);
+    const float dAyz_z = dgrad<2>(S.acor[rmm][2], S.acor[rm0][2], S.acor[rmp][2], i1, HX1);
+    const float Fcx = -0.5f * (dAxy_y + dAxz_z);
+    const float Fcy = 0.5f * (dAxy_x - dAyz_z);
+    const float Fcz = 0.5f * (dAxz_x + dAyz_y);
+
+    // previous-step history of this node
+    const float php = h_in[node];
+    const float upx = h_in[nodes + node], upy = h_in[2 * nodes + node], upz = h_in[3 * nodes + node];
+    const float spx = h_in[4 * nodes + node], spy = h_in[5 * nodes + node], spz = h_in[6 * nodes + node];
+
+    // degenerate mobility, flux S (frozen phi0), mixture properties
+    const float fdeg = ph1 * (1.f - ph1) * (1.f - ph0);
+    const float mob = k.M_cst + k.M_deg * fdeg;
+    const float sfac = (k.rho1 - k.rho2) * mob * k.inv_gam1;
+    const float Sx = sfac * gmx, Sy = sfac * gmy, Sz = sfac * gmz;
+    const float rho = k.rho0 * ph0 + k.rho1 * ph1 + k.rho2 * ph2;
+    const float grx = (k.rho0 - k.rho2) * g0x + (k.rho1 - k.rho2) * g1x;
+    const float gry = (k.rho0 - k.rho2) * g0y + (k.rho1 - k.rho2) * g1y;
+    const float grz = (k.rho0 - k.rho2) * g0z + (k.rho1 - k.rho2) * g1z;
+    const float muv = k.mu0 * ph0 + k.mu1 * ph1 + k.mu2 * ph2;
+
+    // F = F_s + F_b + F_c with F_s = (mu0 - mu2) grad phi0 + (mu1 - mu2) grad phi1
+    const float one_m0 = 1.f - ph0;
+    const float Fx = d02 * g0x + d12 * g1x + one_m0 * k.bx + Fcx;
+    const float Fy = d02 * g0y + d12 * g1y + one_m0 * k.by + Fcy;
+    const float Fz = d02 * g0z + d12 * g1z + one_m0 * k.bz + Fcz;
+
+    // NS populations and their moments
+    float g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = __ldcs(g_in + i * nodes + node);
+    float sum_nz = 0.f, mx = 0.f, my = 0.f, mz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+    float ex = 0.f, ey = 0.f, ez = 0.f, bxm = 0.f, bym = 0.f, bzm = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int cx = CX(i), cy = CY(i), cz = CZ(i);
+      const float v = g[i];
+      sum_nz += v;
+      if (cx) mx += cx > 0 ? v : -v;
+      if (cy) my += cy > 0 ? v : -v;
+      if (cz) mz += cz > 0 ? v : -v;
+      if (cx && cy) pxy += cx * cy > 0 ? v : -v;
+      if (cx && cz) pxz += cx * cz > 0 ? v : -v;
+      if (cy && cz) pyz += cy * cz > 0 ? v : -v;
+      // third-order sums: sum c_a (c_b^2 + c_c^2) g and sum c_a (c_b^2 - c_c^2) g (cyclic a, b, c)
+      if (cx && (cy || cz)) {
+        ex += cx > 0 ? v : -v;
+        bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v;
+      }
+      if (cy && (cz || cx)) {
+        ey += cy > 0 ? v : -v;
+        bym += ((cz ? 1 : -1) * cy > 0) ? v : -v;
+      }
+      if (cz && (cx || cy)) {
+        ez += cz > 0 ? v : -v;
+        bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v;
+      }
+    }
+
+    // velocity with the solid penalisation force (u_w = 0)
+    const float inv_rho = __frcp_rn(rho);
+    const float usx = (mx + 0.5f * Fx) * inv_rho;
+    const float usy = (my + 0.5f * Fy) * inv_rho;
+    const float usz = (mz + 0.5f * Fz) * inv_rho;
+    const float damp = 1.f - 0.5f * ph0;
+    const float ux = usx * damp, uy = usy * damp, uz = usz * damp;
+    const float Ftx = Fx - ph0 * rho * usx, Fty = Fy - ph0 * rho * usy, Ftz = Fz - ph0 * rho * usz;
+
+    // local viscous rates (s0 = s4 = s2a)
+    const float om = fmaxf(one_m0, kOneMinusPhi0Floor);
+    const float ra = rho * om * k.a2a, rb = rho * om * k.a2b;
+    const float s2a = __fdividef(ra, 0.5f * ra + muv);
+    const float s2b = __fdividef(rb, 0.5f * rb + muv);
+    const float inv_s2a = 0.5f + __fdividef(muv, ra);
+
+    // pressure (Sec. 3)
+    const float udg = ux * grx + uy * gry + uz * grz;
+    const float q = (rho * ux - Sx) * ux + (rho * uy - Sy) * uy + (rho * uz - Sz) * uz;
+    const float rhop = k.rho0 * ph0 + k.rho1 * php + k.rho2 * (1.f - ph0 - php);
+    const float qp = (rhop * upx - spx) * upx + (rhop * upy - spy) * upy + (rhop * upz - spz) * upz;
+    const float H = k.Kp * ((k.h0 - k.h2) * inv_s2a + k.h3);
+    const float p = k.pf * (sum_nz + (0.5f + H) * udg - k.wq * q + 0.5f * k.Kp * (q - qp));
+
+    // push destinations; interior nodes use fixed offsets
+    const bool edge = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
+    auto store = [&](float* __restrict__ out, int i, float v) {
+      const int cx = CX(i), cy = CY(i), cz = CZ(i);
+      if (!edge) {
+        out[i * nodes + node + cz * plane + cy * nx + cx] = v;
+        return;
+      }
+      int xd = x + cx, yd = y + cy, zd = z + cz;
+      bool bb = false;
+      if (xd < 0 || xd >= nx) {
+        if (per_x) xd = xd < 0 ? xd + nx : xd - nx;
+        else bb = true;
+      }
+      if (yd < 0 || yd >= ny) {
+        if (per_y) yd = yd < 0 ? yd + ny : yd - ny;
+        else bb = true;
+      }
+      if (zd < 0 || zd >= nz) {
+        if (per_z) zd = zd < 0 ? zd + nz : zd - nz;
+        else bb = true;
+      }
+      const int dst = bb ? OPP(i) * nodes + node : i * nodes + (zd * ny + yd) * nx + xd;
+      out[dst] = v;
+    };
+
+    // ---- NS collision: g* = (1 - s2a) g + w_i X_i (see the file header) ----
+    {
+      const float om2a = 1.f - 0.5f * s2a;
+      // equilibrium second moments e_ab and the force moment M^2F_ab (Sec. 3)
+      const float exx = rho * ux * ux - Sx * ux, eyy = rho * uy * uy - Sy * uy, ezz = rho * uz * uz - Sz * uz;
+      const float exy = rho * ux * uy - 0.5f * (Sx * uy + ux * Sy);
+      const float exz = rho * ux * uz - 0.5f * (Sx * uz + ux * Sz);
+      const float eyz = rho * uy * uz - 0.5f * (Sy * uz + uy * Sz);
+      const float dSxx = Sx * ux - spx * upx, dSyy = Sy * uy - spy * upy, dSzz = Sz * uz - spz * upz;
+      const float dSxy = 0.5f * (Sx * uy + ux * Sy) - 0.5f * (spx * upy + upx * spy);
+      const float dSxz = 0.5f * (Sx * uz + ux * Sz) - 0.5f * (spx * upz + upx * spz);
+      const float dSyz = 0.5f * (Sy * uz + uy * Sz) - 0.5f * (spy * upz + upy * spz);
+      const float iso = (1.f - 3.f * cs2) * udg;
+      const float Mxx = 2.f * ux * Fx - dSxx + 2.f * cs2 * ux * grx + iso;
+      const float Myy = 2.f * uy * Fy - dSyy + 2.f * cs2 * uy * gry + iso;
+      const float Mzz = 2.f * uz * Fz - dSzz + 2.f * cs2 * uz * grz + iso;
+      const float Mxy = ux * Fy + Fx * uy - dSxy + cs2 * (ux * gry + grx * uy);
+      const float Mxz = ux * Fz + Fx * uz - dSxz + cs2 * (ux * grz + grx * uz);
+      const float Myz = uy * Fz + Fy * uz - dSyz + cs2 * (uy * grz + gry * uz);
+      const float i2n = __frcp_rn(cs2 - cs4), ic2 = __frcp_rn(cs2), ic4 = __frcp_rn(cs4);
+      const float Dx = (s2a * exx + om2a * Mxx) * i2n;
+      const float Dy = (s2a * eyy + om2a * Myy) * i2n;
+      const float Dz = (s2a * ezz + om2a * Mzz) * i2n;
+      const float base = s2a * p * ic2 + om2a * udg - cs2 * (Dx + Dy + Dz);
+      const float d1 = k.s1n - s2a;
+      const float Vx = (s2a * rho * ux + om2a * Ftx - d1 * (mx - rho * ux + 0.5f * Ftx)) * ic2;
+      const float Vy = (s2a * rho * uy + om2a * Fty - d1 * (my - rho * uy + 0.5f * Fty)) * ic2;
+      const float Vz = (s2a * rho * uz + om2a * Ftz - d1 * (mz - rho * uz + 0.5f * Ftz)) * ic2;
+      const float db = s2b - s2a;
+      const float Oxy = (s2a * exy + om2a * Mxy - db * (pxy - exy + 0.5f * Mxy)) * ic4;
+      const float Oxz = (s2a * exz + om2a * Mxz - db * (pxz - exz + 0.5f * Mxz)) * ic4;
+      const float Oyz = (s2a * eyz + om2a * Myz - db * (pyz - eyz + 0.5f * Myz)) * ic4;
+      // third-order group: T_a = (s3 - s2a) m_A,a / |A|^2, U_a = (s3 - s2a) m_B,a / |B|^2
+      const float d3 = k.s3n - s2a;
+      const float iB = __frcp_rn(2.f * cs4), iA = __frcp_rn(2.f * cs4 * (1.f - 2.f * cs2));
+      const float k3 = 1.f - 2.f * cs2;
+      const float Tx = d3 * (ex - 2.f * cs2 * mx) * iA, Ty = d3 * (ey - 2.f * cs2 * my) * iA,
+                  Tz = d3 * (ez - 2.f * cs2 * mz) * iA;
+      const float Ux = d3 * bxm * iB, Uy = d3 * bym * iB, Uz = d3 * bzm * iB;
+      const float Px = k3 * Tx + Ux, Qx = k3 * Tx - Ux;   // edge factors per axis: B_a = +c_a or -c_a
+      const float Py = k3 * Ty + Uy, Qy = k3 * Ty - Uy;
+      const float Pz = k3 * Tz + Uz, Qz = k3 * Tz - Uz;
+      const float om1 = 1.f - s2a;
+      store(g_out, 0, om1 * g[0] + k.w0 * base - s2a * p * ic2);
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int cx = CX(i), cy = CY(i), cz = CZ(i);
+        float X = base;
+        if (cx) X += cx > 0 ? Dx + Vx : Dx - Vx;
+        if (cy) X += cy > 0 ? Dy + Vy : Dy - Vy;
+        if (cz) X += cz > 0 ? Dz + Vz : Dz - Vz;
+        if (cx && cy) X += cx * cy > 0 ? Oxy : -Oxy;
+        if (cx && cz) X += cx * cz > 0 ? Oxz : -Oxz;
+        if (cy && cz) X += cy * cz > 0 ? Oyz : -Oyz;
+        if (i < 7) {
+          // axis: A_a(c) = -2 cs2 c_a, B_a(c) = 0
+          const float T = cx ? Tx : (cy ? Ty : Tz);
+          const int c = cx + cy + cz;
+          X += c > 0 ? 2.f * cs2 * T : -2.f * cs2 * T;
+        } else {
+          // edge: -c_a [(1 - 2 cs2) T_a + B_a U_a / c_a] over its two axes
+          if (cx) { const float e = cy ? Px : Qx; X -= cx > 0 ? e : -e; }
+          if (cy) { const float e = cz ? Py : Qy; X -= cy > 0 ? e : -e; }
+          if (cz) { const float e = cx ? Pz : Qz; X -= cz > 0 ? e : -e; }
+        }
+        store(g_out, i, om1 * g[i] + weight(k, i) * X);
+      }
+    }
+
+    // ---- CH collision ----
+    {
+      const float emb = k.eta * mub;
+      const float corr = k.corr_scale * (1.f - fdeg);
+      // first moment of R: d_t(phi1 u) + cs2 corr eta grad mubar
+      const float Rx = (ph1 * ux - php * upx) + cs2 * corr * k.eta * gmx;
+      const float Ry = (ph1 * uy - php * upy) + cs2 * corr * k.eta * gmy;
+      const float Rz = (ph1 * uz - php * upz) + cs2 * corr * k.eta * gmz;
+      const float ic2 = __frcp_rn(cs2);
+      if (k.ch_fast != 0.f) {
+        // f* = f^eq + R/2 - (s1 - 1) P1 v: only j = sum c f enters
+        const float jx = j_in[node], jy = j_in[nodes + node], jz = j_in[2 * nodes + node];
+        const float ax = (ph1 * ux + (1.f - k.s1c) * (jx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx) * ic2;
+        const float ay = (ph1 * uy + (1.f - k.s1c) * (jy - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry) * ic2;
+        const float az = (ph1 * uz + (1.f - k.s1c) * (jz - ph1 * uz) + (1.f - 0.5f * k.s1c) * Rz) * ic2;
+        float rest = ph1;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int cx = CX(i), cy = CY(i), cz = CZ(i);
+          float s = emb;
+          if (cx) s += cx > 0 ? ax : -ax;
+          if (cy) s += cy > 0 ? ay : -ay;
+          if (cz) s += cz > 0 ? az : -az;
+          const float v = weight(k, i) * s;
+          rest -= v;
+          store(f_out, i, v);
+        }
+        store(f_out, 0, rest);   // the rest population closes the zeroth moment
+      } else {
+        float f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = f_in[i * nodes + node];
+        float jx = 0.f, jy = 0.f, jz = 0.f, qxx = 0.f, qyy = 0.f, qzz = 0.f, qxy = 0.f, qxz = 0.f, qyz = 0.f;
+        float ex = 0.f, ey = 0.f, ez = 0.f, bxm = 0.f, bym = 0.f, bzm = 0.f;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int cx = CX(i), cy = CY(i), cz = CZ(i);
+          const float v = f[i];
+          if (cx) { jx += cx > 0 ? v : -v; qxx += v; }
+          if (cy) { jy += cy > 0 ? v : -v; qyy += v; }
+          if (cz) { jz += cz > 0 ? v : -v; qzz += v; }
+          if (cx && cy) qxy += cx * cy > 0 ? v : -v;
+          if (cx && cz) qxz += cx * cz > 0 ? v : -v;
+          if (cy && cz) qyz += cy * cz > 0 ? v : -v;
+          if (cx && (cy || cz)) { ex += cx > 0 ? v : -v; bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v; }
+          if (cy && (cz || cx)) { ey += cy > 0 ? v : -v; bym += ((cz ? 1 : -1) * cy > 0) ? v : -v; }
+          if (cz && (cx || cy)) { ez += cz > 0 ? v : -v; bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v; }
+        }
+        const float s4 = k.s4c, om4 = 1.f - s4, oh4 = 1.f - 0.5f * s4;
+        const float d1 = (k.s1c - s4) * ic2;
+        const float m1x = jx - ph1 * ux + 0.5f * Rx, m1y = jy - ph1 * uy + 0.5f * Ry, m1z = jz - ph1 * uz + 0.5f * Rz;
+        const float d2a = (k.s2ac - s4) * __frcp_rn(cs2 - cs4);
+        const float m2x = qxx - cs2 * emb, m2y = qyy - cs2 * emb, m2z = qzz - cs2 * emb;
+        const float d2b = (k.s2bc - s4) * __frcp_rn(cs4);
+        const float d3 = k.s3c - s4;
+        const float iB = __frcp_rn(2.f * cs4), iA = __frcp_rn(2.f * cs4 * (1.f - 2.f * cs2));
+        const float k3 = 1.f - 2.f * cs2;
+        const float Tx = d3 * (ex - 2.f * cs2 * jx) * iA, Ty = d3 * (ey - 2.f * cs2 * jy) * iA,
+                    Tz = d3 * (ez - 2.f * cs2 * jz) * iA;
+        const float Ux = d3 * bxm * iB, Uy = d3 * bym * iB, Uz = d3 * bzm * iB;
+        const float Px = k3 * Tx + Ux, Qx = k3 * Tx - Ux;
+        const float Py = k3 * Ty + Uy, Qy = k3 * Ty - Uy;
+        const float Pz = k3 * Tz + Uz, Qz = k3 * Tz - Uz;
+        const float p2 = -cs2 * d2a * (m2x + m2y + m2z);   // c-independent part of the P2a term
+        // rest population: f^eq_0 = phi1 + (w0 - 1) eta mubar, R_0 = 0
+        store(f_out, 0, om4 * f[0] + s4 * (ph1 + (k.w0 - 1.f) * emb) - k.w0 * p2);
+        const float ux1 = ph1 * ux * ic2, uy1 = ph1 * uy * ic2, uz1 = ph1 * uz * ic2;
+        const float rx = Rx * ic2, ry = Ry * ic2, rz = Rz * ic2;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int cx = CX(i), cy = CY(i), cz = CZ(i);
+          // f^eq_i / w_i = eta mubar + c.phi u / cs2;  R_i / w_i = c.R / cs2
+          float feq = emb, Rc = 0.f, L = p2;
+          if (cx) { feq += cx > 0 ? ux1 : -ux1; Rc += cx > 0 ? rx : -rx; L += (cx > 0 ? m1x : -m1x) * d1 + d2a * m2x; }
+          if (cy) { feq += cy > 0 ? uy1 : -uy1; Rc += cy > 0 ? ry : -ry; L += (cy > 0 ? m1y : -m1y) * d1 + d2a * m2y; }
+          if (cz) { feq += cz > 0 ? uz1 : -uz1; Rc += cz > 0 ? rz : -rz; L += (cz > 0 ? m1z : -m1z) * d1 + d2a * m2z; }
+          if (cx && cy) L += (cx * cy > 0 ? qxy : -qxy) * d2b;
+          if (cx && cz) L += (cx * cz > 0 ? qxz : -qxz) * d2b;
+          if (cy && cz) L += (cy * cz > 0 ? qyz : -qyz) * d2b;
+          if (i < 7) {
+            const float T = cx ? Tx : (cy ? Ty : Tz);
+            const int c = cx + cy + cz;
+            L -= c > 0 ? 2.f * cs2 * T : -2.f * cs2 * T;
+          } else {
+            if (cx) { const float e = cy ? Px : Qx; L += cx > 0 ? e : -e; }
+            if (cy) { const float e = cz ? Py : Qy; L += cy > 0 ? e : -e; }
+            if (cz) { const float e = cx ? Pz : Qz; L += cz > 0 ? e : -e; }
+          }
+          const float w = weight(k, i);
+          store(f_out, i, om4 * f[i] + w * (s4 * feq + oh4 * Rc - L));
+        }
+      }
+    }
+
+    // history of this step (phi1 was written by the moment pass)
+    h_out[nodes + node] = ux;
+    h_out[2 * nodes + node] = uy;
+    h_out[3 * nodes + node] = uz;
+    h_out[4 * nodes + node] = Sx;
+    h_out[5 * nodes + node] = Sy;
+    h_out[6 * nodes + node] = Sz;
+    if (OBS) {
+      a.p_out[(long long)b * nodes + node] = p;
+      const float u2 = ux * ux + uy * uy + uz * uz;
+      if (!(u2 <= 0.25f) || !(fabsf(ph1) < 1e30f)) atomicOr(a.flag, 1u);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, float* g, float* hist,
+                              const InstanceConsts* consts, int nx, int ny, int nz, int per_x, int per_y,
+                              int per_z, int nbatch, cudaStream_t s) {
+  const long long total = (long long)nx * ny * nz * nbatch;
+  const long long blocks = std::min<long long>((total + 255) / 256, 1LL << 20);
+  d3q19_init<<<(unsigned)blocks, 256, 0, s>>>(phi0, phi1, f, g, hist, consts, nx, ny, nz, per_x, per_y, per_z,
+                                               nbatch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+  const int nodes = (int)a.nodes;
+  const int vec4 = (nodes & 3) == 0;
+  const int per_thread = vec4 ? 4 : 1;
+  const int mblocks = (nodes / per_thread + 255) / 256;
+  d3q19_moments<<<dim3(mblocks, nbatch), 256, 0, s>>>(a.f_in, a.hist_out, a.mom, nodes, vec4);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  const size_t smem = sizeof(StepSmem3);
+  static bool configured = false;   // attribute set once per process (both variants)
+  if (!configured) {
+    e = cudaFuncSetAttribute(d3q19_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(d3q19_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int ntx = (a.nx + TX - 1) / TX;
+  const int nstrips = (a.nz + a.strip - 1) / a.strip;
+  dim3 grid(ntx * nstrips, (a.ny + TY - 1) / TY, nbatch);
+  if (observe) d3q19_step<true><<<grid, NT, smem, s>>>(a);
+  else d3q19_step<false><<<grid, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
 
 }  // namespace lbm

@@ -48,6 +48,7 @@ struct StepArgs {
   const float* hist_in;   // [b][k][nodes]: phi1, u (d), S (d) at the previous step
   float* hist_out;
   float* p_out;           // written only by the observing variant
+  float* mom;             // D3Q19: [b][3][nodes] first moment of f, written by the moment pass
   const InstanceConsts* consts;
   unsigned int* flag;     // divergence flag (observing variant)
   int nx, ny, nz;

@@ -29,6 +29,9 @@ __all__ = [
     "random_disks_droplet",
     "rsa_spheres",
     "porous_inlet_slab",
+    "spheres_phi0",
+    "sphere_box_droplet",
+    "wall_drop_3d",
     "splitmix64",
 ]
 
@@ -255,25 +258,76 @@ def porous_inlet_slab(n=256, seed=0, W=4.0, slab=32.0, rmin=10.0, rmax=20.0, tar
     """
     if spheres is None:
         spheres = rsa_spheres(n, seed, rmin, rmax, target_solid)
-    ax = np.arange(n, dtype=np.float64)
-    phi0 = np.zeros((n, n, n))
-    for (cx, cy, cz, r) in spheres:
-        lo = [int(math.floor(c - r - 2 * W)) for c in (cz, cy, cx)]
-        hi = [int(math.ceil(c + r + 2 * W)) + 1 for c in (cz, cy, cx)]
-        iz = np.arange(lo[0], hi[0]) % n
-        iy = np.arange(lo[1], hi[1]) % n
-        ix = np.arange(lo[2], hi[2]) % n
-        dz = np.arange(lo[0], hi[0]) - cz
-        dy = np.arange(lo[1], hi[1]) - cy
-        dx = np.arange(lo[2], hi[2]) - cx
-        d = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
-        blk = diffuse(r - d, W)
-        sub = phi0[np.ix_(iz, iy, ix)]
-        phi0[np.ix_(iz, iy, ix)] = np.maximum(sub, blk)
-    del ax
+    phi0 = spheres_phi0((n, n, n), spheres, W)
     x = np.arange(n, dtype=np.float64)[None, None, :]
     phi1 = (1.0 - phi0) * diffuse(slab - x, W)
     phi1 = np.broadcast_to(phi1, phi0.shape).copy()
     poro = 1.0 - phi0.mean()
     return Geometry(phi0, phi1, (True, True, True), probe_origin=(0.0, 0.0, 0.0), probe_axis=0,
                     note=f"{len(spheres)} RSA spheres r in [{rmin},{rmax}], seed {seed}, porosity {poro:.4f}")
+
+
+def spheres_phi0(shape, spheres, W=4.0):
+    """Diffuse solid indicator of (possibly overlapping) spheres on a periodic box.
+
+    ``shape`` is ``(nz, ny, nx)``; ``spheres`` lists ``(cx, cy, cz, r)``.  Each
+    sphere is drawn with its periodic images and the union takes the maximum.
+    """
+    nz, ny, nx = shape
+    phi0 = np.zeros(shape)
+    for (cx, cy, cz, r) in spheres:
+        lo = [int(math.floor(c - r - 2 * W)) for c in (cz, cy, cx)]
+        hi = [int(math.ceil(c + r + 2 * W)) + 1 for c in (cz, cy, cx)]
+        rng = []
+        for lo_a, hi_a, n_a, c in zip(lo, hi, shape, (cz, cy, cx)):
+            if hi_a - lo_a >= n_a:
+                # nearest periodic image of every node along this axis
+                idx = np.arange(n_a)
+                d = idx - c
+                d = d - n_a * np.round(d / n_a)
+                rng.append((idx, d))
+            else:
+                k = np.arange(lo_a, hi_a)
+                rng.append((k % n_a, k - c))
+        (iz, dz), (iy, dy), (ix, dx) = rng
+        d = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
+        blk = diffuse(r - d, W)
+        sub = phi0[np.ix_(iz, iy, ix)]
+        phi0[np.ix_(iz, iy, ix)] = np.maximum(sub, blk)
+    return phi0
+
+
+def sphere_box_droplet(nx, ny, nz, spheres, slab=None, drop=None, W=4.0, periodic=(True, True, True)):
+    """Spheres in a box with fluid 1 either filling ``x < slab`` or as a drop.
+
+    ``drop`` is ``(cx, cy, cz, R)``.  ``phi1 = (1 - phi0) * indicator``.
+    """
+    phi0 = spheres_phi0((nz, ny, nx), spheres, W)
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    if drop is not None:
+        cx, cy, cz, R = drop
+        ind = diffuse(R - np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2), W)
+    else:
+        ind = diffuse(slab - x, W)
+    phi1 = (1.0 - phi0) * ind
+    return Geometry(phi0, phi1, tuple(periodic), probe_origin=(0.0, 0.0, 0.0), probe_axis=0,
+                    note=f"{len(spheres)} spheres")
+
+
+def wall_drop_3d(nx, ny, nz, wall_layers, R, W=4.0, xc=None, yc=None):
+    """Flat solid layer at the bottom (z) with a spherical drop resting on it.
+
+    Periodic in x and y, half-way walls in z.  The drop centre sits on the
+    solid surface ``z = wall_layers - 1/2``.
+    """
+    xc = (nx - 1) / 2.0 if xc is None else xc
+    yc = (ny - 1) / 2.0 if yc is None else yc
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    zw = wall_layers - 0.5
+    phi0 = diffuse(zw - z, W)
+    ind = diffuse(R - np.sqrt((x - xc) ** 2 + (y - yc) ** 2 + (z - zw) ** 2), W)
+    phi1 = (1.0 - phi0) * ind
+    return Geometry(phi0, phi1, (True, True, False), probe_origin=(xc, yc, 0.0), probe_axis=2,
+                    wall_level=zw, droplet_radius=R, note="drop on a flat wall (3D)")

@@ -19,54 +19,13 @@ import numpy as np
 import pytest
 
 from _parity import as_inputs, gpu_run, oracle_run, rel_l2
+from _parity import compare_run as _compare
 from oracle import lbm as olbm
 from oracle import model as omodel
 from oracle import observables as oobs
 from synthetic import cylinder_droplet, free_drop, wall_droplet
 
 pytestmark = pytest.mark.gpu
-
-
-def _compare(L, lattice, geo, prm, periodic, steps, strip=None, tol=1e-5, tol_pop=1e-4, u_abs=None, p_abs=None):
-    phi0, phi1 = as_inputs(geo)
-    ctx = gpu_run(L, lattice, phi0, phi1, prm, periodic, steps, strip)
-    try:
-        g_phi1, g_u, g_p = ctx.get_fields()
-        g_f, g_g = ctx.get_populations()
-        obs = ctx.observables(0)
-    finally:
-        ctx.close()
-    st = olbm.init_state(lattice, phi0.astype(np.float64), phi1.astype(np.float64), omodel.Params(**prm),
-                         tuple(periodic))
-    u_peak, done = 0.0, 0
-    while done < steps:
-        k = min(100, steps - done)
-        olbm.step(st, nsteps=k)
-        done += k
-        u_peak = max(u_peak, float(np.linalg.norm(st.macro["u"])))
-    n = phi0.size
-    o_phi1 = st.macro["phi1"].ravel()
-    o_u = st.macro["u"].reshape(-1, n)
-    o_p = st.macro["p"].ravel()
-    q = st.f.shape[0]
-    g_gg = g_g[0].astype(np.float64)
-    g_gg[0] += prm.get("rho", (1.0, 1.0, 1.0))[0]   # the library stores g_0 minus rho_0
-    du = np.linalg.norm(g_u[0].astype(np.float64) - o_u)
-    errs = dict(phi1=rel_l2(g_phi1[0], o_phi1), u=du / max(u_peak, 1e-300), u_end=rel_l2(g_u[0], o_u),
-                p=rel_l2(g_p[0], o_p), f=rel_l2(g_f[0], st.f.reshape(q, n)), g=rel_l2(g_gg, st.g.reshape(q, n)))
-    if u_abs is None:
-        assert errs["phi1"] <= tol and errs["u"] <= tol, errs
-    else:
-        errs["u_abs"] = float(np.sqrt(np.mean((g_u[0].astype(np.float64) - o_u) ** 2)))
-        assert errs["phi1"] <= tol and errs["u_abs"] <= u_abs, errs
-    print("parity", errs)
-    assert errs["f"] <= tol_pop and errs["g"] <= tol_pop, errs
-    if p_abs is None:
-        assert errs["p"] <= tol_pop, errs
-    else:
-        errs["p_abs"] = float(np.sqrt(np.mean((g_p[0].astype(np.float64) - o_p) ** 2)))
-        assert errs["p_abs"] <= p_abs, errs
-    return st, obs, errs
 
 
 def test_flat_wall_1000_steps_ragged(lbm_lib):
