@@ -1,19 +1,26 @@
 #!/usr/bin/env python
 """Throughput of the coupled CH + NS lattice Boltzmann step on GB300.
 
-Workload: the disk + droplet lattice of the cylinder experiment (Sec. 4.3) at
-1024 x 1024 nodes, D2Q9, solid disk of radius 160 lu, droplet of radius 120 lu
-on its top, density and viscosity ratio 10, contact angle swept over
-{30, 60, 90, 120, 150} deg.  The five angles are five independent instances
-advanced by one launch per time step.  A "step" is one time step of all five
-instances (5 x 1024^2 lattice updates); the metric is million lattice updates
-per second (MLUPS) over the whole job.
+Default workload (``--workload disk1024x5``): the disk + droplet lattice of
+the cylinder experiment (Sec. 4.3) at 1024 x 1024 nodes, D2Q9, solid disk of
+radius 160 lu, droplet of radius 120 lu on its top, density and viscosity
+ratio 10, contact angle swept over {30, 60, 90, 120, 150} deg.  The five
+angles are five independent instances advanced by one launch per time step.
+A "step" is one time step of all five instances (5 x 1024^2 lattice
+updates).
 
-Rank 0 prints one JSON line.  Under torchrun every rank runs the same batch on
-its own GPU (independent instances, no collective on the data path; weak
+``--workload porous256``: the 3D porous run, D3Q19 on 256^3 nodes, seeded
+random non-overlapping spheres (radii 10-20 lu, porosity about 0.6), fluid 1
+in the inlet slab x < 32, contact angle 120 deg, body force 1e-6 along x,
+ratios 1, d0 = 1/3.  A step is one time step of that lattice (two launches:
+moment pass and fused kernel).
+
+The metric is million lattice updates per second (MLUPS) over the whole job.
+Rank 0 prints one JSON line.  Under torchrun every rank runs the same work on
+its own GPU (independent lattices, no collective on the data path; weak
 scaling), timing is the maximum over ranks.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 """
 from __future__ import annotations
 
@@ -32,8 +39,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "coupled CH+NS LBM MLUPS on 1 GB300, % of HBM roofline, time-to-equilibrium"
-BYTES_PER_LU = 188   # f, g read+write 144; phi0 4; history (phi1, u, S) read 20 + write 20
 FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic HBM bytes per lattice update.  D2Q9: f, g read + write 144;
+# phi0 4; history (phi1, u, S) read 20 + write 20.  D3Q19: f, g read + write
+# 304; phi0 4; history (phi1, u, S) read 28 + write 28.  Of the D3Q19 bytes
+# the moment pass moves f read 76 + phi1 write 4 and the fused kernel the
+# other 284.
+WORKLOADS = {
+    "disk1024x5": dict(lattice="D2Q9", size=1024, bytes_per_lu=188, kernel="d2q9_step", kernel_bytes_per_lu=188,
+                       kernel_src="lbm_d2q9.cu", profile="d2q9_step_disk1024x5.md", launches_per_step=1,
+                       oracle_us_per_node_step=2.5),
+    "porous256": dict(lattice="D3Q19", size=256, bytes_per_lu=364, kernel="d3q19_step", kernel_bytes_per_lu=284,
+                      kernel_src="lbm_d3q19.cu", profile="d3q19_step_porous256.md", launches_per_step=2,
+                      oracle_us_per_node_step=8.5),
+}
 
 
 def log(*a):
@@ -47,8 +67,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--size", type=int, default=1024, help="lattice side (default: the 1024^2 workload)")
+    ap.add_argument("--cpu-seconds", type=float, default=60.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS))
+    ap.add_argument("--size", type=int, default=None, help="lattice side (default: the workload's)")
     return ap.parse_args()
 
 
@@ -109,11 +130,11 @@ class Clocks:
                 if any(r[3].split()[0].replace(".", "").isdigit() for r in rows) else None}
 
 
-def traffic_from_profile(lu_per_launch):
+def traffic_from_profile(spec, lu_per_launch):
     """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2311_05091_gb300", "csrc", "lbm_d2q9.cu")
-    summ = os.path.join(ROOT, "profiles", "d2q9_step_disk1024x5.md")
+    src = os.path.join(ROOT, "paper_2311_05091_gb300", "csrc", spec["kernel_src"])
+    summ = os.path.join(ROOT, "profiles", spec["profile"])
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         kv = {}
@@ -129,39 +150,67 @@ def traffic_from_profile(lu_per_launch):
         return None
 
 
-def oracle_sample(size_nodes, steps, theta=30.0):
-    """Time the FP64 oracle on a square crop of one instance of the workload (single thread)."""
+def make_workload(name, size=None):
+    spec = WORKLOADS[name]
+    n = size or spec["size"]
+    if name == "disk1024x5":
+        from synthetic.workloads import disk_sweep
+        return disk_sweep(n=n, Rs=160.0 * n / 1024, R0=120.0 * n / 1024)
+    from synthetic.workloads import porous_slab
+    return porous_slab(n=n, rmin=10.0 * n / 256, rmax=20.0 * n / 256, slab=32.0 * n / 256)
+
+
+def oracle_sample(wl, steps, cpu_seconds, us_per_node_step):
+    """Time the FP64 oracle (single thread) on a crop of instance 0 of the workload.
+
+    The crop is a square (2D) or cube (3D) at the origin sized so that
+    ``steps`` oracle steps take about ``cpu_seconds``; it keeps the
+    workload's periodicity.  Returns (MLUPS, seconds, description).
+    """
+    import numpy as np
+    d = 2 if wl["lattice"] == "D2Q9" else 3
+    nodes = cpu_seconds / (us_per_node_step * 1e-6 * max(steps, 1))
+    full = wl["nx"]
+    side = int(max(8, min(full, nodes ** (1.0 / d))))
+    if d == 2:
+        side = max(8, side - side % 8)
+        sl = (slice(0, side), slice(0, side))
+    else:
+        sl = (slice(0, side),) * 3
+    phi0 = np.ascontiguousarray(wl["phi0"][0][sl], dtype=np.float64)
+    phi1 = np.ascontiguousarray(wl["phi1"][0][sl], dtype=np.float64)
+    prm = dict(wl["params"][0])
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    np.savez(path, phi0=phi0, phi1=phi1)
+    periodic = tuple(wl["periodic"][:d])
     code = f"""
-import os, sys, time, json, math
+import sys, time, json
 sys.path.insert(0, {ROOT!r})
 import numpy as np
 from oracle import lbm, model
-from synthetic.workloads import disk_sweep
-n = {int(size_nodes)}
-wl = disk_sweep(n=n, Rs=160.0 * n / 1024, R0=120.0 * n / 1024, thetas=({theta},))
-prm = dict(wl["params"][0])
-st = lbm.init_state("D2Q9", wl["phi0"][0].astype(np.float64), wl["phi1"][0].astype(np.float64),
-                    model.Params(**prm), (True, True))
+z = np.load({path!r})
+prm = {prm!r}
+st = lbm.init_state({wl["lattice"]!r}, z["phi0"], z["phi1"], model.Params(**prm), {periodic!r})
 c = model.constants(model.Params(**prm))
 lbm.step(st, c, 1)
 t = time.perf_counter()
 lbm.step(st, c, {int(steps)})
 dt = time.perf_counter() - t
-print(json.dumps({{"seconds": dt, "lu": n * n * {int(steps)}}}))
+print(json.dumps({{"seconds": dt, "lu": int(z["phi0"].size) * {int(steps)}}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    finally:
+        os.unlink(path)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["lu"] / d["seconds"] / 1e6, d["seconds"]
-
-
-def oracle_sample_size(cpu_seconds, steps):
-    """Square crop whose `steps` oracle steps take about cpu_seconds (about 2 us per node-step)."""
-    nodes = cpu_seconds / (2.0e-6 * max(steps, 1))
-    side = int(math.sqrt(max(nodes, 1024)))
-    return max(32, min(1024, side - side % 8))
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    crop = "x".join([str(side)] * d)
+    desc = (f"FP64 oracle, {steps} steps of a {crop} crop at the origin of instance 0 "
+            f"(theta {prm.get('theta_deg', 90.0):g} deg), {res['seconds']:.1f} s, 1 thread")
+    return res["lu"] / res["seconds"] / 1e6, res["seconds"], desc
 
 
 def dist_setup(gpus):
@@ -197,16 +246,18 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    spec = WORKLOADS[args.workload]
+    wl = make_workload(args.workload, args.size)
     total = args.steps + args.warmup
-    side = oracle_sample_size(120.0, total)
-    mlups, secs = oracle_sample(side, args.steps)
+    # a few minutes of oracle work in all, whatever K and W are
+    mlups, secs, desc = oracle_sample(wl, args.steps, 120.0 * args.steps / max(total, 1),
+                                      spec["oracle_us_per_node_step"])
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"FP64 oracle on a {side}x{side} crop of one instance of the 1024^2 disk+droplet "
-                                   f"workload (theta 30 deg); each step one oracle time step of that crop"},
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} steps of a {side}x{side} crop, 1 thread"},
+            "config": {"workload": f"{desc.split(',')[1].strip()} of {wl['name']}; each step one oracle time "
+                                   f"step of that crop"},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if world > 1:
         line["note"] = "rank 0 alone runs the CPU reference"
@@ -223,14 +274,17 @@ def run_gpu(args):
     from paper_2311_05091_gb300.build import build
     build()
     from paper_2311_05091_gb300 import _lbm as L
-    from synthetic.workloads import disk_sweep
 
-    n = args.size
-    wl = disk_sweep(n=n, Rs=160.0 * n / 1024, R0=120.0 * n / 1024)
+    spec = WORKLOADS[args.workload]
+    wl = make_workload(args.workload, args.size)
     nb = len(wl["params"])
-    lu = wl["nx"] * wl["ny"] * nb
+    nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]
+    d = 2 if wl["lattice"] == "D2Q9" else 3
+    nodes = nx * ny * nz
+    lu = nodes * nb
+    lattice = L.LBM_D2Q9 if d == 2 else L.LBM_D3Q19
     stream = torch.cuda.Stream()
-    ctx = L.Context(L.LBM_D2Q9, wl["nx"], wl["ny"], 1, periodic=(True, True, False),
+    ctx = L.Context(lattice, nx, ny, nz, periodic=tuple(wl["periodic"]),
                     batch=[L.lbm_default_params(**p) for p in wl["params"]])
     ctx.set_stream(stream.cuda_stream)
 
@@ -240,7 +294,7 @@ def run_gpu(args):
     h_phi0, h_phi1 = pinned(wl["phi0"].shape), pinned(wl["phi1"].shape)
     h_phi0[...] = wl["phi0"]
     h_phi1[...] = wl["phi1"]
-    o_phi1, o_u, o_p = pinned((nb, n * n)), pinned((nb, 2, n * n)), pinned((nb, n * n))
+    o_phi1, o_u, o_p = pinned((nb, nodes)), pinned((nb, d, nodes)), pinned((nb, nodes))
 
     ctx.set_solid(h_phi0)
     ctx.set_phase(h_phi1)
@@ -254,7 +308,7 @@ def run_gpu(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
     ev0.record(stream)
-    ctx.step(args.steps)          # one step-kernel launch per step
+    ctx.step(args.steps)
     ev1.record(stream)
     ev1.synchronize()
     clk = clocks.stop()
@@ -264,14 +318,14 @@ def run_gpu(args):
     ctx.sync()
     ms = max_over_ranks(world, ms)
     value = world * lu * args.steps / (ms * 1e-3) / 1e6
-    launches = args.steps
+    launches = args.steps * spec["launches_per_step"]
 
-    # cross-check: the same kernel with a CUDA-event pair around every launch
+    # per-kernel device time: CUDA events around each launch of nchk more steps
     nchk = min(args.steps, 500)
     ctx.set_profiling(True)
-    ctx.kernel_time()
+    ctx.kernel_time_split()
     ctx.step(nchk)
-    kernel_ms, nk = ctx.kernel_time()
+    (moment_ms, fused_ms), nk = ctx.kernel_time_split()
     ctx.set_profiling(False)
     ctx.sync()
 
@@ -293,40 +347,50 @@ def run_gpu(args):
     if rank != 0:
         return 0
     peak, peak_kind = peaks()
-    per_launch_ms = ms / args.steps          # timed region / launches (gaps included)
-    achieved = BYTES_PER_LU * lu / (per_launch_ms * 1e-3) / 1e9
-    traffic = traffic_from_profile(lu)
+    step_ms = ms / args.steps
+    if d == 2:
+        # one launch per step: the graph-replayed step time (gaps included) is the launch time
+        kernel_ms = step_ms
+    else:
+        kernel_ms = fused_ms / max(nk, 1)
+    achieved = spec["kernel_bytes_per_lu"] * lu / (kernel_ms * 1e-3) / 1e9
+    traffic = traffic_from_profile(spec, lu)
+    rw = (spec["bytes_per_lu"] / 2) * lu / 1e9
+    cfg = {"workload": wl["name"], "lattice": wl["lattice"], "nx": nx, "ny": ny, "nz": nz, "instances": nb,
+           "thetas": [p["theta_deg"] for p in wl["params"]], "d0": wl["params"][0]["d0"], "W": 4.0,
+           "lu_per_step": lu, "bytes_per_lu": spec["bytes_per_lu"],
+           "l2": f"no flush: each step moves about {2 * rw:.2f} GB through HBM (> 129 MB L2)",
+           "parallelism": f"weak, {world} x independent copies of the workload"}
+    if d == 2:
+        cfg.update(density_ratio=10, viscosity_ratio=10)
+    else:
+        cfg.update(density_ratio=1, viscosity_ratio=1, body_force=wl["params"][0]["body_force"][0],
+                   note=wl["geometry"].note)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["name"], "lattice": "D2Q9", "nx": n, "ny": n, "instances": nb,
-                   "thetas": [p["theta_deg"] for p in wl["params"]], "density_ratio": 10, "viscosity_ratio": 10,
-                   "d0": 0.5, "W": 4.0, "lu_per_step": lu, "bytes_per_lu": BYTES_PER_LU,
-                   "l2": f"no flush: each step reads {lu * 96 / 1e9:.2f} GB and writes {lu * 92 / 1e9:.2f} GB "
-                         f"(> 129 MB L2)",
-                   "parallelism": f"weak, {world} x independent 5-instance batches"},
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "kernel": "d2q9_step", "kernel_ms_per_launch": per_launch_ms, "launches": launches,
-                     "bytes_per_lu": BYTES_PER_LU,
-                     "event_bracketed_ms_per_launch": kernel_ms / max(nk, 1)},
+                     "kernel": spec["kernel"], "kernel_ms_per_launch": kernel_ms,
+                     "kernel_bytes_per_lu": spec["kernel_bytes_per_lu"],
+                     "event_bracketed_ms_per_step": (moment_ms + fused_ms) / max(nk, 1),
+                     "step_achieved_gbs": spec["bytes_per_lu"] * lu / (step_ms * 1e-3) / 1e9,
+                     "step_frac": spec["bytes_per_lu"] * lu / (step_ms * 1e-3) / 1e9 / peak},
         "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": 8 * lu / args.steps,
-                "d2h_bytes_per_step": 16 * lu / args.steps,
+                "d2h_bytes_per_step": (8 + 4 * d) * lu / args.steps,
                 "note": "set_solid + set_phase from pinned host, K steps, get_fields to pinned host"},
         "gpu_launches": launches,
         "clocks": clk,
         "check": {"mass1": obs["mass1"], "umax": obs["umax"], "dp": obs["dp"]},
     }
+    if d == 3:
+        line["roofline"]["moment_pass_ms_per_launch"] = moment_ms / max(nk, 1)
     if world == 1 and not args.no_cpu_baseline:
-        steps = 8
-        side = oracle_sample_size(args.cpu_seconds, steps)
         try:
-            mlups, secs = oracle_sample(side, steps)
-            line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                                    "sample": f"FP64 oracle, {steps} steps of a {side}x{side} crop of one instance "
-                                              f"(theta 30 deg), {secs:.1f} s, 1 thread"}
+            mlups, secs, desc = oracle_sample(wl, 8, args.cpu_seconds, spec["oracle_us_per_node_step"])
+            line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc}
         except Exception as e:   # the GPU number stands on its own
             line["cpu_baseline"] = {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {str(e)[:200]}"}

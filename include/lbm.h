@@ -146,13 +146,19 @@ int lbm_set_stream(lbm_ctx* ctx, void* stream);
  * flight (0 keeps the current value; the D3Q19 kernel ignores it). */
 int lbm_set_launch(lbm_ctx* ctx, int strip, int depth);
 
-/* Kernel timing.  While enabled, every step-kernel launch is bracketed by a
- * pair of CUDA events recorded on the context's stream (CUDA-graph replay is
- * off meanwhile).  lbm_kernel_time synchronises, returns the summed device
- * duration (ms) and the number of launches timed since the last read, and
- * starts a new count.  Outputs may be NULL. */
+/* Kernel timing.  While enabled, every time step is bracketed by CUDA
+ * events recorded on the context's stream, with one more between the D3Q19
+ * moment pass and the fused kernel (CUDA-graph replay is off meanwhile).
+ * lbm_kernel_time synchronises, returns the summed device duration (ms) and
+ * the number of steps timed since the last read, and starts a new count.
+ * Outputs may be NULL. */
 int lbm_set_profiling(lbm_ctx* ctx, int enable);
 int lbm_kernel_time(lbm_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Same timing split per kernel: part_ms[0] the D3Q19 moment pass (0 for
+ * D2Q9), part_ms[1] the fused step kernel, summed over the *steps timed
+ * steps; also starts a new count.  part_ms points to 2 doubles or is NULL. */
+int lbm_kernel_time_split(lbm_ctx* ctx, double* part_ms, int64_t* steps);
 
 /* Copy the solid indicator phi0 (host, nbatch*nz*ny*nx floats) to the device. */
 int lbm_set_solid(lbm_ctx* ctx, const float* phi0_host);

@@ -27,7 +27,7 @@ EXPORTS = [
     "lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy", "lbm_set_stream",
     "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
     "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
-    "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_observables_noalloc",
+    "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_kernel_time_split", "lbm_observables_noalloc",
 ]
 
 
@@ -92,6 +92,7 @@ def library():
         "lbm_set_profiling": (c_int, [P, c_int]),
         "lbm_observables_noalloc": (c_int, [P, P, P, c_int, P, ctypes.c_longlong, P, P]),
         "lbm_kernel_time": (c_int, [P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_int64)]),
+        "lbm_kernel_time_split": (c_int, [P, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_int64)]),
         "lbm_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -258,10 +259,17 @@ def lbm_set_profiling(ctx, enable):
 
 
 def lbm_kernel_time(ctx):
-    """(summed device milliseconds, launches) of the step kernels timed since the last read."""
+    """(summed device milliseconds, steps) of the step kernels timed since the last read."""
     ms, n = c_double(), ctypes.c_int64()
     _check(library().lbm_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(n)), "lbm_kernel_time", ctx)
     return ms.value, n.value
+
+
+def lbm_kernel_time_split(ctx):
+    """((moment-pass ms, fused-kernel ms), steps) timed since the last read."""
+    ms, n = (c_double * 2)(), ctypes.c_int64()
+    _check(library().lbm_kernel_time_split(ctx, ms, ctypes.byref(n)), "lbm_kernel_time_split", ctx)
+    return (ms[0], ms[1]), n.value
 
 
 def lbm_strerror(status) -> str:
@@ -313,5 +321,6 @@ class Context:
     def observables(self, instance=0): return lbm_observables(self.ctx, instance)
     def set_profiling(self, enable): lbm_set_profiling(self.ctx, enable)
     def kernel_time(self): return lbm_kernel_time(self.ctx)
+    def kernel_time_split(self): return lbm_kernel_time_split(self.ctx)
     def contact_angle(self, instance, mode, column, y_c=0.0, disk_radius=0.0):
         return lbm_contact_angle(self.ctx, instance, mode, column, y_c, disk_radius)

@@ -227,9 +227,20 @@ StepArgs step_args(lbm_ctx* c, int from) {
   return a;
 }
 
-cudaError_t launch_step(lbm_ctx* c, int from, bool observe, cudaStream_t s) {
+// One time step.  D3Q19 runs its moment pass first; `mid`, when given, is
+// recorded between the moment pass and the fused kernel (D2Q9: before it).
+cudaError_t launch_step(lbm_ctx* c, int from, bool observe, cudaStream_t s, cudaEvent_t mid = nullptr) {
   const StepArgs a = step_args(c, from);
-  if (c->lattice == LBM_D2Q9) return lbm::launch_d2q9_step(a, c->nbatch, observe, s);
+  if (c->lattice == LBM_D2Q9) {
+    if (mid) cudaEventRecord(mid, s);
+    return lbm::launch_d2q9_step(a, c->nbatch, observe, s);
+  }
+  cudaError_t e = lbm::launch_d3q19_moments(a, c->nbatch, s);
+  if (e != cudaSuccess) return e;
+  if (mid) {
+    e = cudaEventRecord(mid, s);
+    if (e != cudaSuccess) return e;
+  }
   return lbm::launch_d3q19_step(a, c->nbatch, observe, s);
 }
 
@@ -341,17 +352,17 @@ double disk_hmax(double t, double Rs, double S0) {
 // launch one step, bracketed by an event pair when profiling
 int timed_step(lbm_ctx* c, bool observe) {
   if (c->profiling) {
-    while (c->ev.size() < 2 * (c->ev_used + 1)) {
+    while (c->ev.size() < 3 * (c->ev_used + 1)) {
       cudaEvent_t e;
       LBM_CK(c, cudaEventCreate(&e));
       c->ev.push_back(e);
     }
-    LBM_CK(c, cudaEventRecord(c->ev[2 * c->ev_used], c->stream));
+    LBM_CK(c, cudaEventRecord(c->ev[3 * c->ev_used], c->stream));
   }
-  cudaError_t e = launch_step(c, c->cur, observe, c->stream);
+  cudaError_t e = launch_step(c, c->cur, observe, c->stream, c->profiling ? c->ev[3 * c->ev_used + 1] : nullptr);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
   if (c->profiling) {
-    LBM_CK(c, cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream));
+    LBM_CK(c, cudaEventRecord(c->ev[3 * c->ev_used + 2], c->stream));
     ++c->ev_used;
   }
   return LBM_OK;
@@ -545,18 +556,32 @@ int lbm_set_profiling(lbm_ctx* c, int enable) {
   return LBM_OK;
 }
 
-int lbm_kernel_time(lbm_ctx* c, double* total_ms, int64_t* launches) {
+int lbm_kernel_time_split(lbm_ctx* c, double* part_ms, int64_t* steps) {
   if (int s = check_ready(c, false)) return s;
   LBM_CK(c, cudaStreamSynchronize(c->stream));
-  double tot = 0.0;
+  double t0 = 0.0, t1 = 0.0;
   for (size_t k = 0; k < c->ev_used; ++k) {
-    float ms = 0.f;
-    LBM_CK(c, cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
-    tot += ms;
+    float a = 0.f, b = 0.f;
+    LBM_CK(c, cudaEventElapsedTime(&a, c->ev[3 * k], c->ev[3 * k + 1]));
+    LBM_CK(c, cudaEventElapsedTime(&b, c->ev[3 * k + 1], c->ev[3 * k + 2]));
+    t0 += a;
+    t1 += b;
   }
-  if (total_ms) *total_ms = tot;
-  if (launches) *launches = (int64_t)c->ev_used;
+  if (part_ms) {
+    part_ms[0] = t0;
+    part_ms[1] = t1;
+  }
+  if (steps) *steps = (int64_t)c->ev_used;
   c->ev_used = 0;
+  return LBM_OK;
+}
+
+int lbm_kernel_time(lbm_ctx* c, double* total_ms, int64_t* launches) {
+  double part[2] = {0.0, 0.0};
+  int64_t steps = 0;
+  if (int s = lbm_kernel_time_split(c, part, &steps)) return s;
+  if (total_ms) *total_ms = part[0] + part[1];
+  if (launches) *launches = steps;
   return LBM_OK;
 }
 

@@ -695,15 +695,17 @@ cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, fl
   return cudaGetLastError();
 }
 
-cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+cudaError_t launch_d3q19_moments(const StepArgs& a, int nbatch, cudaStream_t s) {
   const int nodes = (int)a.nodes;
   const int vec4 = (nodes & 3) == 0;
   const int per_thread = vec4 ? 4 : 1;
   const int mblocks = (nodes / per_thread + 255) / 256;
   d3q19_moments<<<dim3(mblocks, nbatch), 256, 0, s>>>(a.f_in, a.hist_out, a.mom, nodes, vec4);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
 
+cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   const size_t smem = sizeof(StepSmem3);
   static bool configured = false;   // attribute set once per process (both variants)
   if (!configured) {

@@ -67,6 +67,8 @@ cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaSt
 cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, float* g,
                               float* hist, const InstanceConsts* consts, int nx, int ny, int nz,
                               int per_x, int per_y, int per_z, int nbatch, cudaStream_t s);
+// D3Q19 steps are two launches: the moment pass, then the fused kernel.
+cudaError_t launch_d3q19_moments(const StepArgs& a, int nbatch, cudaStream_t s);
 cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s);
 
 // Observables: deterministic two-pass reduction of one instance.

@@ -33,6 +33,7 @@ __all__ = [
     "sphere_box_droplet",
     "wall_drop_3d",
     "splitmix64",
+    "splitmix64_block",
 ]
 
 
@@ -215,37 +216,117 @@ def random_disks_droplet(n=256, seed=0, W=4.0, ny=None):
     return g, theta
 
 
+def splitmix64_block(seed, start, count):
+    """Draws ``start + 1 .. start + count`` of ``splitmix64(seed)`` as one array.
+
+    The k-th draw of the generator mixes the state ``seed + k * gamma`` (mod
+    2^64), so a block of draws is a vectorised evaluation with the same values.
+    """
+    k = np.arange(start + 1, start + 1 + count, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+
+
 def rsa_spheres(n=256, seed=0, rmin=10.0, rmax=20.0, target_solid=0.4, max_fail=1_000_000):
     """Random sequential addition of non-overlapping spheres with periodic images.
 
     Radii uniform in ``[rmin, rmax]``; stops when the sharp solid fraction
     reaches ``target_solid`` or after ``max_fail`` consecutive rejections.
+    Candidates are drawn in sequence (radius, then x, y, z centre) from
+    ``splitmix64``; blocks of candidates are tested together, which gives the
+    same accepted list as testing them one at a time.
     Returns the list ``[(cx, cy, cz, r), ...]``.
     """
-    u = splitmix64(seed * 104729 + 3)
+    gen_seed = seed * 104729 + 3
     L = float(n)
+    # cell lists: a candidate can only overlap spheres whose centre lies in its
+    # own or one of the 26 neighbouring cells (cell side >= 2 rmax)
+    nc = max(1, int(L // (2.0 * rmax)))
+    use_cells = nc >= 3
+    if not use_cells:
+        nc = 1
+    h = L / nc
+    members = [[] for _ in range(nc ** 3)]
     spheres = []
+    cen = np.empty((0, 3))
+    rad = np.empty(0)
+
+    def cell_of(p):
+        q = np.minimum((p // h).astype(np.int64), nc - 1)
+        return (q[..., 2] * nc + q[..., 1]) * nc + q[..., 0]
+
+    def neighbour_table():
+        if not use_cells:
+            return np.arange(len(rad))[None, :]
+        lists = []
+        for cid in range(nc ** 3):
+            ix, iy, iz = cid % nc, (cid // nc) % nc, cid // (nc * nc)
+            idx = []
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        idx += members[(((iz + dz) % nc) * nc + (iy + dy) % nc) * nc + (ix + dx) % nc]
+            lists.append(idx)
+        width = max(1, max(len(x) for x in lists))
+        tab = np.full((nc ** 3, width), -1, dtype=np.int64)
+        for cid, idx in enumerate(lists):
+            tab[cid, :len(idx)] = idx
+        return tab
+
+    def clear_of(c, r, tab):
+        rows = tab[cell_of(c)] if use_cells else np.broadcast_to(tab, (len(r), tab.shape[1]))
+        if rows.shape[1] == 0:
+            return np.ones(len(r), dtype=bool)
+        valid = rows >= 0
+        safe = np.where(valid, rows, 0)
+        d = np.abs(c[:, None, :] - cen[safe])
+        d = np.minimum(d, L - d)
+        d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+        hit = (d2 < (r[:, None] + rad[safe]) ** 2) & valid
+        return ~np.any(hit, axis=1)
+
     vol = 0.0
     fails = 0
+    drawn = 0
+    B = 8192
+    tab = neighbour_table()
     while vol / L ** 3 < target_solid and fails < max_fail:
-        r = rmin + (rmax - rmin) * u()
-        c = (L * u(), L * u(), L * u())
-        ok = True
-        for (qx, qy, qz, qr) in spheres:
-            d2 = 0.0
-            for a, b in zip(c, (qx, qy, qz)):
-                d = abs(a - b)
-                d = min(d, L - d)
-                d2 += d * d
-            if d2 < (r + qr) ** 2:
-                ok = False
+        u = splitmix64_block(gen_seed, drawn, 4 * B).reshape(B, 4)
+        drawn += 4 * B
+        r = rmin + (rmax - rmin) * u[:, 0]
+        c = L * u[:, 1:]
+        ok = clear_of(c, r, tab) if len(rad) else np.ones(B, dtype=bool)
+        pos = 0
+        while pos < B:
+            nxt = np.flatnonzero(ok[pos:])
+            if nxt.size == 0:
+                if fails + (B - pos) >= max_fail:
+                    return spheres
+                fails += B - pos
                 break
-        if ok:
-            spheres.append((c[0], c[1], c[2], r))
-            vol += 4.0 / 3.0 * math.pi * r ** 3
+            j = pos + int(nxt[0])
+            if fails + (j - pos) >= max_fail:
+                return spheres
             fails = 0
-        else:
-            fails += 1
+            spheres.append((float(c[j, 0]), float(c[j, 1]), float(c[j, 2]), float(r[j])))
+            cen = np.vstack([cen, c[j][None]])
+            rad = np.append(rad, r[j])
+            members[int(cell_of(c[j][None])[0]) if use_cells else 0].append(len(rad) - 1)
+            tab = neighbour_table()
+            vol += 4.0 / 3.0 * math.pi * r[j] ** 3
+            if vol / L ** 3 >= target_solid:
+                return spheres
+            pos = j + 1
+            if pos < B:
+                # later candidates of the block against the new sphere only
+                d = np.abs(c[pos:] - c[j])
+                d = np.minimum(d, L - d)
+                d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+                ok[pos:] &= ~(d2 < (r[pos:] + r[j]) ** 2)
     return spheres
 
 

@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .geometry import cylinder_droplet, wall_droplet
+from .geometry import cylinder_droplet, porous_inlet_slab, wall_droplet
 
 # Disk + droplet on a 1024^2 periodic lattice, contact angle swept over five
 # values, density and viscosity ratio 10 (fluid 1 heavier and more viscous;
@@ -33,3 +33,18 @@ def flat_wall(nx=128, ny=64, wall_rows=8, R=25.0, W=4.0, theta=60.0, d0=0.5):
     return dict(name=f"D2Q9 flat wall {nx}x{ny}, R={R}, theta={theta}", lattice="D2Q9", nx=nx, ny=ny, nz=1,
                 periodic=(True, False, False), phi0=geo.phi0.astype(np.float32)[None],
                 phi1=geo.phi1.astype(np.float32)[None], params=params, geometry=geo)
+
+
+def porous_slab(n=256, seed=0, W=4.0, slab=32.0, rmin=10.0, rmax=20.0, target_solid=0.4, body_force=1e-6):
+    """3D porous run: RSA spheres (radii uniform in [rmin, rmax], sharp solid
+    fraction ``target_solid``) on an n^3 periodic D3Q19 lattice, the
+    non-wetting fluid 1 filling the inlet slab x < ``slab``, contact angle
+    120 deg, body force along x, density and viscosity ratio 1, d0 = 1/3."""
+    geo = porous_inlet_slab(n=n, seed=seed, W=W, slab=slab, rmin=rmin, rmax=rmax, target_solid=target_solid)
+    params = [dict(W=W, M_deg=0.1, theta_deg=120.0, kappa=0.0, sigma=0.01, d0=1.0 / 3.0,
+                   body_force=(body_force, 0.0, 0.0))]
+    return dict(name=f"D3Q19 porous {n}^3 ({geo.note}), inlet slab x<{slab:g}, theta=120, body force "
+                     f"{body_force:g} x, ratios 1, d0=1/3",
+                lattice="D3Q19", nx=n, ny=n, nz=n, periodic=(True, True, True),
+                phi0=geo.phi0.astype(np.float32)[None], phi1=geo.phi1.astype(np.float32)[None],
+                params=params, geometry=geo)
