@@ -49,7 +49,9 @@
  * every later call except lbm_destroy and lbm_last_error returns LBM_ESTATE.
  * Asynchronous failures and divergence (NaN or |u| > 0.5 found by the step
  * that closes each lbm_step call) surface at the next synchronising call
- * (lbm_sync, lbm_get_*, lbm_observables) as LBM_ECUDA / LBM_EDIVERGED.
+ * (lbm_sync, lbm_get_*, lbm_observables) as LBM_ECUDA / LBM_EDIVERGED; a
+ * bounded device wait for an asynchronous tile load that gave up surfaces
+ * there as LBM_ETIMEOUT (the step it belonged to is incomplete).
  */
 #ifndef LBM_H_
 #define LBM_H_
@@ -142,8 +144,12 @@ int lbm_set_stream(lbm_ctx* ctx, void* stream);
 
 /* Launch tuning; results do not depend on it (bitwise).  strip >= 1: rows
  * (D2Q9) or z planes (D3Q19) swept by one CTA of the step kernel.  depth in
- * 1..3: rows of asynchronous global-to-shared copies each D2Q9 CTA keeps in
- * flight (0 keeps the current value; the D3Q19 kernel ignores it). */
+ * 1..3 (0 keeps the current value): D2Q9, rows of asynchronous
+ * global-to-shared copies each CTA keeps in flight (default 1); D3Q19, 1
+ * selects the generic fused kernel (synchronous halo loads), 2 or 3 the
+ * pipelined one (TMA tile loads of the owned columns, asynchronous halo
+ * copies one plane ahead; default 2), which needs nx % 4 == 0 and otherwise
+ * falls back to the generic kernel. */
 int lbm_set_launch(lbm_ctx* ctx, int strip, int depth);
 
 /* Kernel timing.  While enabled, every time step is bracketed by CUDA

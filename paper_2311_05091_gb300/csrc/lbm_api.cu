@@ -53,6 +53,9 @@ struct lbm_ctx {
   float* phi0 = nullptr;
   float* p = nullptr;
   float* mom = nullptr;        // D3Q19 moment-pass scratch
+  // D3Q19 tensor maps of the step's input buffers, one set per starting buffer
+  alignas(64) unsigned char d3maps[2][512];
+  bool d3maps_ok = false;
   unsigned int* dflag = nullptr;
   double* dpart = nullptr;
   double* dobs = nullptr;
@@ -241,7 +244,9 @@ cudaError_t launch_step(lbm_ctx* c, int from, bool observe, cudaStream_t s, cuda
     e = cudaEventRecord(mid, s);
     if (e != cudaSuccess) return e;
   }
-  return lbm::launch_d3q19_step(a, c->nbatch, observe, s);
+  // depth 1 selects the generic kernel; otherwise the pipelined one where its tensor maps exist
+  const void* maps = (c->d3maps_ok && c->depth != 1) ? c->d3maps[from] : nullptr;
+  return lbm::launch_d3q19_step(a, c->nbatch, observe, s, maps);
 }
 
 int ensure_graph(lbm_ctx* c, int from) {
@@ -277,6 +282,8 @@ int check_flag(lbm_ctx* c) {
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   if (flag) {
     LBM_CK(c, cudaMemsetAsync(c->dflag, 0, sizeof(unsigned int), c->stream));
+    if (flag & 2u)
+      return set_err(c, LBM_ETIMEOUT, "a bounded wait for an asynchronous tile load gave up; the step is incomplete");
     return set_err(c, LBM_EDIVERGED, "divergence: NaN or |u| > 0.5 at the last observed step");
   }
   return LBM_OK;
@@ -434,6 +441,7 @@ int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_m
     }
   }
   c->strip = default_strip(c);
+  c->depth = is3d ? 2 : 1;
   const size_t pop = sizeof(float) * (size_t)c->q * nodes * nbatch;
   const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * nodes * nbatch;
   const size_t fld = sizeof(float) * (size_t)nodes * nbatch;
@@ -456,6 +464,13 @@ int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_m
     e = cudaMemcpy(c->dconsts, c->hconsts.data(), sizeof(InstanceConsts) * nbatch, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->dflag, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(c->p, 0, fld);
+  if (e == cudaSuccess && is3d && lbm::d3q19_maps_bytes() <= sizeof(c->d3maps[0])) {
+    int r = 0;
+    for (int i = 0; i < 2 && r == 0; ++i)
+      r = lbm::build_d3q19_maps(c->g[i], c->mom, c->hist[i], nx, ny, nz, nbatch, c->d3maps[i]);
+    if (r < 0) e = cudaErrorInvalidValue;   // the driver refused a tensor map
+    c->d3maps_ok = r == 0;
+  }
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? LBM_ENOMEM : LBM_ECUDA;
     set_err(nullptr, code, "device set-up failed: %s", cudaGetErrorString(e));

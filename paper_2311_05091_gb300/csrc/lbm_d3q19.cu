@@ -37,6 +37,10 @@
 // second read of phi1 (4 B).
 //
 // The NS rest population is stored minus the constant rho_0 of lambda_0.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
 #include <algorithm>
 
 #include "lbm_internal.cuh"
@@ -259,7 +263,349 @@ __global__ void __launch_bounds__(256) d3q19_moments(const float* __restrict__ f
 }
 
 // ---------------------------------------------------------------------------
-// fused step
+// per-node update shared by both fused kernels
+// ---------------------------------------------------------------------------
+// Inputs of one node that do not come from a stencil: its NS populations, the
+// first moment j of its CH populations and its previous-step history.
+struct OwnIn {
+  float g[Q];
+  float jx, jy, jz;
+  float php, upx, upy, upz, spx, spy, spz;
+};
+
+// Ring planes (z-1, z, z+1) around the node: phi0 / phi1 on the two-halo tile
+// (index i2, row stride sw2), mubar_1 and the products on the one-halo tile
+// (index i1, row stride sw1).
+struct Rings {
+  const float* p0[3];
+  const float* p1[3];
+  int i2, sw2;
+  const float* mu[3];
+  const float* ac[3][3];   // [product][plane]
+  int i1, sw1;
+};
+
+struct Outs {
+  const float* f_in;   // instance base, read by the general CH path
+  float* f_out;
+  float* g_out;
+  float* h_out;
+  float* p_out;
+  unsigned int* flag;
+  int nx, ny, nz, per_x, per_y, per_z, nodes, plane;
+};
+
+template <bool OBS>
+__device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings& R, const OwnIn& in,
+                                            const Outs& o, int x, int y, int z) {
+  const int nx = o.nx, ny = o.ny, nz = o.nz, nodes = o.nodes, plane = o.plane;
+  const int node = z * plane + y * nx + x;
+  const float cs2 = k.cs2, cs4 = k.cs4;
+  const int i2 = R.i2, s2 = R.sw2, i1 = R.i1, s1 = R.sw1;
+
+  // stencils of phi0, phi1 and mubar_1, products
+  const float ph0 = R.p0[1][i2], ph1 = R.p1[1][i2], ph2 = 1.f - ph0 - ph1;
+  const float g0x = dgrad<0>(R.p0[0], R.p0[1], R.p0[2], i2, s2), g0y = dgrad<1>(R.p0[0], R.p0[1], R.p0[2], i2, s2),
+              g0z = dgrad<2>(R.p0[0], R.p0[1], R.p0[2], i2, s2);
+  const float g1x = dgrad<0>(R.p1[0], R.p1[1], R.p1[2], i2, s2), g1y = dgrad<1>(R.p1[0], R.p1[1], R.p1[2], i2, s2),
+              g1z = dgrad<2>(R.p1[0], R.p1[1], R.p1[2], i2, s2);
+  float mu0, mu1, mu2;
+  chem_pot(k, ph0, ph1, lap3(R.p0[0], R.p0[1], R.p0[2], i2, s2), lap3(R.p1[0], R.p1[1], R.p1[2], i2, s2), mu0,
+           mu1, mu2);
+  const float d02 = mu0 - mu2, d12 = mu1 - mu2;
+  const float mub = R.mu[1][i1];
+  const float gmx = dgrad<0>(R.mu[0], R.mu[1], R.mu[2], i1, s1), gmy = dgrad<1>(R.mu[0], R.mu[1], R.mu[2], i1, s1),
+              gmz = dgrad<2>(R.mu[0], R.mu[1], R.mu[2], i1, s1);
+  // correction force F_c,b = 1/2 sum_a d_a (S_a u_b - u_a S_b), products A_xy, A_xz, A_yz
+  const float dAxy_x = dgrad<0>(R.ac[0][0], R.ac[0][1], R.ac[0][2], i1, s1);
+  const float dAxy_y = dgrad<1>(R.ac[0][0], R.ac[0][1], R.ac[0][2], i1, s1);
+  const float dAxz_x = dgrad<0>(R.ac[1][0], R.ac[1][1], R.ac[1][2], i1, s1);
+  const float dAxz_z = dgrad<2>(R.ac[1][0], R.ac[1][1], R.ac[1][2], i1, s1);
+  const float dAyz_y = dgrad<1>(R.ac[2][0], R.ac[2][1], R.ac[2][2], i1, s1);
+  const float dAyz_z = dgrad<2>(R.ac[2][0], R.ac[2][1], R.ac[2][2], i1, s1);
+  const float Fcx = -0.5f * (dAxy_y + dAxz_z);
+  const float Fcy = 0.5f * (dAxy_x - dAyz_z);
+  const float Fcz = 0.5f * (dAxz_x + dAyz_y);
+
+  const float php = in.php, upx = in.upx, upy = in.upy, upz = in.upz;
+  const float spx = in.spx, spy = in.spy, spz = in.spz;
+
+  // degenerate mobility, flux S (frozen phi0), mixture properties
+  const float fdeg = ph1 * (1.f - ph1) * (1.f - ph0);
+  const float mob = k.M_cst + k.M_deg * fdeg;
+  const float sfac = (k.rho1 - k.rho2) * mob * k.inv_gam1;
+  const float Sx = sfac * gmx, Sy = sfac * gmy, Sz = sfac * gmz;
+  const float rho = k.rho0 * ph0 + k.rho1 * ph1 + k.rho2 * ph2;
+  const float grx = (k.rho0 - k.rho2) * g0x + (k.rho1 - k.rho2) * g1x;
+  const float gry = (k.rho0 - k.rho2) * g0y + (k.rho1 - k.rho2) * g1y;
+  const float grz = (k.rho0 - k.rho2) * g0z + (k.rho1 - k.rho2) * g1z;
+  const float muv = k.mu0 * ph0 + k.mu1 * ph1 + k.mu2 * ph2;
+
+  // F = F_s + F_b + F_c with F_s = (mu0 - mu2) grad phi0 + (mu1 - mu2) grad phi1
+  const float one_m0 = 1.f - ph0;
+  const float Fx = d02 * g0x + d12 * g1x + one_m0 * k.bx + Fcx;
+  const float Fy = d02 * g0y + d12 * g1y + one_m0 * k.by + Fcy;
+  const float Fz = d02 * g0z + d12 * g1z + one_m0 * k.bz + Fcz;
+
+  // NS moments
+  const float* g = in.g;
+  float sum_nz = 0.f, mx = 0.f, my = 0.f, mz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+  float ex = 0.f, ey = 0.f, ez = 0.f, bxm = 0.f, bym = 0.f, bzm = 0.f;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int cx = CX(i), cy = CY(i), cz = CZ(i);
+    const float v = g[i];
+    sum_nz += v;
+    if (cx) mx += cx > 0 ? v : -v;
+    if (cy) my += cy > 0 ? v : -v;
+    if (cz) mz += cz > 0 ? v : -v;
+    if (cx && cy) pxy += cx * cy > 0 ? v : -v;
+    if (cx && cz) pxz += cx * cz > 0 ? v : -v;
+    if (cy && cz) pyz += cy * cz > 0 ? v : -v;
+    // third-order sums: sum c_a (c_b^2 + c_c^2) g and sum c_a (c_b^2 - c_c^2) g (cyclic a, b, c)
+    if (cx && (cy || cz)) {
+      ex += cx > 0 ? v : -v;
+      bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v;
+    }
+    if (cy && (cz || cx)) {
+      ey += cy > 0 ? v : -v;
+      bym += ((cz ? 1 : -1) * cy > 0) ? v : -v;
+    }
+    if (cz && (cx || cy)) {
+      ez += cz > 0 ? v : -v;
+      bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v;
+    }
+  }
+
+  // velocity with the solid penalisation force (u_w = 0)
+  const float inv_rho = __frcp_rn(rho);
+  const float usx = (mx + 0.5f * Fx) * inv_rho;
+  const float usy = (my + 0.5f * Fy) * inv_rho;
+  const float usz = (mz + 0.5f * Fz) * inv_rho;
+  const float damp = 1.f - 0.5f * ph0;
+  const float ux = usx * damp, uy = usy * damp, uz = usz * damp;
+  const float Ftx = Fx - ph0 * rho * usx, Fty = Fy - ph0 * rho * usy, Ftz = Fz - ph0 * rho * usz;
+
+  // local viscous rates (s0 = s4 = s2a)
+  const float om = fmaxf(one_m0, kOneMinusPhi0Floor);
+  const float ra = rho * om * k.a2a, rb = rho * om * k.a2b;
+  const float s2a = __fdividef(ra, 0.5f * ra + muv);
+  const float s2b = __fdividef(rb, 0.5f * rb + muv);
+  const float inv_s2a = 0.5f + __fdividef(muv, ra);
+
+  // pressure (Sec. 3)
+  const float udg = ux * grx + uy * gry + uz * grz;
+  const float q = (rho * ux - Sx) * ux + (rho * uy - Sy) * uy + (rho * uz - Sz) * uz;
+  const float rhop = k.rho0 * ph0 + k.rho1 * php + k.rho2 * (1.f - ph0 - php);
+  const float qp = (rhop * upx - spx) * upx + (rhop * upy - spy) * upy + (rhop * upz - spz) * upz;
+  const float H = k.Kp * ((k.h0 - k.h2) * inv_s2a + k.h3);
+  const float p = k.pf * (sum_nz + (0.5f + H) * udg - k.wq * q + 0.5f * k.Kp * (q - qp));
+
+  // push destinations; interior nodes use fixed offsets
+  const bool edge = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
+  auto store = [&](float* __restrict__ out, int i, float v) {
+    const int cx = CX(i), cy = CY(i), cz = CZ(i);
+    if (!edge) {
+      out[i * nodes + node + cz * plane + cy * nx + cx] = v;
+      return;
+    }
+    int xd = x + cx, yd = y + cy, zd = z + cz;
+    bool bb = false;
+    if (xd < 0 || xd >= nx) {
+      if (o.per_x) xd = xd < 0 ? xd + nx : xd - nx;
+      else bb = true;
+    }
+    if (yd < 0 || yd >= ny) {
+      if (o.per_y) yd = yd < 0 ? yd + ny : yd - ny;
+      else bb = true;
+    }
+    if (zd < 0 || zd >= nz) {
+      if (o.per_z) zd = zd < 0 ? zd + nz : zd - nz;
+      else bb = true;
+    }
+    const int dst = bb ? OPP(i) * nodes + node : i * nodes + (zd * ny + yd) * nx + xd;
+    out[dst] = v;
+  };
+
+  // ---- NS collision: g* = (1 - s2a) g + w_i X_i (see the file header) ----
+  {
+    const float om2a = 1.f - 0.5f * s2a;
+    // equilibrium second moments e_ab and the force moment M^2F_ab (Sec. 3)
+    const float exx = rho * ux * ux - Sx * ux, eyy = rho * uy * uy - Sy * uy, ezz = rho * uz * uz - Sz * uz;
+    const float exy = rho * ux * uy - 0.5f * (Sx * uy + ux * Sy);
+    const float exz = rho * ux * uz - 0.5f * (Sx * uz + ux * Sz);
+    const float eyz = rho * uy * uz - 0.5f * (Sy * uz + uy * Sz);
+    const float dSxx = Sx * ux - spx * upx, dSyy = Sy * uy - spy * upy, dSzz = Sz * uz - spz * upz;
+    const float dSxy = 0.5f * (Sx * uy + ux * Sy) - 0.5f * (spx * upy + upx * spy);
+    const float dSxz = 0.5f * (Sx * uz + ux * Sz) - 0.5f * (spx * upz + upx * spz);
+    const float dSyz = 0.5f * (Sy * uz + uy * Sz) - 0.5f * (spy * upz + upy * spz);
+    const float iso = (1.f - 3.f * cs2) * udg;
+    const float Mxx = 2.f * ux * Fx - dSxx + 2.f * cs2 * ux * grx + iso;
+    const float Myy = 2.f * uy * Fy - dSyy + 2.f * cs2 * uy * gry + iso;
+    const float Mzz = 2.f * uz * Fz - dSzz + 2.f * cs2 * uz * grz + iso;
+    const float Mxy = ux * Fy + Fx * uy - dSxy + cs2 * (ux * gry + grx * uy);
+    const float Mxz = ux * Fz + Fx * uz - dSxz + cs2 * (ux * grz + grx * uz);
+    const float Myz = uy * Fz + Fy * uz - dSyz + cs2 * (uy * grz + gry * uz);
+    const float i2n = __frcp_rn(cs2 - cs4), ic2 = __frcp_rn(cs2), ic4 = __frcp_rn(cs4);
+    const float Dx = (s2a * exx + om2a * Mxx) * i2n;
+    const float Dy = (s2a * eyy + om2a * Myy) * i2n;
+    const float Dz = (s2a * ezz + om2a * Mzz) * i2n;
+    const float base = s2a * p * ic2 + om2a * udg - cs2 * (Dx + Dy + Dz);
+    const float d1 = k.s1n - s2a;
+    const float Vx = (s2a * rho * ux + om2a * Ftx - d1 * (mx - rho * ux + 0.5f * Ftx)) * ic2;
+    const float Vy = (s2a * rho * uy + om2a * Fty - d1 * (my - rho * uy + 0.5f * Fty)) * ic2;
+    const float Vz = (s2a * rho * uz + om2a * Ftz - d1 * (mz - rho * uz + 0.5f * Ftz)) * ic2;
+    const float db = s2b - s2a;
+    const float Oxy = (s2a * exy + om2a * Mxy - db * (pxy - exy + 0.5f * Mxy)) * ic4;
+    const float Oxz = (s2a * exz + om2a * Mxz - db * (pxz - exz + 0.5f * Mxz)) * ic4;
+    const float Oyz = (s2a * eyz + om2a * Myz - db * (pyz - eyz + 0.5f * Myz)) * ic4;
+    // third-order group: T_a = (s3 - s2a) m_A,a / |A|^2, U_a = (s3 - s2a) m_B,a / |B|^2
+    const float d3 = k.s3n - s2a;
+    const float iB = __frcp_rn(2.f * cs4), iA = __frcp_rn(2.f * cs4 * (1.f - 2.f * cs2));
+    const float k3 = 1.f - 2.f * cs2;
+    const float Tx = d3 * (ex - 2.f * cs2 * mx) * iA, Ty = d3 * (ey - 2.f * cs2 * my) * iA,
+                Tz = d3 * (ez - 2.f * cs2 * mz) * iA;
+    const float Ux = d3 * bxm * iB, Uy = d3 * bym * iB, Uz = d3 * bzm * iB;
+    const float Px = k3 * Tx + Ux, Qx = k3 * Tx - Ux;   // edge factors per axis: B_a = +c_a or -c_a
+    const float Py = k3 * Ty + Uy, Qy = k3 * Ty - Uy;
+    const float Pz = k3 * Tz + Uz, Qz = k3 * Tz - Uz;
+    const float om1 = 1.f - s2a;
+    store(o.g_out, 0, om1 * g[0] + k.w0 * base - s2a * p * ic2);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int cx = CX(i), cy = CY(i), cz = CZ(i);
+      float X = base;
+      if (cx) X += cx > 0 ? Dx + Vx : Dx - Vx;
+      if (cy) X += cy > 0 ? Dy + Vy : Dy - Vy;
+      if (cz) X += cz > 0 ? Dz + Vz : Dz - Vz;
+      if (cx && cy) X += cx * cy > 0 ? Oxy : -Oxy;
+      if (cx && cz) X += cx * cz > 0 ? Oxz : -Oxz;
+      if (cy && cz) X += cy * cz > 0 ? Oyz : -Oyz;
+      if (i < 7) {
+        // axis: A_a(c) = -2 cs2 c_a, B_a(c) = 0
+        const float T = cx ? Tx : (cy ? Ty : Tz);
+        const int c = cx + cy + cz;
+        X += c > 0 ? 2.f * cs2 * T : -2.f * cs2 * T;
+      } else {
+        // edge: -c_a [(1 - 2 cs2) T_a + B_a U_a / c_a] over its two axes
+        if (cx) { const float e = cy ? Px : Qx; X -= cx > 0 ? e : -e; }
+        if (cy) { const float e = cz ? Py : Qy; X -= cy > 0 ? e : -e; }
+        if (cz) { const float e = cx ? Pz : Qz; X -= cz > 0 ? e : -e; }
+      }
+      store(o.g_out, i, om1 * g[i] + weight(k, i) * X);
+    }
+  }
+
+  // ---- CH collision ----
+  {
+    const float emb = k.eta * mub;
+    const float corr = k.corr_scale * (1.f - fdeg);
+    // first moment of R: d_t(phi1 u) + cs2 corr eta grad mubar
+    const float Rx = (ph1 * ux - php * upx) + cs2 * corr * k.eta * gmx;
+    const float Ry = (ph1 * uy - php * upy) + cs2 * corr * k.eta * gmy;
+    const float Rz = (ph1 * uz - php * upz) + cs2 * corr * k.eta * gmz;
+    const float ic2 = __frcp_rn(cs2);
+    if (k.ch_fast != 0.f) {
+      // f* = f^eq + R/2 - (s1 - 1) P1 v: only j = sum c f enters
+      const float jx = in.jx, jy = in.jy, jz = in.jz;
+      const float ax = (ph1 * ux + (1.f - k.s1c) * (jx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx) * ic2;
+      const float ay = (ph1 * uy + (1.f - k.s1c) * (jy - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry) * ic2;
+      const float az = (ph1 * uz + (1.f - k.s1c) * (jz - ph1 * uz) + (1.f - 0.5f * k.s1c) * Rz) * ic2;
+      float rest = ph1;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int cx = CX(i), cy = CY(i), cz = CZ(i);
+        float s = emb;
+        if (cx) s += cx > 0 ? ax : -ax;
+        if (cy) s += cy > 0 ? ay : -ay;
+        if (cz) s += cz > 0 ? az : -az;
+        const float v = weight(k, i) * s;
+        rest -= v;
+        store(o.f_out, i, v);
+      }
+      store(o.f_out, 0, rest);   // the rest population closes the zeroth moment
+    } else {
+      float f[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = o.f_in[i * nodes + node];
+      float jx = 0.f, jy = 0.f, jz = 0.f, qxx = 0.f, qyy = 0.f, qzz = 0.f, qxy = 0.f, qxz = 0.f, qyz = 0.f;
+      float ex = 0.f, ey = 0.f, ez = 0.f, bxm = 0.f, bym = 0.f, bzm = 0.f;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int cx = CX(i), cy = CY(i), cz = CZ(i);
+        const float v = f[i];
+        if (cx) { jx += cx > 0 ? v : -v; qxx += v; }
+        if (cy) { jy += cy > 0 ? v : -v; qyy += v; }
+        if (cz) { jz += cz > 0 ? v : -v; qzz += v; }
+        if (cx && cy) qxy += cx * cy > 0 ? v : -v;
+        if (cx && cz) qxz += cx * cz > 0 ? v : -v;
+        if (cy && cz) qyz += cy * cz > 0 ? v : -v;
+        if (cx && (cy || cz)) { ex += cx > 0 ? v : -v; bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v; }
+        if (cy && (cz || cx)) { ey += cy > 0 ? v : -v; bym += ((cz ? 1 : -1) * cy > 0) ? v : -v; }
+        if (cz && (cx || cy)) { ez += cz > 0 ? v : -v; bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v; }
+      }
+      const float s4 = k.s4c, om4 = 1.f - s4, oh4 = 1.f - 0.5f * s4;
+      const float d1 = (k.s1c - s4) * ic2;
+      const float m1x = jx - ph1 * ux + 0.5f * Rx, m1y = jy - ph1 * uy + 0.5f * Ry, m1z = jz - ph1 * uz + 0.5f * Rz;
+      const float d2a = (k.s2ac - s4) * __frcp_rn(cs2 - cs4);
+      const float m2x = qxx - cs2 * emb, m2y = qyy - cs2 * emb, m2z = qzz - cs2 * emb;
+      const float d2b = (k.s2bc - s4) * __frcp_rn(cs4);
+      const float d3 = k.s3c - s4;
+      const float iB = __frcp_rn(2.f * cs4), iA = __frcp_rn(2.f * cs4 * (1.f - 2.f * cs2));
+      const float k3 = 1.f - 2.f * cs2;
+      const float Tx = d3 * (ex - 2.f * cs2 * jx) * iA, Ty = d3 * (ey - 2.f * cs2 * jy) * iA,
+                  Tz = d3 * (ez - 2.f * cs2 * jz) * iA;
+      const float Ux = d3 * bxm * iB, Uy = d3 * bym * iB, Uz = d3 * bzm * iB;
+      const float Px = k3 * Tx + Ux, Qx = k3 * Tx - Ux;
+      const float Py = k3 * Ty + Uy, Qy = k3 * Ty - Uy;
+      const float Pz = k3 * Tz + Uz, Qz = k3 * Tz - Uz;
+      const float p2 = -cs2 * d2a * (m2x + m2y + m2z);   // c-independent part of the P2a term
+      // rest population: f^eq_0 = phi1 + (w0 - 1) eta mubar, R_0 = 0
+      store(o.f_out, 0, om4 * f[0] + s4 * (ph1 + (k.w0 - 1.f) * emb) - k.w0 * p2);
+      const float ux1 = ph1 * ux * ic2, uy1 = ph1 * uy * ic2, uz1 = ph1 * uz * ic2;
+      const float rx = Rx * ic2, ry = Ry * ic2, rz = Rz * ic2;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int cx = CX(i), cy = CY(i), cz = CZ(i);
+        // f^eq_i / w_i = eta mubar + c.phi u / cs2;  R_i / w_i = c.R / cs2
+        float feq = emb, Rc = 0.f, L = p2;
+        if (cx) { feq += cx > 0 ? ux1 : -ux1; Rc += cx > 0 ? rx : -rx; L += (cx > 0 ? m1x : -m1x) * d1 + d2a * m2x; }
+        if (cy) { feq += cy > 0 ? uy1 : -uy1; Rc += cy > 0 ? ry : -ry; L += (cy > 0 ? m1y : -m1y) * d1 + d2a * m2y; }
+        if (cz) { feq += cz > 0 ? uz1 : -uz1; Rc += cz > 0 ? rz : -rz; L += (cz > 0 ? m1z : -m1z) * d1 + d2a * m2z; }
+        if (cx && cy) L += (cx * cy > 0 ? qxy : -qxy) * d2b;
+        if (cx && cz) L += (cx * cz > 0 ? qxz : -qxz) * d2b;
+        if (cy && cz) L += (cy * cz > 0 ? qyz : -qyz) * d2b;
+        if (i < 7) {
+          const float T = cx ? Tx : (cy ? Ty : Tz);
+          const int c = cx + cy + cz;
+          L -= c > 0 ? 2.f * cs2 * T : -2.f * cs2 * T;
+        } else {
+          if (cx) { const float e = cy ? Px : Qx; L += cx > 0 ? e : -e; }
+          if (cy) { const float e = cz ? Py : Qy; L += cy > 0 ? e : -e; }
+          if (cz) { const float e = cx ? Pz : Qz; L += cz > 0 ? e : -e; }
+        }
+        const float w = weight(k, i);
+        store(o.f_out, i, om4 * f[i] + w * (s4 * feq + oh4 * Rc - L));
+      }
+    }
+  }
+
+  // history of this step (phi1 was written by the moment pass)
+  o.h_out[nodes + node] = ux;
+  o.h_out[2 * nodes + node] = uy;
+  o.h_out[3 * nodes + node] = uz;
+  o.h_out[4 * nodes + node] = Sx;
+  o.h_out[5 * nodes + node] = Sy;
+  o.h_out[6 * nodes + node] = Sz;
+  if (OBS) {
+    o.p_out[node] = p;
+    const float u2 = ux * ux + uy * uy + uz * uz;
+    if (!(u2 <= 0.25f) || !(fabsf(ph1) < 1e30f)) atomicOr(o.flag, 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused step, generic form (any nx): synchronous loads into the rings
 // ---------------------------------------------------------------------------
 struct StepSmem3 {
   float phi1[RP][N2];
@@ -271,7 +617,7 @@ struct StepSmem3 {
 
 template <bool OBS>
 __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   StepSmem3& S = *reinterpret_cast<StepSmem3*>(smem_raw);
 
   const int t = threadIdx.x;
@@ -290,15 +636,20 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   if (t < (int)(sizeof(InstanceConsts) / 4))
     reinterpret_cast<float*>(&S.k)[t] = reinterpret_cast<const float*>(a.consts + b)[t];
 
-  const float* __restrict__ f_in = a.f_in + (long long)b * Q * nodes;
   const float* __restrict__ g_in = a.g_in + (long long)b * Q * nodes;
   const float* __restrict__ p0_in = a.phi0 + (long long)b * nodes;
   const float* __restrict__ h_in = a.hist_in + (long long)b * NH * nodes;
-  float* __restrict__ f_out = a.f_out + (long long)b * Q * nodes;
-  float* __restrict__ g_out = a.g_out + (long long)b * Q * nodes;
-  float* __restrict__ h_out = a.hist_out + (long long)b * NH * nodes;
-  const float* __restrict__ phi1_now = h_out;   // written by the moment pass of this step
+  const float* __restrict__ phi1_now = a.hist_out + (long long)b * NH * nodes;   // moment pass of this step
   const float* __restrict__ j_in = a.mom + (long long)b * 3 * nodes;
+  Outs o;
+  o.f_in = a.f_in + (long long)b * Q * nodes;
+  o.f_out = a.f_out + (long long)b * Q * nodes;
+  o.g_out = a.g_out + (long long)b * Q * nodes;
+  o.h_out = a.hist_out + (long long)b * NH * nodes;
+  o.p_out = a.p_out + (long long)b * nodes;
+  o.flag = a.flag;
+  o.nx = nx; o.ny = ny; o.nz = nz; o.per_x = per_x; o.per_y = per_y; o.per_z = per_z;
+  o.nodes = nodes; o.plane = plane;
 
   // phi0 / phi1 of logical plane zl on the two-halo tile into ring slot sl
   auto load_phi = [&](int zl, int sl) {
@@ -307,9 +658,9 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
       const int px = p % HX2, py = p / HX2;
       const int xl = x0 - 2 + px, yl = y0 - 2 + py;
       if (xl > nx + 1 || yl > ny + 1) continue;   // beyond what the last real column needs
-      const int o = zo + wrap_or_mirror(yl, ny, per_y) * nx + wrap_or_mirror(xl, nx, per_x);
-      S.phi1[sl][p] = phi1_now[o];
-      S.phi0[sl][p] = p0_in[o];
+      const int off = zo + wrap_or_mirror(yl, ny, per_y) * nx + wrap_or_mirror(xl, nx, per_x);
+      S.phi1[sl][p] = phi1_now[off];
+      S.phi0[sl][p] = p0_in[off];
     }
   };
   // antisymmetric products of the previous step's S and u on the one-halo tile
@@ -319,9 +670,9 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
       const int px = p % HX1, py = p / HX1;
       const int xl = x0 - 1 + px, yl = y0 - 1 + py;
       if (xl > nx || yl > ny) continue;
-      const int o = zo + wrap_or_mirror(yl, ny, per_y) * nx + wrap_or_mirror(xl, nx, per_x);
-      const float ux = h_in[nodes + o], uy = h_in[2 * nodes + o], uz = h_in[3 * nodes + o];
-      const float sx = h_in[4 * nodes + o], sy = h_in[5 * nodes + o], sz = h_in[6 * nodes + o];
+      const int off = zo + wrap_or_mirror(yl, ny, per_y) * nx + wrap_or_mirror(xl, nx, per_x);
+      const float ux = h_in[nodes + off], uy = h_in[2 * nodes + off], uz = h_in[3 * nodes + off];
+      const float sx = h_in[4 * nodes + off], sy = h_in[5 * nodes + off], sz = h_in[6 * nodes + off];
       S.acor[sl][0][p] = sx * uy - ux * sy;
       S.acor[sl][1][p] = sx * uz - ux * sz;
       S.acor[sl][2][p] = sy * uz - uy * sz;
@@ -329,7 +680,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   };
   const InstanceConsts& k = S.k;
   // mubar_1 of logical plane zl on the one-halo tile; phi ring slots of zl-1, zl, zl+1
-  auto calc_mub = [&](int zl, int rm, int r0, int rp, int sl) {
+  auto calc_mub = [&](int rm, int r0, int rp, int sl) {
     for (int p = t; p < N1; p += NT) {
       const int px = p % HX1, py = p / HX1;
       if (x0 - 1 + px > nx || y0 - 1 + py > ny) continue;
@@ -348,8 +699,8 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   load_hist(zs - 1, ring(zs - 1, RM));
   load_hist(zs, ring(zs, RM));
   __syncthreads();
-  calc_mub(zs - 1, ring(zs - 2, RP), ring(zs - 1, RP), ring(zs, RP), ring(zs - 1, RM));
-  calc_mub(zs, ring(zs - 1, RP), ring(zs, RP), ring(zs + 1, RP), ring(zs, RM));
+  calc_mub(ring(zs - 2, RP), ring(zs - 1, RP), ring(zs, RP), ring(zs - 1, RM));
+  calc_mub(ring(zs - 1, RP), ring(zs, RP), ring(zs + 1, RP), ring(zs, RM));
 
   const int x = x0 + tx, y = y0 + ty;
   const bool own = x < nx && y < ny;
@@ -358,329 +709,331 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
     load_phi(z + 2, ring(z + 2, RP));
     load_hist(z + 1, ring(z + 1, RM));
     __syncthreads();
-    calc_mub(z + 1, ring(z, RP), ring(z + 1, RP), ring(z + 2, RP), ring(z + 1, RM));
+    calc_mub(ring(z, RP), ring(z + 1, RP), ring(z + 2, RP), ring(z + 1, RM));
     __syncthreads();
     if (!own) continue;
 
     const int node = z * plane + y * nx + x;
-    const float cs2 = k.cs2, cs4 = k.cs4;
-    const int rpm = ring(z - 1, RP), rp0 = ring(z, RP), rpp = ring(z + 1, RP);
-    const int rmm = ring(z - 1, RM), rm0 = ring(z, RM), rmp = ring(z + 1, RM);
-    const int i2 = (ty + 2) * HX2 + (tx + 2);
-    const int i1 = (ty + 1) * HX1 + (tx + 1);
-
-    // stencils of phi0, phi1 (two-halo ring) and mubar_1, products (one-halo ring)
-    const float* A0m = S.phi0[rpm];
-    const float* A00 = S.phi0[rp0];
-    const float* A0p = S.phi0[rpp];
-    const float* A1m = S.phi1[rpm];
-    const float* A10 = S.phi1[rp0];
-    const float* A1p = S.phi1[rpp];
-    const float ph0 = A00[i2], ph1 = A10[i2], ph2 = 1.f - ph0 - ph1;
-    const float g0x = dgrad<0>(A0m, A00, A0p, i2, HX2), g0y = dgrad<1>(A0m, A00, A0p, i2, HX2),
-                g0z = dgrad<2>(A0m, A00, A0p, i2, HX2);
-    const float g1x = dgrad<0>(A1m, A10, A1p, i2, HX2), g1y = dgrad<1>(A1m, A10, A1p, i2, HX2),
-                g1z = dgrad<2>(A1m, A10, A1p, i2, HX2);
-    float mu0, mu1, mu2;
-    chem_pot(k, ph0, ph1, lap3(A0m, A00, A0p, i2, HX2), lap3(A1m, A10, A1p, i2, HX2), mu0, mu1, mu2);
-    const float d02 = mu0 - mu2, d12 = mu1 - mu2;
-    const float* Mm = S.mub[rmm];
-    const float* M0 = S.mub[rm0];
-    const float* Mp = S.mub[rmp];
-    const float mub = M0[i1];
-    const float gmx = dgrad<0>(Mm, M0, Mp, i1, HX1), gmy = dgrad<1>(Mm, M0, Mp, i1, HX1),
-                gmz = dgrad<2>(Mm, M0, Mp, i1, HX1);
-    // correction force F_c,b = 1/2 sum_a d_a (S_a u_b - u_a S_b), products A_xy, A_xz, A_yz
-    const float dAxy_x = dgrad<0>(S.acor[rmm][0], S.acor[rm0][0], S.acor[rmp][0], i1, HX1);
-    const float dAxy_y = dgrad<1>(S.acor[rmm][0], S.acor[rm0][0], S.acor[rmp][0], i1, HX1);
-    const float dAxz_x = dgrad<0>(S.acor[rmm][1], S.acor[rm0][1], S.acor[rmp][1], i1, HX1);
-    const float dAxz_z = dgrad<2>(S.acor[rmm][1], S.acor[rm0][1], S.acor[rmp][1], i1, HX1);
-    const float dAyz_y = dgrad<1>(S.acor[rmm][2], S.acor[rm0][2], S.acor[rmp][2], i1, HX1);
-    const float dAyz_z = dgrad<2>(S.acor[rmm][2], S.acor[rm0][2], S.acor[rmp][2], i1, HX1);
-    const float Fcx = -0.5f * (dAxy_y + dAxz_z);
-    const float Fcy = 0.5f * (dAxy_x - dAyz_z);
-    const float Fcz = 0.5f * (dAxz_x + dAyz_y);
-
-    // previous-step history of this node
-    const float php = h_in[node];
-    const float upx = h_in[nodes + node], upy = h_in[2 * nodes + node], upz = h_in[3 * nodes + node];
-    const float spx = h_in[4 * nodes + node], spy = h_in[5 * nodes + node], spz = h_in[6 * nodes + node];
-
-    // degenerate mobility, flux S (frozen phi0), mixture properties
-    const float fdeg = ph1 * (1.f - ph1) * (1.f - ph0);
-    const float mob = k.M_cst + k.M_deg * fdeg;
-    const float sfac = (k.rho1 - k.rho2) * mob * k.inv_gam1;
-    const float Sx = sfac * gmx, Sy = sfac * gmy, Sz = sfac * gmz;
-    const float rho = k.rho0 * ph0 + k.rho1 * ph1 + k.rho2 * ph2;
-    const float grx = (k.rho0 - k.rho2) * g0x + (k.rho1 - k.rho2) * g1x;
-    const float gry = (k.rho0 - k.rho2) * g0y + (k.rho1 - k.rho2) * g1y;
-    const float grz = (k.rho0 - k.rho2) * g0z + (k.rho1 - k.rho2) * g1z;
-    const float muv = k.mu0 * ph0 + k.mu1 * ph1 + k.mu2 * ph2;
-
-    // F = F_s + F_b + F_c with F_s = (mu0 - mu2) grad phi0 + (mu1 - mu2) grad phi1
-    const float one_m0 = 1.f - ph0;
-    const float Fx = d02 * g0x + d12 * g1x + one_m0 * k.bx + Fcx;
-    const float Fy = d02 * g0y + d12 * g1y + one_m0 * k.by + Fcy;
-    const float Fz = d02 * g0z + d12 * g1z + one_m0 * k.bz + Fcz;
-
-    // NS populations and their moments
-    float g[Q];
+    OwnIn in;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = __ldcs(g_in + i * nodes + node);
-    float sum_nz = 0.f, mx = 0.f, my = 0.f, mz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
-    float ex = 0.f, ey = 0.f, ez = 0.f, bxm = 0.f, bym = 0.f, bzm = 0.f;
+    for (int i = 0; i < Q; ++i) in.g[i] = __ldcs(g_in + i * nodes + node);
+    in.jx = j_in[node];
+    in.jy = j_in[nodes + node];
+    in.jz = j_in[2 * nodes + node];
+    in.php = h_in[node];
+    in.upx = h_in[nodes + node];
+    in.upy = h_in[2 * nodes + node];
+    in.upz = h_in[3 * nodes + node];
+    in.spx = h_in[4 * nodes + node];
+    in.spy = h_in[5 * nodes + node];
+    in.spz = h_in[6 * nodes + node];
+    Rings R;
+    const int rp[3] = {ring(z - 1, RP), ring(z, RP), ring(z + 1, RP)};
+    const int rm[3] = {ring(z - 1, RM), ring(z, RM), ring(z + 1, RM)};
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int cx = CX(i), cy = CY(i), cz = CZ(i);
-      const float v = g[i];
-      sum_nz += v;
-      if (cx) mx += cx > 0 ? v : -v;
-      if (cy) my += cy > 0 ? v : -v;
-      if (cz) mz += cz > 0 ? v : -v;
-      if (cx && cy) pxy += cx * cy > 0 ? v : -v;
-      if (cx && cz) pxz += cx * cz > 0 ? v : -v;
-      if (cy && cz) pyz += cy * cz > 0 ? v : -v;
-      // third-order sums: sum c_a (c_b^2 + c_c^2) g and sum c_a (c_b^2 - c_c^2) g (cyclic a, b, c)
-      if (cx && (cy || cz)) {
-        ex += cx > 0 ? v : -v;
-        bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v;
-      }
-      if (cy && (cz || cx)) {
-        ey += cy > 0 ? v : -v;
-        bym += ((cz ? 1 : -1) * cy > 0) ? v : -v;
-      }
-      if (cz && (cx || cy)) {
-        ez += cz > 0 ? v : -v;
-        bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v;
-      }
+    for (int q = 0; q < 3; ++q) {
+      R.p0[q] = S.phi0[rp[q]];
+      R.p1[q] = S.phi1[rp[q]];
+      R.mu[q] = S.mub[rm[q]];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) R.ac[c][q] = S.acor[rm[q]][c];
     }
-
-    // velocity with the solid penalisation force (u_w = 0)
-    const float inv_rho = __frcp_rn(rho);
-    const float usx = (mx + 0.5f * Fx) * inv_rho;
-    const float usy = (my + 0.5f * Fy) * inv_rho;
-    const float usz = (mz + 0.5f * Fz) * inv_rho;
-    const float damp = 1.f - 0.5f * ph0;
-    const float ux = usx * damp, uy = usy * damp, uz = usz * damp;
-    const float Ftx = Fx - ph0 * rho * usx, Fty = Fy - ph0 * rho * usy, Ftz = Fz - ph0 * rho * usz;
-
-    // local viscous rates (s0 = s4 = s2a)
-    const float om = fmaxf(one_m0, kOneMinusPhi0Floor);
-    const float ra = rho * om * k.a2a, rb = rho * om * k.a2b;
-    const float s2a = __fdividef(ra, 0.5f * ra + muv);
-    const float s2b = __fdividef(rb, 0.5f * rb + muv);
-    const float inv_s2a = 0.5f + __fdividef(muv, ra);
-
-    // pressure (Sec. 3)
-    const float udg = ux * grx + uy * gry + uz * grz;
-    const float q = (rho * ux - Sx) * ux + (rho * uy - Sy) * uy + (rho * uz - Sz) * uz;
-    const float rhop = k.rho0 * ph0 + k.rho1 * php + k.rho2 * (1.f - ph0 - php);
-    const float qp = (rhop * upx - spx) * upx + (rhop * upy - spy) * upy + (rhop * upz - spz) * upz;
-    const float H = k.Kp * ((k.h0 - k.h2) * inv_s2a + k.h3);
-    const float p = k.pf * (sum_nz + (0.5f + H) * udg - k.wq * q + 0.5f * k.Kp * (q - qp));
-
-    // push destinations; interior nodes use fixed offsets
-    const bool edge = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
-    auto store = [&](float* __restrict__ out, int i, float v) {
-      const int cx = CX(i), cy = CY(i), cz = CZ(i);
-      if (!edge) {
-        out[i * nodes + node + cz * plane + cy * nx + cx] = v;
-        return;
-      }
-      int xd = x + cx, yd = y + cy, zd = z + cz;
-      bool bb = false;
-      if (xd < 0 || xd >= nx) {
-        if (per_x) xd = xd < 0 ? xd + nx : xd - nx;
-        else bb = true;
-      }
-      if (yd < 0 || yd >= ny) {
-        if (per_y) yd = yd < 0 ? yd + ny : yd - ny;
-        else bb = true;
-      }
-      if (zd < 0 || zd >= nz) {
-        if (per_z) zd = zd < 0 ? zd + nz : zd - nz;
-        else bb = true;
-      }
-      const int dst = bb ? OPP(i) * nodes + node : i * nodes + (zd * ny + yd) * nx + xd;
-      out[dst] = v;
-    };
-
-    // ---- NS collision: g* = (1 - s2a) g + w_i X_i (see the file header) ----
-    {
-      const float om2a = 1.f - 0.5f * s2a;
-      // equilibrium second moments e_ab and the force moment M^2F_ab (Sec. 3)
-      const float exx = rho * ux * ux - Sx * ux, eyy = rho * uy * uy - Sy * uy, ezz = rho * uz * uz - Sz * uz;
-      const float exy = rho * ux * uy - 0.5f * (Sx * uy + ux * Sy);
-      const float exz = rho * ux * uz - 0.5f * (Sx * uz + ux * Sz);
-      const float eyz = rho * uy * uz - 0.5f * (Sy * uz + uy * Sz);
-      const float dSxx = Sx * ux - spx * upx, dSyy = Sy * uy - spy * upy, dSzz = Sz * uz - spz * upz;
-      const float dSxy = 0.5f * (Sx * uy + ux * Sy) - 0.5f * (spx * upy + upx * spy);
-      const float dSxz = 0.5f * (Sx * uz + ux * Sz) - 0.5f * (spx * upz + upx * spz);
-      const float dSyz = 0.5f * (Sy * uz + uy * Sz) - 0.5f * (spy * upz + upy * spz);
-      const float iso = (1.f - 3.f * cs2) * udg;
-      const float Mxx = 2.f * ux * Fx - dSxx + 2.f * cs2 * ux * grx + iso;
-      const float Myy = 2.f * uy * Fy - dSyy + 2.f * cs2 * uy * gry + iso;
-      const float Mzz = 2.f * uz * Fz - dSzz + 2.f * cs2 * uz * grz + iso;
-      const float Mxy = ux * Fy + Fx * uy - dSxy + cs2 * (ux * gry + grx * uy);
-      const float Mxz = ux * Fz + Fx * uz - dSxz + cs2 * (ux * grz + grx * uz);
-      const float Myz = uy * Fz + Fy * uz - dSyz + cs2 * (uy * grz + gry * uz);
-      const float i2n = __frcp_rn(cs2 - cs4), ic2 = __frcp_rn(cs2), ic4 = __frcp_rn(cs4);
-      const float Dx = (s2a * exx + om2a * Mxx) * i2n;
-      const float Dy = (s2a * eyy + om2a * Myy) * i2n;
-      const float Dz = (s2a * ezz + om2a * Mzz) * i2n;
-      const float base = s2a * p * ic2 + om2a * udg - cs2 * (Dx + Dy + Dz);
-      const float d1 = k.s1n - s2a;
-      const float Vx = (s2a * rho * ux + om2a * Ftx - d1 * (mx - rho * ux + 0.5f * Ftx)) * ic2;
-      const float Vy = (s2a * rho * uy + om2a * Fty - d1 * (my - rho * uy + 0.5f * Fty)) * ic2;
-      const float Vz = (s2a * rho * uz + om2a * Ftz - d1 * (mz - rho * uz + 0.5f * Ftz)) * ic2;
-      const float db = s2b - s2a;
-      const float Oxy = (s2a * exy + om2a * Mxy - db * (pxy - exy + 0.5f * Mxy)) * ic4;
-      const float Oxz = (s2a * exz + om2a * Mxz - db * (pxz - exz + 0.5f * Mxz)) * ic4;
-      const float Oyz = (s2a * eyz + om2a * Myz - db * (pyz - eyz + 0.5f * Myz)) * ic4;
-      // third-order group: T_a = (s3 - s2a) m_A,a / |A|^2, U_a = (s3 - s2a) m_B,a / |B|^2
-      const float d3 = k.s3n - s2a;
-      const float iB = __frcp_rn(2.f * cs4), iA = __frcp_rn(2.f * cs4 * (1.f - 2.f * cs2));
-      const float k3 = 1.f - 2.f * cs2;
-      const float Tx = d3 * (ex - 2.f * cs2 * mx) * iA, Ty = d3 * (ey - 2.f * cs2 * my) * iA,
-                  Tz = d3 * (ez - 2.f * cs2 * mz) * iA;
-      const float Ux = d3 * bxm * iB, Uy = d3 * bym * iB, Uz = d3 * bzm * iB;
-      const float Px = k3 * Tx + Ux, Qx = k3 * Tx - Ux;   // edge factors per axis: B_a = +c_a or -c_a
-      const float Py = k3 * Ty + Uy, Qy = k3 * Ty - Uy;
-      const float Pz = k3 * Tz + Uz, Qz = k3 * Tz - Uz;
-      const float om1 = 1.f - s2a;
-      store(g_out, 0, om1 * g[0] + k.w0 * base - s2a * p * ic2);
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int cx = CX(i), cy = CY(i), cz = CZ(i);
-        float X = base;
-        if (cx) X += cx > 0 ? Dx + Vx : Dx - Vx;
-        if (cy) X += cy > 0 ? Dy + Vy : Dy - Vy;
-        if (cz) X += cz > 0 ? Dz + Vz : Dz - Vz;
-        if (cx && cy) X += cx * cy > 0 ? Oxy : -Oxy;
-        if (cx && cz) X += cx * cz > 0 ? Oxz : -Oxz;
-        if (cy && cz) X += cy * cz > 0 ? Oyz : -Oyz;
-        if (i < 7) {
-          // axis: A_a(c) = -2 cs2 c_a, B_a(c) = 0
-          const float T = cx ? Tx : (cy ? Ty : Tz);
-          const int c = cx + cy + cz;
-          X += c > 0 ? 2.f * cs2 * T : -2.f * cs2 * T;
-        } else {
-          // edge: -c_a [(1 - 2 cs2) T_a + B_a U_a / c_a] over its two axes
-          if (cx) { const float e = cy ? Px : Qx; X -= cx > 0 ? e : -e; }
-          if (cy) { const float e = cz ? Py : Qy; X -= cy > 0 ? e : -e; }
-          if (cz) { const float e = cx ? Pz : Qz; X -= cz > 0 ? e : -e; }
-        }
-        store(g_out, i, om1 * g[i] + weight(k, i) * X);
-      }
-    }
-
-    // ---- CH collision ----
-    {
-      const float emb = k.eta * mub;
-      const float corr = k.corr_scale * (1.f - fdeg);
-      // first moment of R: d_t(phi1 u) + cs2 corr eta grad mubar
-      const float Rx = (ph1 * ux - php * upx) + cs2 * corr * k.eta * gmx;
-      const float Ry = (ph1 * uy - php * upy) + cs2 * corr * k.eta * gmy;
-      const float Rz = (ph1 * uz - php * upz) + cs2 * corr * k.eta * gmz;
-      const float ic2 = __frcp_rn(cs2);
-      if (k.ch_fast != 0.f) {
-        // f* = f^eq + R/2 - (s1 - 1) P1 v: only j = sum c f enters
-        const float jx = j_in[node], jy = j_in[nodes + node], jz = j_in[2 * nodes + node];
-        const float ax = (ph1 * ux + (1.f - k.s1c) * (jx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx) * ic2;
-        const float ay = (ph1 * uy + (1.f - k.s1c) * (jy - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry) * ic2;
-        const float az = (ph1 * uz + (1.f - k.s1c) * (jz - ph1 * uz) + (1.f - 0.5f * k.s1c) * Rz) * ic2;
-        float rest = ph1;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          const int cx = CX(i), cy = CY(i), cz = CZ(i);
-          float s = emb;
-          if (cx) s += cx > 0 ? ax : -ax;
-          if (cy) s += cy > 0 ? ay : -ay;
-          if (cz) s += cz > 0 ? az : -az;
-          const float v = weight(k, i) * s;
-          rest -= v;
-          store(f_out, i, v);
-        }
-        store(f_out, 0, rest);   // the rest population closes the zeroth moment
-      } else {
-        float f[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] = f_in[i * nodes + node];
-        float jx = 0.f, jy = 0.f, jz = 0.f, qxx = 0.f, qyy = 0.f, qzz = 0.f, qxy = 0.f, qxz = 0.f, qyz = 0.f;
-        float ex = 0.f, ey = 0.f, ez = 0.f, bxm = 0.f, bym = 0.f, bzm = 0.f;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          const int cx = CX(i), cy = CY(i), cz = CZ(i);
-          const float v = f[i];
-          if (cx) { jx += cx > 0 ? v : -v; qxx += v; }
-          if (cy) { jy += cy > 0 ? v : -v; qyy += v; }
-          if (cz) { jz += cz > 0 ? v : -v; qzz += v; }
-          if (cx && cy) qxy += cx * cy > 0 ? v : -v;
-          if (cx && cz) qxz += cx * cz > 0 ? v : -v;
-          if (cy && cz) qyz += cy * cz > 0 ? v : -v;
-          if (cx && (cy || cz)) { ex += cx > 0 ? v : -v; bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v; }
-          if (cy && (cz || cx)) { ey += cy > 0 ? v : -v; bym += ((cz ? 1 : -1) * cy > 0) ? v : -v; }
-          if (cz && (cx || cy)) { ez += cz > 0 ? v : -v; bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v; }
-        }
-        const float s4 = k.s4c, om4 = 1.f - s4, oh4 = 1.f - 0.5f * s4;
-        const float d1 = (k.s1c - s4) * ic2;
-        const float m1x = jx - ph1 * ux + 0.5f * Rx, m1y = jy - ph1 * uy + 0.5f * Ry, m1z = jz - ph1 * uz + 0.5f * Rz;
-        const float d2a = (k.s2ac - s4) * __frcp_rn(cs2 - cs4);
-        const float m2x = qxx - cs2 * emb, m2y = qyy - cs2 * emb, m2z = qzz - cs2 * emb;
-        const float d2b = (k.s2bc - s4) * __frcp_rn(cs4);
-        const float d3 = k.s3c - s4;
-        const float iB = __frcp_rn(2.f * cs4), iA = __frcp_rn(2.f * cs4 * (1.f - 2.f * cs2));
-        const float k3 = 1.f - 2.f * cs2;
-        const float Tx = d3 * (ex - 2.f * cs2 * jx) * iA, Ty = d3 * (ey - 2.f * cs2 * jy) * iA,
-                    Tz = d3 * (ez - 2.f * cs2 * jz) * iA;
-        const float Ux = d3 * bxm * iB, Uy = d3 * bym * iB, Uz = d3 * bzm * iB;
-        const float Px = k3 * Tx + Ux, Qx = k3 * Tx - Ux;
-        const float Py = k3 * Ty + Uy, Qy = k3 * Ty - Uy;
-        const float Pz = k3 * Tz + Uz, Qz = k3 * Tz - Uz;
-        const float p2 = -cs2 * d2a * (m2x + m2y + m2z);   // c-independent part of the P2a term
-        // rest population: f^eq_0 = phi1 + (w0 - 1) eta mubar, R_0 = 0
-        store(f_out, 0, om4 * f[0] + s4 * (ph1 + (k.w0 - 1.f) * emb) - k.w0 * p2);
-        const float ux1 = ph1 * ux * ic2, uy1 = ph1 * uy * ic2, uz1 = ph1 * uz * ic2;
-        const float rx = Rx * ic2, ry = Ry * ic2, rz = Rz * ic2;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          const int cx = CX(i), cy = CY(i), cz = CZ(i);
-          // f^eq_i / w_i = eta mubar + c.phi u / cs2;  R_i / w_i = c.R / cs2
-          float feq = emb, Rc = 0.f, L = p2;
-          if (cx) { feq += cx > 0 ? ux1 : -ux1; Rc += cx > 0 ? rx : -rx; L += (cx > 0 ? m1x : -m1x) * d1 + d2a * m2x; }
-          if (cy) { feq += cy > 0 ? uy1 : -uy1; Rc += cy > 0 ? ry : -ry; L += (cy > 0 ? m1y : -m1y) * d1 + d2a * m2y; }
-          if (cz) { feq += cz > 0 ? uz1 : -uz1; Rc += cz > 0 ? rz : -rz; L += (cz > 0 ? m1z : -m1z) * d1 + d2a * m2z; }
-          if (cx && cy) L += (cx * cy > 0 ? qxy : -qxy) * d2b;
-          if (cx && cz) L += (cx * cz > 0 ? qxz : -qxz) * d2b;
-          if (cy && cz) L += (cy * cz > 0 ? qyz : -qyz) * d2b;
-          if (i < 7) {
-            const float T = cx ? Tx : (cy ? Ty : Tz);
-            const int c = cx + cy + cz;
-            L -= c > 0 ? 2.f * cs2 * T : -2.f * cs2 * T;
-          } else {
-            if (cx) { const float e = cy ? Px : Qx; L += cx > 0 ? e : -e; }
-            if (cy) { const float e = cz ? Py : Qy; L += cy > 0 ? e : -e; }
-            if (cz) { const float e = cx ? Pz : Qz; L += cz > 0 ? e : -e; }
-          }
-          const float w = weight(k, i);
-          store(f_out, i, om4 * f[i] + w * (s4 * feq + oh4 * Rc - L));
-        }
-      }
-    }
-
-    // history of this step (phi1 was written by the moment pass)
-    h_out[nodes + node] = ux;
-    h_out[2 * nodes + node] = uy;
-    h_out[3 * nodes + node] = uz;
-    h_out[4 * nodes + node] = Sx;
-    h_out[5 * nodes + node] = Sy;
-    h_out[6 * nodes + node] = Sz;
-    if (OBS) {
-      a.p_out[(long long)b * nodes + node] = p;
-      const float u2 = ux * ux + uy * uy + uz * uz;
-      if (!(u2 <= 0.25f) || !(fabsf(ph1) < 1e30f)) atomicOr(a.flag, 1u);
-    }
+    R.i2 = (ty + 2) * HX2 + (tx + 2);
+    R.sw2 = HX2;
+    R.i1 = (ty + 1) * HX1 + (tx + 1);
+    R.sw1 = HX1;
+    node_update<OBS>(k, R, in, o, x, y, z);
   }
+}
+
+// ---------------------------------------------------------------------------
+// fused step, pipelined form (nx % 4 == 0).  The owned columns of plane z+1
+// (g, j, history: 29 planes of 32 x 8 floats) arrive by three TMA tile loads
+// while plane z is computed; the halo tiles of phi0 / phi1 (plane z+3) and of
+// the history u, S (plane z+2) arrive by 16-byte asynchronous copies issued
+// one plane ahead, with the wrap / mirror of each 4-column chunk fixed per
+// CTA.  Every wait on the TMA barrier is bounded.
+// ---------------------------------------------------------------------------
+constexpr int PW = 40;                       // halo tile row: columns x0-4 .. x0+35 (16-byte aligned chunks)
+constexpr int PR2 = TY + 4, PR1 = TY + 2;    // rows of the two-halo and one-halo tiles
+constexpr int RP5 = 5;                       // phi ring: z-1 .. z+2 in use, z+3 in flight
+constexpr int NOWN = Q + 3 + NH;             // owned planes per z: g, j, history
+constexpr unsigned kOwnBytes = NOWN * NT * 4;
+constexpr int kSpinLimit = 1 << 22;          // try_wait polls before a TMA wait gives up
+
+struct TmaMaps {
+  CUtensorMap g, j, h;   // g: (nx, ny, nz, 19 nb), j: (.., 3 nb), h: (.., 7 nb); boxes 32 x 8 x 1 x {19, 3, 7}
+};
+
+struct alignas(128) PipeSmem3 {
+  float own[NOWN][NT];              // TMA destination: g 0-18, j 19-21, history 22-28
+  float phi1[RP5][PR2 * PW];
+  float phi0[RP5][PR2 * PW];
+  float hus[2][6][PR1 * PW];        // history u, S (planes 1-6) on the one-halo tile
+  float mub[RM][N1];
+  float acor[RM][3][N1];
+  InstanceConsts k;
+  unsigned long long bar;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void bar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// bounded wait for phase `parity`; returns false when the poll limit is reached
+__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
+  for (int it = 0; it < kSpinLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load4(float* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <bool OBS>
+__global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const __grid_constant__ TmaMaps maps) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  PipeSmem3& S = *reinterpret_cast<PipeSmem3*>(smem_raw);
+
+  const int t = threadIdx.x;
+  const int tx = t % TX, ty = t / TX;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int per_x = a.per_x, per_y = a.per_y, per_z = a.per_z;
+  const int ntx = (nx + TX - 1) / TX;
+  const int x0 = (blockIdx.x % ntx) * TX;
+  const int zs = (blockIdx.x / ntx) * a.strip;
+  const int ze = min(zs + a.strip, nz);
+  const int y0 = blockIdx.y * TY;
+  const int b = blockIdx.z;
+  const int nodes = (int)a.nodes;
+  const int plane = nx * ny;
+  if (t < (int)(sizeof(InstanceConsts) / 4))
+    reinterpret_cast<float*>(&S.k)[t] = reinterpret_cast<const float*>(a.consts + b)[t];
+
+  const float* __restrict__ p0_in = a.phi0 + (long long)b * nodes;
+  const float* __restrict__ h_in = a.hist_in + (long long)b * NH * nodes;
+  const float* __restrict__ phi1_now = a.hist_out + (long long)b * NH * nodes;   // moment pass of this step
+  Outs o;
+  o.f_in = a.f_in + (long long)b * Q * nodes;
+  o.f_out = a.f_out + (long long)b * Q * nodes;
+  o.g_out = a.g_out + (long long)b * Q * nodes;
+  o.h_out = a.hist_out + (long long)b * NH * nodes;
+  o.p_out = a.p_out + (long long)b * nodes;
+  o.flag = a.flag;
+  o.nx = nx; o.ny = ny; o.nz = nz; o.per_x = per_x; o.per_y = per_y; o.per_z = per_z;
+  o.nodes = nodes; o.plane = plane;
+
+  // Chunk copies of this thread, fixed for the whole sweep.  A chunk is four
+  // columns xs .. xs+3 of one row: inside the lattice or wrapped it is one
+  // 16-byte copy from column `off`; mirrored it is four 4-byte copies from
+  // off, off-1, off-2, off-3; mode -1 skips it.
+  //   phi chunk  t       (t < 240): array t / 120 (phi1, phi0), row, chunk of the two-halo tile
+  //   hist chunk t + 256 m (< 600): array id / 100 (u_x .. S_z), row, chunk of the one-halo tile
+  auto chunk = [&](int ylog, int xs, int ymax, int xmax, int& off, int& mode) {
+    mode = -1;
+    off = 0;
+    if (ylog > ymax || xs > xmax) return;
+    const int yr = wrap_or_mirror(ylog, ny, per_y) * nx;
+    if (xs >= 0 && xs < nx) {
+      mode = 0;
+      off = yr + xs;
+    } else if (per_x) {
+      mode = 0;
+      off = yr + (xs < 0 ? xs + nx : xs - nx);
+    } else {
+      mode = 1;
+      off = yr + (xs < 0 ? -1 - xs : 2 * nx - 1 - xs);
+    }
+  };
+  int pc_off, pc_mode, pc_dst;
+  const float* pc_src;
+  {
+    const int arr = t / 120, rem = t % 120, r = rem / 10, kk = rem % 10;
+    chunk(y0 - 2 + r, x0 - 4 + 4 * kk, ny + 1, nx + 1, pc_off, pc_mode);
+    if (t >= 240) pc_mode = -1;
+    pc_dst = r * PW + 4 * kk;
+    pc_src = arr == 0 ? phi1_now : p0_in;
+  }
+  int hc_off[3], hc_mode[3], hc_dst[3], hc_arr[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int id = t + NT * m;
+    const int arr = id / 100, rem = id % 100, r = rem / 10, kk = rem % 10;
+    chunk(y0 - 1 + r, x0 - 4 + 4 * kk, ny, nx, hc_off[m], hc_mode[m]);
+    if (id >= 600) hc_mode[m] = -1;
+    hc_dst[m] = r * PW + 4 * kk;
+    hc_arr[m] = arr;
+  }
+  auto copy_chunk = [&](float* dst, const float* src, int mode) {
+    if (mode == 0) {
+      cp16(dst, src);
+    } else if (mode == 1) {
+      cp4(dst, src);
+      cp4(dst + 1, src - 1);
+      cp4(dst + 2, src - 2);
+      cp4(dst + 3, src - 3);
+    }
+  };
+  auto issue_phi = [&](int zl) {
+    if (pc_mode < 0) return;
+    const int zo = wrap_or_mirror(zl, nz, per_z) * plane;
+    float* base = (t / 120 == 0 ? S.phi1 : S.phi0)[ring(zl, RP5)];
+    copy_chunk(base + pc_dst, pc_src + zo + pc_off, pc_mode);
+  };
+  auto issue_hist = [&](int zl) {
+    const int zo = wrap_or_mirror(zl, nz, per_z) * plane;
+    const int sl = zl & 1;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      if (hc_mode[m] < 0) continue;
+      copy_chunk(&S.hus[sl][hc_arr[m]][hc_dst[m]], h_in + (hc_arr[m] + 1) * nodes + zo + hc_off[m], hc_mode[m]);
+    }
+  };
+  auto issue_own = [&](int z) {   // one thread
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    bar_expect(&S.bar, kOwnBytes);
+    tma_load4(S.own[0], &maps.g, x0, y0, z, b * Q, &S.bar);
+    tma_load4(S.own[Q], &maps.j, x0, y0, z, b * 3, &S.bar);
+    tma_load4(S.own[Q + 3], &maps.h, x0, y0, z, b * NH, &S.bar);
+  };
+
+  const InstanceConsts& k = S.k;
+  auto calc_mub = [&](int zl) {   // phi ring planes zl-1 .. zl+1 -> mubar ring slot of zl
+    const float* q0[3] = {S.phi0[ring(zl - 1, RP5)], S.phi0[ring(zl, RP5)], S.phi0[ring(zl + 1, RP5)]};
+    const float* q1[3] = {S.phi1[ring(zl - 1, RP5)], S.phi1[ring(zl, RP5)], S.phi1[ring(zl + 1, RP5)]};
+    float* dst = S.mub[ring(zl, RM)];
+    for (int p = t; p < N1; p += NT) {
+      const int px = p % HX1, py = p / HX1;
+      if (x0 - 1 + px > nx || y0 - 1 + py > ny) continue;
+      const int i = (py + 1) * PW + (px + 3);
+      float mu0, mu1, mu2;
+      chem_pot(k, q0[1][i], q1[1][i], lap3(q0[0], q0[1], q0[2], i, PW), lap3(q1[0], q1[1], q1[2], i, PW), mu0, mu1,
+               mu2);
+      dst[p] = mubar1_of(k, mu0, mu1, mu2);
+    }
+  };
+  auto calc_prod = [&](int zl) {  // history slot of zl -> product ring slot of zl
+    const int sl = zl & 1;
+    const int rm = ring(zl, RM);
+    for (int p = t; p < N1; p += NT) {
+      const int px = p % HX1, py = p / HX1;
+      if (x0 - 1 + px > nx || y0 - 1 + py > ny) continue;
+      const int i = py * PW + (px + 3);
+      const float ux = S.hus[sl][0][i], uy = S.hus[sl][1][i], uz = S.hus[sl][2][i];
+      const float sx = S.hus[sl][3][i], sy = S.hus[sl][4][i], sz = S.hus[sl][5][i];
+      S.acor[rm][0][p] = sx * uy - ux * sy;
+      S.acor[rm][1][p] = sx * uz - ux * sz;
+      S.acor[rm][2][p] = sy * uz - uy * sz;
+    }
+  };
+
+  // prologue
+  if (t == 0) {
+    bar_init(&S.bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();   // constants and barrier visible
+  if (t == 0) issue_own(zs);
+  for (int q = -2; q <= 1; ++q) issue_phi(zs + q);
+  issue_hist(zs - 1);
+  issue_hist(zs);
+  cp_commit();
+  cp_wait_all();
+  __syncthreads();
+  calc_mub(zs - 1);
+  calc_mub(zs);
+  calc_prod(zs - 1);
+  calc_prod(zs);
+  __syncthreads();   // history slot of zs-1 is free again
+  issue_phi(zs + 2);
+  issue_hist(zs + 1);
+  cp_commit();
+
+  const int x = x0 + tx, y = y0 + ty;
+  const bool own = x < nx && y < ny;
+  bool ok = true;
+  unsigned pending = 0;
+  for (int z = zs; z < ze; ++z) {
+    cp_wait_all();                                      // phi z+2, history z+1
+    const unsigned parity = (unsigned)(z - zs) & 1u;
+    if (!bar_wait(&S.bar, parity)) {                    // owned planes of z
+      ok = false;
+      pending = parity;
+    }
+    if (!__syncthreads_and(ok)) {
+      if (t == 0) atomicOr(o.flag, 2u);
+      ok = false;
+      break;
+    }
+    if (z + 3 <= ze + 1) issue_phi(z + 3);
+    if (z + 2 <= ze) issue_hist(z + 2);
+    cp_commit();
+    calc_prod(z + 1);
+    calc_mub(z + 1);
+    __syncthreads();
+
+    // owned inputs of plane z into registers, then the slot takes plane z+1
+    OwnIn in;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) in.g[i] = S.own[i][t];
+    in.jx = S.own[Q][t];
+    in.jy = S.own[Q + 1][t];
+    in.jz = S.own[Q + 2][t];
+    in.php = S.own[Q + 3][t];
+    in.upx = S.own[Q + 4][t];
+    in.upy = S.own[Q + 5][t];
+    in.upz = S.own[Q + 6][t];
+    in.spx = S.own[Q + 7][t];
+    in.spy = S.own[Q + 8][t];
+    in.spz = S.own[Q + 9][t];
+    __syncthreads();
+    if (t == 0 && z + 1 < ze) issue_own(z + 1);
+    if (!own) continue;
+
+    Rings R;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      R.p0[q] = S.phi0[ring(z - 1 + q, RP5)];
+      R.p1[q] = S.phi1[ring(z - 1 + q, RP5)];
+      R.mu[q] = S.mub[ring(z - 1 + q, RM)];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) R.ac[c][q] = S.acor[ring(z - 1 + q, RM)][c];
+    }
+    R.i2 = (ty + 2) * PW + (tx + 4);
+    R.sw2 = PW;
+    R.i1 = (ty + 1) * HX1 + (tx + 1);
+    R.sw1 = HX1;
+    node_update<OBS>(k, R, in, o, x, y, z);
+  }
+  // leave no copy in flight: asynchronous copies, and a TMA load issued for a plane not processed
+  cp_wait_all();
+  if (!ok) (void)bar_wait(&S.bar, pending);   // one more bounded wait for the TMA load that was late
 }
 
 }  // namespace
@@ -704,8 +1057,56 @@ cudaError_t launch_d3q19_moments(const StepArgs& a, int nbatch, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+size_t d3q19_maps_bytes() { return sizeof(TmaMaps); }
+
+int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx, int ny, int nz, int nbatch,
+                     void* out) {
+  if (nx % 4 != 0) return 1;   // TMA strides must be multiples of 16 bytes
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return -1;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  TmaMaps m;
+  auto one = [&](CUtensorMap* map, const float* base, int planes) {
+    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)planes * nbatch};
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nz * 4};
+    const cuuint32_t box[4] = {TX, TY, 1, (cuuint32_t)planes};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (!one(&m.g, g, Q) || !one(&m.j, mom, 3) || !one(&m.h, hist, NH)) return -1;
+  memcpy(out, &m, sizeof m);
+  return 0;
+}
+
+cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s, const void* maps) {
   cudaError_t e = cudaSuccess;
+  const int ntx = (a.nx + TX - 1) / TX;
+  const int nstrips = (a.nz + a.strip - 1) / a.strip;
+  dim3 grid(ntx * nstrips, (a.ny + TY - 1) / TY, nbatch);
+  if (maps) {
+    TmaMaps m;
+    memcpy(&m, maps, sizeof m);
+    const size_t smem = sizeof(PipeSmem3);
+    static bool configured = false;
+    if (!configured) {
+      e = cudaFuncSetAttribute(d3q19_step_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(d3q19_step_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    if (observe) d3q19_step_pipe<true><<<grid, NT, smem, s>>>(a, m);
+    else d3q19_step_pipe<false><<<grid, NT, smem, s>>>(a, m);
+    return cudaGetLastError();
+  }
   const size_t smem = sizeof(StepSmem3);
   static bool configured = false;   // attribute set once per process (both variants)
   if (!configured) {
@@ -715,9 +1116,6 @@ cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaS
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int ntx = (a.nx + TX - 1) / TX;
-  const int nstrips = (a.nz + a.strip - 1) / a.strip;
-  dim3 grid(ntx * nstrips, (a.ny + TY - 1) / TY, nbatch);
   if (observe) d3q19_step<true><<<grid, NT, smem, s>>>(a);
   else d3q19_step<false><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();

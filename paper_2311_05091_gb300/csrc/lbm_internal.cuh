@@ -69,7 +69,16 @@ cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, fl
                               int per_x, int per_y, int per_z, int nbatch, cudaStream_t s);
 // D3Q19 steps are two launches: the moment pass, then the fused kernel.
 cudaError_t launch_d3q19_moments(const StepArgs& a, int nbatch, cudaStream_t s);
-cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s);
+// maps: tensor maps of the buffers the step reads (from build_d3q19_maps), or
+// nullptr for the generic kernel (any nx)
+cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s, const void* maps);
+// Tensor maps of one set of input buffers (g, j scratch, history) for the
+// pipelined D3Q19 kernel: 0 on success, 1 if nx % 4 != 0 (not supported),
+// -1 on a driver error.  out receives d3q19_maps_bytes() bytes and must be
+// 64-byte aligned.
+size_t d3q19_maps_bytes();
+int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx, int ny, int nz, int nbatch,
+                     void* out);
 
 // Observables: deterministic two-pass reduction of one instance.
 //   phi0, phi1, u (d planes), p: device fields of one instance, n nodes.

@@ -112,3 +112,32 @@ def test_batch_instances_are_independent(lbm_lib):
         assert np.array_equal(b_phi1[i], s_phi1[0]) and np.array_equal(b_u[i], s_u[0])
     st = oracle_run("D3Q19", phi0, phi1, prms[0], (True, True, True), 100)
     assert rel_l2(b_phi1[0], st.macro["phi1"]) < 1e-5
+
+
+def test_pipelined_and_generic_kernels_agree_bitwise(lbm_lib):
+    # depth 1 selects the generic fused kernel, depth 2 the pipelined (TMA) one
+    phi0, phi1 = as_inputs(porous_box())
+    L = lbm_lib
+    nz, ny, nx = phi0.shape
+    out = []
+    for depth in (1, 2):
+        ctx = L.Context(L.LBM_D3Q19, nx, ny, nz, periodic=(True, True, True),
+                        params=L.lbm_default_params(**POROUS_PRM))
+        try:
+            ctx.set_launch(6, depth)
+            ctx.set_solid(phi0)
+            ctx.set_phase(phi1)
+            ctx.step(60)
+            out.append(ctx.get_populations() + ctx.get_fields())
+        finally:
+            ctx.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_pipelined_kernel_walls_and_ragged_tiles(lbm_lib):
+    # nx % 4 == 0 with mirror ghosts on x and y: the reversed 4-byte halo chunks
+    geo = sphere_box_droplet(40, 13, 11, [(20.0, 6.0, 5.0, 3.0)], drop=(8.0, 6.0, 5.0, 3.5),
+                             periodic=(False, False, True))
+    prm = dict(theta_deg=70.0, sigma=0.01, d0=0.3, rho=(1.0, 2.0, 1.0), mu=(0.05, 0.05, 0.02))
+    compare_run(lbm_lib, "D3Q19", geo, prm, (False, False, True), 400, strip=4)
