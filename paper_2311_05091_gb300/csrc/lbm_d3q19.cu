@@ -120,6 +120,37 @@ __device__ __forceinline__ float lap3(const float* pm, const float* p0, const fl
   return axis * (1.f / 3.f) + edge * (1.f / 6.f);
 }
 
+// The same two operators on the 19 values v[d] = v(x + c_d), gathered once.
+__device__ __forceinline__ void gather19(const float* pm, const float* p0, const float* pp, int i, int sw,
+                                         float (&v)[Q]) {
+#pragma unroll
+  for (int d = 0; d < Q; ++d) v[d] = nb(pm, p0, pp, i, sw, d);
+}
+
+template <int A>
+__device__ __forceinline__ float dgrad_v(const float (&v)[Q]) {
+  float axis = 0.f, edge = 0.f;
+#pragma unroll
+  for (int d = 1; d < Q; ++d) {
+    const int c = CA(d, A);
+    if (c == 0) continue;
+    if (d < 7) axis += c > 0 ? v[d] : -v[d];
+    else edge += c > 0 ? v[d] : -v[d];
+  }
+  return axis * (1.f / 6.f) + edge * (1.f / 12.f);
+}
+
+__device__ __forceinline__ float lap_v(const float (&v)[Q]) {
+  float axis = 0.f, edge = 0.f;
+#pragma unroll
+  for (int d = 1; d < Q; ++d) {
+    const float w = v[d] - v[0];
+    if (d < 7) axis += w;
+    else edge += w;
+  }
+  return axis * (1.f / 3.f) + edge * (1.f / 6.f);
+}
+
 // mu_p = gamma_p psi_p, psi_p = (12/D) phi_p (1 - phi_p)(1 - 2 phi_p) - (3D/4) lap phi_p (Sec. 2.1).
 __device__ __forceinline__ void chem_pot(const InstanceConsts& k, float ph0, float ph1, float lap0,
                                          float lap1, float& mu0, float& mu1, float& mu2) {
@@ -303,26 +334,46 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
   const float cs2 = k.cs2, cs4 = k.cs4;
   const int i2 = R.i2, s2 = R.sw2, i1 = R.i1, s1 = R.sw1;
 
-  // stencils of phi0, phi1 and mubar_1, products
-  const float ph0 = R.p0[1][i2], ph1 = R.p1[1][i2], ph2 = 1.f - ph0 - ph1;
-  const float g0x = dgrad<0>(R.p0[0], R.p0[1], R.p0[2], i2, s2), g0y = dgrad<1>(R.p0[0], R.p0[1], R.p0[2], i2, s2),
-              g0z = dgrad<2>(R.p0[0], R.p0[1], R.p0[2], i2, s2);
-  const float g1x = dgrad<0>(R.p1[0], R.p1[1], R.p1[2], i2, s2), g1y = dgrad<1>(R.p1[0], R.p1[1], R.p1[2], i2, s2),
-              g1z = dgrad<2>(R.p1[0], R.p1[1], R.p1[2], i2, s2);
+  // stencils of phi0, phi1 and mubar_1, products; each neighbourhood is read once
+  float ph0, ph1, g0x, g0y, g0z, g1x, g1y, g1z, lap0, lap1;
+  {
+    float v[Q];
+    gather19(R.p0[0], R.p0[1], R.p0[2], i2, s2, v);
+    ph0 = v[0];
+    g0x = dgrad_v<0>(v);
+    g0y = dgrad_v<1>(v);
+    g0z = dgrad_v<2>(v);
+    lap0 = lap_v(v);
+    gather19(R.p1[0], R.p1[1], R.p1[2], i2, s2, v);
+    ph1 = v[0];
+    g1x = dgrad_v<0>(v);
+    g1y = dgrad_v<1>(v);
+    g1z = dgrad_v<2>(v);
+    lap1 = lap_v(v);
+  }
+  const float ph2 = 1.f - ph0 - ph1;
   float mu0, mu1, mu2;
-  chem_pot(k, ph0, ph1, lap3(R.p0[0], R.p0[1], R.p0[2], i2, s2), lap3(R.p1[0], R.p1[1], R.p1[2], i2, s2), mu0,
-           mu1, mu2);
+  chem_pot(k, ph0, ph1, lap0, lap1, mu0, mu1, mu2);
   const float d02 = mu0 - mu2, d12 = mu1 - mu2;
-  const float mub = R.mu[1][i1];
-  const float gmx = dgrad<0>(R.mu[0], R.mu[1], R.mu[2], i1, s1), gmy = dgrad<1>(R.mu[0], R.mu[1], R.mu[2], i1, s1),
-              gmz = dgrad<2>(R.mu[0], R.mu[1], R.mu[2], i1, s1);
-  // correction force F_c,b = 1/2 sum_a d_a (S_a u_b - u_a S_b), products A_xy, A_xz, A_yz
-  const float dAxy_x = dgrad<0>(R.ac[0][0], R.ac[0][1], R.ac[0][2], i1, s1);
-  const float dAxy_y = dgrad<1>(R.ac[0][0], R.ac[0][1], R.ac[0][2], i1, s1);
-  const float dAxz_x = dgrad<0>(R.ac[1][0], R.ac[1][1], R.ac[1][2], i1, s1);
-  const float dAxz_z = dgrad<2>(R.ac[1][0], R.ac[1][1], R.ac[1][2], i1, s1);
-  const float dAyz_y = dgrad<1>(R.ac[2][0], R.ac[2][1], R.ac[2][2], i1, s1);
-  const float dAyz_z = dgrad<2>(R.ac[2][0], R.ac[2][1], R.ac[2][2], i1, s1);
+  float mub, gmx, gmy, gmz, dAxy_x, dAxy_y, dAxz_x, dAxz_z, dAyz_y, dAyz_z;
+  {
+    float v[Q];
+    gather19(R.mu[0], R.mu[1], R.mu[2], i1, s1, v);
+    mub = v[0];
+    gmx = dgrad_v<0>(v);
+    gmy = dgrad_v<1>(v);
+    gmz = dgrad_v<2>(v);
+    // correction force F_c,b = 1/2 sum_a d_a (S_a u_b - u_a S_b), products A_xy, A_xz, A_yz
+    gather19(R.ac[0][0], R.ac[0][1], R.ac[0][2], i1, s1, v);
+    dAxy_x = dgrad_v<0>(v);
+    dAxy_y = dgrad_v<1>(v);
+    gather19(R.ac[1][0], R.ac[1][1], R.ac[1][2], i1, s1, v);
+    dAxz_x = dgrad_v<0>(v);
+    dAxz_z = dgrad_v<2>(v);
+    gather19(R.ac[2][0], R.ac[2][1], R.ac[2][2], i1, s1, v);
+    dAyz_y = dgrad_v<1>(v);
+    dAyz_z = dgrad_v<2>(v);
+  }
   const float Fcx = -0.5f * (dAxy_y + dAxz_z);
   const float Fcy = 0.5f * (dAxy_x - dAyz_z);
   const float Fcz = 0.5f * (dAxz_x + dAyz_y);
@@ -401,30 +452,22 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
   const float H = k.Kp * ((k.h0 - k.h2) * inv_s2a + k.h3);
   const float p = k.pf * (sum_nz + (0.5f + H) * udg - k.wq * q + 0.5f * k.Kp * (q - qp));
 
-  // push destinations; interior nodes use fixed offsets
-  const bool edge = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
+  // push destinations without branches: per axis and sign, the offset of the
+  // neighbour (periodic wrap folded in) and whether a wall reflects instead
+  const bool wxp = x + 1 >= nx && !o.per_x, wxm = x == 0 && !o.per_x;
+  const bool wyp = y + 1 >= ny && !o.per_y, wym = y == 0 && !o.per_y;
+  const bool wzp = z + 1 >= nz && !o.per_z, wzm = z == 0 && !o.per_z;
+  const int oxp = x + 1 < nx ? 1 : 1 - nx, oxm = x > 0 ? -1 : nx - 1;
+  const int oyp = y + 1 < ny ? nx : nx - plane, oym = y > 0 ? -nx : plane - nx;
+  const int ozp = z + 1 < nz ? plane : plane - nodes, ozm = z > 0 ? -plane : nodes - plane;
   auto store = [&](float* __restrict__ out, int i, float v) {
     const int cx = CX(i), cy = CY(i), cz = CZ(i);
-    if (!edge) {
-      out[i * nodes + node + cz * plane + cy * nx + cx] = v;
-      return;
-    }
-    int xd = x + cx, yd = y + cy, zd = z + cz;
+    int off = 0;
     bool bb = false;
-    if (xd < 0 || xd >= nx) {
-      if (o.per_x) xd = xd < 0 ? xd + nx : xd - nx;
-      else bb = true;
-    }
-    if (yd < 0 || yd >= ny) {
-      if (o.per_y) yd = yd < 0 ? yd + ny : yd - ny;
-      else bb = true;
-    }
-    if (zd < 0 || zd >= nz) {
-      if (o.per_z) zd = zd < 0 ? zd + nz : zd - nz;
-      else bb = true;
-    }
-    const int dst = bb ? OPP(i) * nodes + node : i * nodes + (zd * ny + yd) * nx + xd;
-    out[dst] = v;
+    if (cx) { off += cx > 0 ? oxp : oxm; bb = bb || (cx > 0 ? wxp : wxm); }
+    if (cy) { off += cy > 0 ? oyp : oym; bb = bb || (cy > 0 ? wyp : wym); }
+    if (cz) { off += cz > 0 ? ozp : ozm; bb = bb || (cz > 0 ? wzp : wzm); }
+    out[bb ? OPP(i) * nodes + node : i * nodes + node + off] = v;
   };
 
   // ---- NS collision: g* = (1 - s2a) g + w_i X_i (see the file header) ----
