@@ -148,25 +148,6 @@ __device__ __forceinline__ Nat natural_of(const Her& h, float cs2, float cs4) {
 
 
 
-// Push-stream v (direction i, opposite io) from (x, y); half-way bounce-back
-// sends a population that would leave through a wall back into slot io.
-__device__ __forceinline__ void push(float* __restrict__ out, long long plane, int i, int io, int cx, int cy,
-                                     int x, int y, int nx, int ny, int per_x, int per_y, float v) {
-  int xd = x + cx, yd = y + cy;
-  bool bb = false;
-  if (xd < 0 || xd >= nx) {
-    if (per_x) xd = xd < 0 ? xd + nx : xd - nx;
-    else bb = true;
-  }
-  if (yd < 0 || yd >= ny) {
-    if (per_y) yd = yd < 0 ? yd + ny : yd - ny;
-    else bb = true;
-  }
-  const long long dst = bb ? (long long)io * plane + (long long)y * nx + x
-                           : (long long)i * plane + (long long)yd * nx + xd;
-  out[dst] = v;
-}
-
 // ---------------------------------------------------------------------------
 // initial state: f = f^eq(phi1, mubar_1, u = 0), g = g^eq(p = 0, u = 0) - rho_0 e_0 = 0,
 // history = (phi1, 0, 0, 0, 0)
@@ -507,11 +488,18 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
       const float sum_nz = ng.m0 - g[0];
       const float p = k.pf * (sum_nz + (0.5f + H) * udg - k.wq * q + 0.5f * k.Kp * (q - qp));
 
-      // destinations of the nine pushes; interior nodes use fixed offsets
-      const bool edge = x == 0 || x == nx - 1 || y == 0 || y == ny - 1;
+      // destinations of the nine pushes without branches: per axis and sign the
+      // neighbour's offset (periodic wrap folded in) and whether a wall reflects
+      const bool wxp = x + 1 >= nx && !per_x, wxm = x == 0 && !per_x;
+      const bool wyp = y + 1 >= ny && !per_y, wym = y == 0 && !per_y;
+      const int oxp = x + 1 < nx ? 1 : 1 - nx, oxm = x > 0 ? -1 : nx - 1;
+      const int oyp = y + 1 < ny ? nx : nx - pl, oym = y > 0 ? -nx : pl - nx;
       auto store = [&](float* __restrict__ out, int i, int io, int cx, int cy, float v) {
-        if (!edge) out[i * pl + node + cy * nx + cx] = v;
-        else push(out, plane, i, io, cx, cy, x, y, nx, ny, per_x, per_y, v);
+        int off = 0;
+        bool bb = false;
+        if (cx) { off += cx > 0 ? oxp : oxm; bb = bb || (cx > 0 ? wxp : wxm); }
+        if (cy) { off += cy > 0 ? oyp : oym; bb = bb || (cy > 0 ? wyp : wym); }
+        out[bb ? io * pl + node : i * pl + node + off] = v;
       };
 
       // ---- NS collision in Hermite space ----
