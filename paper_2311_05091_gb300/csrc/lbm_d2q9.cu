@@ -208,36 +208,45 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+__device__ __forceinline__ int inc_mod(int v, int n) { return v + 1 == n ? 0 : v + 1; }
+
 constexpr int PAD = 4;          // own columns start 16 bytes into each slot row
 constexpr int W = BX + 2 * PAD; // slot row width
-constexpr int NARR = 24;        // f (9), phi0, history (5), g (9)
 
-// one row of every array the step reads; array a of the slot is rows[a]:
-// 0-8 f, 9 phi0, 10-14 history (phi1, ux, uy, Sx, Sy), 15-23 g
-struct RowSlot {
-  float rows[NARR][W];
+// Rows staged by asynchronous copies, one ring per group of arrays, each as
+// deep as that group's rows live: f and phi0 only feed stage 1 (phi1 = sum f
+// of row y+2, first moment j of the owned columns), the history feeds stage 2
+// (row y+1) and stage 3 (row y), g only stage 3.
+struct ARow {
+  float rows[10][W];   // f 0-8, phi0 9; two halo columns each side
+};
+struct HRow {
+  float rows[5][W];    // history phi1, ux, uy, Sx, Sy; one halo column each side
+};
+struct GRow {
+  float rows[9][W];    // g, owned columns
 };
 
 template <int D>
 struct StepSmem {
-  RowSlot slot[D + 3];
+  ARow a[D + 1];
+  HRow h[D + 2];
+  GRow g[D + 1];
   float phi1[RP][BX + 4];
   float phi0[RP][BX + 4];
   float mub[RM][BX + 2];
   float acorr[RM][BX + 2];   // S_x u_y - u_x S_y of the previous step
+  float jr[3][2][BX];        // j = sum_i c_i f_i of rows y, y+1, y+2 (owned columns)
   InstanceConsts k;
 };
 
 template <int D>
 constexpr size_t step_smem_bytes() { return sizeof(StepSmem<D>); }
 
-__device__ __forceinline__ int inc_mod(int v, int n) { return v + 1 == n ? 0 : v + 1; }
-
 template <bool OBS, int D>
 __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<D>& S = *reinterpret_cast<StepSmem<D>*>(smem_raw);
-  constexpr int R = D + 3;
 
   const int t = threadIdx.x;
   const int x0 = blockIdx.x * BX;
@@ -261,6 +270,11 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
   auto src_plane = [&](int arr) -> const float* {
     return arr < 9 ? f_in + arr * plane
                    : (arr == 9 ? p0_in : (arr < 15 ? h_in + (arr - 10) * plane : g_in + (arr - 15) * plane));
+  };
+  // destination row of array arr in the slots of rows ra (f, phi0), rh (history), rg (g)
+  auto dst_row = [&](int arr, int ra, int rh, int rg) -> float* {
+    return arr < 10 ? S.a[ring(ra, D + 1)].rows[arr]
+                    : (arr < 15 ? S.h[ring(rh, D + 2)].rows[arr - 10] : S.g[ring(rg, D + 1)].rows[arr - 15]);
   };
 
   const bool vec16 = (nx & 3) == 0;
@@ -289,61 +303,70 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
   const int h_px = wrap_or_mirror(h_xl, nx, per_x);
   const float* __restrict__ h_src = h_arr >= 0 ? src_plane(h_arr) : f_in;
 
-  // issue the asynchronous copies of logical row r into slot sl
-  auto issue = [&](int r, int sl) {
-    if (r <= ye + 1) {
-      RowSlot& slot = S.slot[sl];
-      const long long rowb = (long long)wrap_or_mirror(r, ny, per_y) * nx;
-      const bool own_row = r >= ys && r < ye;
-      if (vec16) {
-        // chunk m of this thread: array (t >> 5) + 4 m, columns x0 + 4 (t & 31) .. + 3
-        const int j = t & 31;
-        const int xc = x0 + 4 * j;
-        if (xc < nx) {
+  // The copies issued for iteration target q: f / phi0 of row q+2, history of
+  // row q+1, g of row q -- each only where a later stage reads it.
+  auto issue = [&](int q) {
+    const int ra = q + 2, rh = q + 1, rg = q;
+    const bool need_a = ra >= ys - 2 && ra <= ye + 1;
+    const bool need_h = rh >= ys - 1 && rh <= ye;
+    const bool need_g = rg >= ys && rg < ye;
+    const int ba = wrap_or_mirror(ra, ny, per_y) * nx;
+    const int bh = wrap_or_mirror(rh, ny, per_y) * nx;
+    const int bg = wrap_or_mirror(rg, ny, per_y) * nx;
+    auto need = [&](int arr) { return arr < 10 ? need_a : (arr < 15 ? need_h : need_g); };
+    auto rowb = [&](int arr) { return arr < 10 ? ba : (arr < 15 ? bh : bg); };
+    if (vec16) {
+      // chunk m of this thread: array (t >> 5) + 4 m, columns x0 + 4 (t & 31) .. + 3
+      const int j = t & 31;
+      const int xc = x0 + 4 * j;
+      if (xc < nx) {
 #pragma unroll
-          for (int m = 0; m < 6; ++m) {
-            const int arr = (t >> 5) + 4 * m;
-            if (arr < 15 || own_row) cp_async16(&slot.rows[arr][PAD + 4 * j], src_plane(arr) + rowb + xc);
-          }
+        for (int m = 0; m < 6; ++m) {
+          const int arr = (t >> 5) + 4 * m;
+          if (need(arr)) cp_async16(dst_row(arr, ra, rh, rg) + PAD + 4 * j, src_plane(arr) + rowb(arr) + xc);
         }
-      } else if (x < nx) {
-#pragma unroll
-        for (int arr = 0; arr < NARR; ++arr)
-          if (arr < 15 || own_row) cp_async4(&slot.rows[arr][PAD + t], src_plane(arr) + rowb + x);
       }
-      if (h_active) cp_async4(&slot.rows[h_arr][h_col], h_src + rowb + h_px);
+    } else if (x < nx) {
+#pragma unroll
+      for (int arr = 0; arr < 24; ++arr)
+        if (need(arr)) cp_async4(dst_row(arr, ra, rh, rg) + PAD + t, src_plane(arr) + rowb(arr) + x);
     }
+    if (h_active && need(h_arr)) cp_async4(dst_row(h_arr, ra, rh, rg) + h_col, h_src + rowb(h_arr) + h_px);
     cp_commit();   // empty groups keep the group count uniform
   };
 
   const InstanceConsts& k = S.k;
-  // rotating ring indices of rows y-1, y, y+1, y+2 (phi rings) and y-1, y, y+1 (mubar rings)
-  int pm = ring(ys - 1, RP), p0 = ring(ys, RP), pp = ring(ys + 1, RP), pq = ring(ys + 2, RP);
-  int mm = ring(ys - 1, RM), m0 = ring(ys, RM), mp = ring(ys + 1, RM);
-  // slot of rows ys-2 + q is q mod R
 
-  // stage 1: phi1 = sum f and phi0 of the row in slot sl into phi ring row sp.
-  // After the wait and a barrier every thread sees the whole slot.
-  auto stage1 = [&](int sl, int sp) {
-    const RowSlot& slot = S.slot[sl];
+  // stage 1: phi1 = sum f and phi0 of row r into phi ring row sp; j of the owned columns.
+  auto stage1 = [&](int r, int sp) {
+    const ARow& slot = S.a[ring(r, D + 1)];
+    float(&jr)[2][BX] = S.jr[ring(r, 3)];
     auto one = [&](int c) {
       const int xl = x0 - 2 + c;
       if (xl > nx + 1) return;
       const int col = c + PAD - 2;
-      float sum = slot.rows[0][col];
+      float v[9];
 #pragma unroll
-      for (int i = 1; i < 9; ++i) sum += slot.rows[i][col];
+      for (int i = 0; i < 9; ++i) v[i] = slot.rows[i][col];
+      float sum = v[0];
+#pragma unroll
+      for (int i = 1; i < 9; ++i) sum += v[i];
       S.phi1[sp][c] = sum;
       S.phi0[sp][c] = slot.rows[9][col];
+      if (c >= 2 && c < BX + 2) {
+        jr[0][c - 2] = (v[1] - v[3]) + (v[5] - v[6]) - (v[7] - v[8]);
+        jr[1][c - 2] = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+      }
     };
     one(t);
     if ((t & 31) == 0) one(BX + (t >> 5));   // the four extra columns, one per warp
   };
 
-  // stage 2: mubar_1 and the correction-force product of the row in slot sl;
-  // returns mu0 - mu2 and mu1 - mu2 of this thread's own column
-  auto stage2 = [&](int sl, int cm, int cp, int cq, int sm, float& d02, float& d12) {
-    const RowSlot& slot = S.slot[sl];
+  // stage 2: mubar_1 and the correction-force product of row r (phi ring rows
+  // cm, cp, cq = r-1, r, r+1) into mubar ring row sm; returns mu0 - mu2 and
+  // mu1 - mu2 of this thread's own column
+  auto stage2 = [&](int r, int cm, int cp, int cq, int sm, float& d02, float& d12) {
+    const HRow& slot = S.h[ring(r, D + 2)];
     const float* A1m = S.phi1[cm];
     const float* A1p = S.phi1[cp];
     const float* A1q = S.phi1[cq];
@@ -360,7 +383,7 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
       chem_pot(k, v0.c, v1.c, iso_lap(v0), iso_lap(v1), mu0, mu1, mu2);
       S.mub[sm][s] = mubar1_of(k, mu0, mu1, mu2);
       const int col = s + PAD - 1;
-      S.acorr[sm][s] = slot.rows[13][col] * slot.rows[12][col] - slot.rows[11][col] * slot.rows[14][col];
+      S.acorr[sm][s] = slot.rows[3][col] * slot.rows[2][col] - slot.rows[1][col] * slot.rows[4][col];
       if (own) {
         d02 = mu0 - mu2;
         d12 = mu1 - mu2;
@@ -371,57 +394,38 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
     if (t == 96) one(BX + 1, false);
   };
 
-  // prologue: copies of rows ys-2 .. ys+D, phi rows ys-2 .. ys+1, mubar rows ys-1, ys
-  for (int q = 0; q < R; ++q) issue(ys - 2 + q, q);
+  // The sweep starts four iterations early: iterations ys-4 .. ys-1 only run
+  // the stages whose rows exist (stage 1 from row ys-2, stage 2 from row ys-1).
+  const int yb = ys - 4;
+  for (int q = yb; q < yb + D; ++q) issue(q);
   __syncthreads();   // constants visible
-  cp_wait<R - 1>();
-  __syncthreads();
-  stage1(0, ring(ys - 2, RP));
-  __syncthreads();   // slot 0 read by all threads before it is refilled
-  issue(ys + 1 + D, 0);
-  cp_wait<R - 1>();
-  __syncthreads();
-  stage1(1, pm);
-  cp_wait<R - 2>();
-  __syncthreads();
-  stage1(2, p0);
-  cp_wait<R - 3>();
-  __syncthreads();
-  stage1(3 % R, pp);
-  __syncthreads();
+  // rotating ring indices of rows y-1, y, y+1, y+2 (phi rings) and y-1, y, y+1 (mubar rings)
+  int pm = ring(yb - 1, RP), p0 = ring(yb, RP), pp = ring(yb + 1, RP), pq = ring(yb + 2, RP);
+  int mm = ring(yb - 1, RM), m0 = ring(yb, RM), mp = ring(yb + 1, RM);
   float d02 = 0.f, d12 = 0.f;       // mu differences of this thread's column, row y
-  {
-    float u02, u12;
-    stage2(1, ring(ys - 2, RP), pm, p0, mm, u02, u12);
-    stage2(2, pm, p0, pp, m0, d02, d12);
-  }
-  __syncthreads();
-
-  int sl_y = 2 % R;            // slot of row y
-  int sl_q = 4 % R;            // slot of row y+2
-  int sl_n = (4 + D) % R;      // slot that receives row y+2+D (it held row y-1)
-  for (int y = ys; y < ye; ++y) {
-    cp_wait<D - 1>();          // row y+2 has landed
-    __syncthreads();           // ... for every thread, and row y-1 is no longer read
-    issue(y + 2 + D, sl_n);
-    stage1(sl_q, pq);
+  for (int y = yb; y < ye; ++y) {
+    cp_wait<D - 1>();          // rows of target y have landed
+    __syncthreads();           // ... for every thread, and the slots refilled next are no longer read
+    issue(y + D);
+    stage1(y + 2, pq);
     __syncthreads();
     float n02 = 0.f, n12 = 0.f;
-    stage2((sl_y + 1) % R, p0, pp, pq, mp, n02, n12);
+    if (y + 1 >= ys - 1) stage2(y + 1, p0, pp, pq, mp, n02, n12);
     __syncthreads();
 
     // ---------------- stage 3: collide and stream row y ----------------
-    if (x < nx) {
-      const RowSlot& sl = S.slot[sl_y];
+    if (y >= ys && x < nx) {
+      const GRow& gs = S.g[ring(y, D + 1)];
+      const HRow& hs = S.h[ring(y, D + 2)];
       const int c = t + 2, s = t + 1, col = t + PAD;
       const int node = y * nx + x;         // instance-relative, < 2^31 (checked at creation)
       const int pl = (int)plane;
       const float cs2 = k.cs2, cs4 = k.cs4;
       float g[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) g[i] = sl.rows[15 + i][col];
-      const float php = sl.rows[10][col], uxp = sl.rows[11][col], uyp = sl.rows[12][col];
-      const float Sxp = sl.rows[13][col], Syp = sl.rows[14][col];
+      for (int i = 0; i < 9; ++i) g[i] = gs.rows[i][col];
+      const float php = hs.rows[0][col], uxp = hs.rows[1][col], uyp = hs.rows[2][col];
+      const float Sxp = hs.rows[3][col], Syp = hs.rows[4][col];
 
       const float* B1m = S.phi1[pm] + c;
       const float* B10 = S.phi1[p0] + c;
@@ -541,11 +545,7 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
 
       // ---- CH collision ----
       {
-        float fv[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fv[i] = sl.rows[i][col];
-        Nat nf = natural(fv);
-        nf.m0 = ph1;   // zeroth moment is the phase field itself
+        const float jx = S.jr[ring(y, 3)][0][t], jy = S.jr[ring(y, 3)][1][t];
         const float emb = k.eta * mub;
         const float corr = k.corr_scale * (1.f - fdeg);
         // R first moment: d_t(phi1 u) + cs2 * corr * eta grad mubar
@@ -555,8 +555,8 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
         if (k.ch_fast != 0.f) {
           // every moment but the first relaxes at rate 1, so f* = f^eq + w_i c_i . dj / cs2 with
           // the post-collision first moment o = phi u + (1 - s1)(j - phi u) + (1 - s1/2) R
-          const float ox = ph1 * ux + (1.f - k.s1c) * (nf.mx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx;
-          const float oy = ph1 * uy + (1.f - k.s1c) * (nf.my - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry;
+          const float ox = ph1 * ux + (1.f - k.s1c) * (jx - ph1 * ux) + (1.f - 0.5f * k.s1c) * Rx;
+          const float oy = ph1 * uy + (1.f - k.s1c) * (jy - ph1 * uy) + (1.f - 0.5f * k.s1c) * Ry;
           const float ic = __frcp_rn(cs2);
           const float ax = ox * ic, ay = oy * ic;
           fo[1] = k.wa * (emb + ax);
@@ -570,6 +570,12 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
           // rest population closes the zeroth moment exactly
           fo[0] = ph1 - (((fo[1] + fo[3]) + (fo[2] + fo[4])) + ((fo[5] + fo[7]) + (fo[6] + fo[8])));
         } else {
+          // every moment enters: the populations of this node again (L2-resident)
+          float fv[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) fv[i] = f_in[i * pl + node];
+          Nat nf = natural(fv);
+          nf.m0 = ph1;   // zeroth moment is the phase field itself
           const Her h = hermite(nf, cs2, cs4);
           const float exx = cs2 * (emb - ph1);
           Her o;
@@ -612,9 +618,6 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
     // rotate the rings to row y+1
     pm = p0; p0 = pp; pp = pq; pq = inc_mod(pq, RP);
     mm = m0; m0 = mp; mp = inc_mod(mp, RM);
-    sl_y = inc_mod(sl_y, R);
-    sl_q = inc_mod(sl_q, R);
-    sl_n = inc_mod(sl_n, R);
   }
   cp_wait<0>();
 }
