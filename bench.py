@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=60.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS))
     ap.add_argument("--size", type=int, default=None, help="lattice side (default: the workload's)")
+    ap.add_argument("--tte-steps", type=int, default=20000,
+                    help="steps of the time-to-equilibrium run (disk workload; 0 skips it)")
+    ap.add_argument("--tte-every", type=int, default=100, help="contact-angle sampling interval")
     return ap.parse_args()
 
 
@@ -232,11 +235,13 @@ def barrier(world):
 
 
 def max_over_ranks(world, v):
+    """Maximum of a host scalar over the ranks (NCCL on the GPU path, gloo on CPU)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -263,6 +268,45 @@ def run_reference(args):
         line["note"] = "rank 0 alone runs the CPU reference"
     print(json.dumps(line), flush=True)
     return 0
+
+
+def time_to_equilibrium(ctx, wl, h_phi0, h_phi1, step_ms, total, every, tol_deg=0.5):
+    """Contact-angle history of every instance from t = 0, sampled every `every` steps.
+
+    theta is measured as in Sec. 4.3 (height of the phi1 = 1/2 contour above
+    the disk centre on the drop's symmetry column, inverted through the
+    two-circle area relation).  The equilibrium angle of an instance is its
+    last sample; its time to equilibrium is the first sample from which every
+    later sample stays within tol_deg of it (at least five samples).
+    """
+    geo = wl["geometry"]
+    xc, yc = geo.disk_center
+    Rs = geo.disk_radius
+    nb = len(wl["params"])
+    ctx.set_solid(h_phi0)
+    ctx.set_phase(h_phi1)
+    th = [[] for _ in range(nb)]
+    um = [[] for _ in range(nb)]
+    for _ in range(total // every):
+        ctx.step(every)
+        for i in range(nb):
+            t, _h = ctx.contact_angle(i, 1, int(round(xc)), float(yc), float(Rs))
+            th[i].append(t)
+            um[i].append(ctx.observables(i)["umax"])
+    out = {"criterion": f"first sample after which theta stays within {tol_deg} deg of its value after {total} "
+                        f"steps (sampled every {every} steps)",
+           "steps_run": total, "sample_every": every, "instances": []}
+    for i in range(nb):
+        eq = th[i][-1]
+        k = len(th[i]) - 1
+        while k > 0 and abs(th[i][k - 1] - eq) <= tol_deg:
+            k -= 1
+        steps = (k + 1) * every if len(th[i]) - k >= 5 else None   # None: not settled within the run
+        out["instances"].append({"theta_in": wl["params"][i]["theta_deg"], "theta_eq": eq,
+                                 "theta_err_deg": eq - wl["params"][i]["theta_deg"], "steps": steps,
+                                 "ms": None if steps is None else steps * step_ms, "umax_at_eq": um[i][k],
+                                 "umax_end": um[i][-1]})
+    return out
 
 
 def run_gpu(args):
@@ -342,6 +386,9 @@ def run_gpu(args):
     e2e_s = max_over_ranks(world, e2e_s)
     e2e = world * lu * args.steps / e2e_s / 1e6
     obs = ctx.observables(0)
+    tte = None
+    if d == 2 and args.tte_steps > 0 and wl["geometry"].disk_center is not None:
+        tte = time_to_equilibrium(ctx, wl, h_phi0, h_phi1, ms / args.steps, args.tte_steps, args.tte_every)
     ctx.close()
 
     if rank != 0:
@@ -384,6 +431,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "check": {"mass1": obs["mass1"], "umax": obs["umax"], "dp": obs["dp"]},
+        "time_to_equilibrium": tte,
     }
     if d == 3:
         line["roofline"]["moment_pass_ms_per_launch"] = moment_ms / max(nk, 1)
