@@ -70,9 +70,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=60.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS))
     ap.add_argument("--size", type=int, default=None, help="lattice side (default: the workload's)")
-    ap.add_argument("--tte-steps", type=int, default=20000,
+    ap.add_argument("--tte-size", type=int, default=256, help="lattice side of the time-to-equilibrium run")
+    ap.add_argument("--tte-steps", type=int, default=150000,
                     help="steps of the time-to-equilibrium run (disk workload; 0 skips it)")
-    ap.add_argument("--tte-every", type=int, default=100, help="contact-angle sampling interval")
+    ap.add_argument("--tte-every", type=int, default=2500, help="contact-angle sampling interval")
     return ap.parse_args()
 
 
@@ -270,32 +271,51 @@ def run_reference(args):
     return 0
 
 
-def time_to_equilibrium(ctx, wl, h_phi0, h_phi1, step_ms, total, every, tol_deg=0.5):
-    """Contact-angle history of every instance from t = 0, sampled every `every` steps.
+def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5):
+    """Contact-angle relaxation of the disk + droplet sweep on a size^2 lattice.
 
-    theta is measured as in Sec. 4.3 (height of the phi1 = 1/2 contour above
-    the disk centre on the drop's symmetry column, inverted through the
-    two-circle area relation).  The equilibrium angle of an instance is its
-    last sample; its time to equilibrium is the first sample from which every
-    later sample stays within tol_deg of it (at least five samples).
+    The five instances start from the droplet of the workload recipe (scaled
+    to size / 1024) and run `total` steps; theta is measured every `every`
+    steps as in Sec. 4.3 (height of the phi1 = 1/2 contour above the disk
+    centre on the drop's symmetry column, inverted through the two-circle
+    area relation).  The equilibrium angle of an instance is its last sample;
+    its time to equilibrium is the first sample from which every later sample
+    stays within tol_deg of it (at least five samples, else None).  Wall time
+    = steps x the device time per step of the same lattice.
     """
+    import torch
+    wl = make_workload("disk1024x5", size)
     geo = wl["geometry"]
     xc, yc = geo.disk_center
     Rs = geo.disk_radius
     nb = len(wl["params"])
-    ctx.set_solid(h_phi0)
-    ctx.set_phase(h_phi1)
-    th = [[] for _ in range(nb)]
-    um = [[] for _ in range(nb)]
-    for _ in range(total // every):
-        ctx.step(every)
-        for i in range(nb):
-            t, _h = ctx.contact_angle(i, 1, int(round(xc)), float(yc), float(Rs))
-            th[i].append(t)
-            um[i].append(ctx.observables(i)["umax"])
-    out = {"criterion": f"first sample after which theta stays within {tol_deg} deg of its value after {total} "
-                        f"steps (sampled every {every} steps)",
-           "steps_run": total, "sample_every": every, "instances": []}
+    ctx = L.Context(L.LBM_D2Q9, size, size, 1, periodic=(True, True, False),
+                    batch=[L.lbm_default_params(**p) for p in wl["params"]])
+    try:
+        ctx.set_stream(stream.cuda_stream)
+        ctx.set_solid(wl["phi0"])
+        ctx.set_phase(wl["phi1"])
+        ctx.step(64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(4096)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms = e0.elapsed_time(e1) / 4096
+        ctx.set_phase(wl["phi1"])   # restart from t = 0
+        th = [[] for _ in range(nb)]
+        um = [[] for _ in range(nb)]
+        for _ in range(total // every):
+            ctx.step(every)
+            for i in range(nb):
+                t, _h = ctx.contact_angle(i, 1, int(round(xc)), float(yc), float(Rs))
+                th[i].append(t)
+                um[i].append(ctx.observables(i)["umax"])
+    finally:
+        ctx.close()
+    out = {"workload": wl["name"], "criterion": f"first sample after which theta stays within {tol_deg} deg of "
+                                                f"its value after {total} steps (sampled every {every} steps)",
+           "steps_run": total, "sample_every": every, "ms_per_step": step_ms, "instances": []}
     for i in range(nb):
         eq = th[i][-1]
         k = len(th[i]) - 1
@@ -386,10 +406,10 @@ def run_gpu(args):
     e2e_s = max_over_ranks(world, e2e_s)
     e2e = world * lu * args.steps / e2e_s / 1e6
     obs = ctx.observables(0)
-    tte = None
-    if d == 2 and args.tte_steps > 0 and wl["geometry"].disk_center is not None:
-        tte = time_to_equilibrium(ctx, wl, h_phi0, h_phi1, ms / args.steps, args.tte_steps, args.tte_every)
     ctx.close()
+    tte = None
+    if d == 2 and args.tte_steps > 0 and rank == 0:
+        tte = time_to_equilibrium(L, stream, args.tte_size, args.tte_steps, args.tte_every)
 
     if rank != 0:
         return 0
