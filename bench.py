@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=60.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS))
     ap.add_argument("--size", type=int, default=None, help="lattice side (default: the workload's)")
+    ap.add_argument("--g-f16", action="store_true",
+                    help="store the NS populations as FP16 (D2Q9; float32 arithmetic and CH populations)")
     ap.add_argument("--tte-size", type=int, default=256, help="lattice side of the time-to-equilibrium run")
     ap.add_argument("--tte-steps", type=int, default=150000,
                     help="steps of the time-to-equilibrium run (disk workload; 0 skips it)")
@@ -271,7 +273,7 @@ def run_reference(args):
     return 0
 
 
-def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5):
+def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5, flags=0):
     """Contact-angle relaxation of the disk + droplet sweep on a size^2 lattice.
 
     The five instances start from the droplet of the workload recipe (scaled
@@ -290,7 +292,7 @@ def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5):
     Rs = geo.disk_radius
     nb = len(wl["params"])
     ctx = L.Context(L.LBM_D2Q9, size, size, 1, periodic=(True, True, False),
-                    batch=[L.lbm_default_params(**p) for p in wl["params"]])
+                    batch=[L.lbm_default_params(**p) for p in wl["params"]], flags=flags)
     try:
         ctx.set_stream(stream.cuda_stream)
         ctx.set_solid(wl["phi0"])
@@ -339,7 +341,14 @@ def run_gpu(args):
     build()
     from paper_2311_05091_gb300 import _lbm as L
 
-    spec = WORKLOADS[args.workload]
+    spec = dict(WORKLOADS[args.workload])
+    flags = 0
+    if args.g_f16:
+        if spec["lattice"] != "D2Q9":
+            raise SystemExit("--g-f16 is built for the D2Q9 workload")
+        flags = L.LBM_STORE_G_F16
+        # NS populations 2 bytes: f, g read + write 72 + 36; phi0 4; history 40
+        spec.update(bytes_per_lu=152, kernel_bytes_per_lu=152, profile="d2q9_step_f16_disk1024x5.md")
     wl = make_workload(args.workload, args.size)
     nb = len(wl["params"])
     nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]
@@ -349,7 +358,7 @@ def run_gpu(args):
     lattice = L.LBM_D2Q9 if d == 2 else L.LBM_D3Q19
     stream = torch.cuda.Stream()
     ctx = L.Context(lattice, nx, ny, nz, periodic=tuple(wl["periodic"]),
-                    batch=[L.lbm_default_params(**p) for p in wl["params"]])
+                    batch=[L.lbm_default_params(**p) for p in wl["params"]], flags=flags)
     ctx.set_stream(stream.cuda_stream)
 
     # pinned host copies of the inputs and outputs (used by the end-to-end leg)
@@ -409,7 +418,7 @@ def run_gpu(args):
     ctx.close()
     tte = None
     if d == 2 and args.tte_steps > 0 and rank == 0:
-        tte = time_to_equilibrium(L, stream, args.tte_size, args.tte_steps, args.tte_every)
+        tte = time_to_equilibrium(L, stream, args.tte_size, args.tte_steps, args.tte_every, flags=flags)
 
     if rank != 0:
         return 0
@@ -428,6 +437,8 @@ def run_gpu(args):
            "lu_per_step": lu, "bytes_per_lu": spec["bytes_per_lu"],
            "l2": f"no flush: each step moves about {2 * rw:.2f} GB through HBM (> 129 MB L2)",
            "parallelism": f"weak, {world} x independent copies of the workload"}
+    cfg["storage"] = ("NS populations FP16 (g * 2^12), CH populations and arithmetic float32" if flags
+                      else "float32 populations")
     if d == 2:
         cfg.update(density_ratio=10, viscosity_ratio=10)
     else:

@@ -134,6 +134,21 @@ int lbm_create(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask,
 int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask,
                      int nbatch, const lbm_params* params, lbm_ctx** out);
 
+/* Storage options of lbm_create_ex. */
+enum {
+  /* NS populations g stored in HBM as IEEE FP16 holding g * 2^12 (the rest
+   * population already shifted by rho_0), arithmetic in float32; the CH
+   * populations stay float32, so the conserved phase field keeps float32
+   * rounding.  D2Q9 only, nx % 8 == 0 (LBM_EUNSUPPORTED / LBM_EINVAL
+   * otherwise).  Relative storage error 2^-11 per value per step; no pattern
+   * of the paper, a bandwidth option: 188 -> 152 bytes per lattice update. */
+  LBM_STORE_G_F16 = 1
+};
+
+/* lbm_create_batch with storage options (0 or LBM_STORE_G_F16). */
+int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask,
+                  int nbatch, const lbm_params* params, int flags, lbm_ctx** out);
+
 /* Free all device memory of the context.  Safe on NULL. */
 void lbm_destroy(lbm_ctx* ctx);
 
@@ -193,15 +208,17 @@ int lbm_get_fields(lbm_ctx* ctx, float* phi1, float* u, float* p);
 /* Current populations f (CH) and g (NS), host buffers of nbatch*Q*nodes
  * floats.  The rest population g_0 is stored minus the constant rho_0 of the
  * pressure equilibrium (lambda_0, Sec. 3), which the dynamics do not depend
- * on.  Either pointer may be NULL.  Synchronous. */
+ * on.  With LBM_STORE_G_F16, g is converted back to float32 (unscaled).
+ * Either pointer may be NULL.  Synchronous. */
 int lbm_get_populations(lbm_ctx* ctx, float* f, float* g);
 
 /* Checkpoint: the whole evolving state (populations, history, step count) as
  * a byte image: a 64-byte header (uint32 magic "LBM1", int32 lattice, nx, ny,
- * nz, nbatch, q, d, int64 step, int64 nodes, 16 bytes padding) followed by
- * float32 f [b][i][nodes], g [b][i][nodes] (g_0 minus rho_0) and the history
- * [b][k][nodes] with k = phi1, u (d components), S (d components) of the last
- * step.  With buf == NULL, *bytes receives the size.  lbm_set_state restores
+ * nz, nbatch, q, d, int64 step, int64 nodes, int32 g storage (0 float32, 1
+ * FP16 scaled by 2^12), 12 bytes padding) followed by float32 f [b][i][nodes],
+ * g [b][i][nodes] in its storage type (g_0 minus rho_0) and the float32
+ * history [b][k][nodes] with k = phi1, u (d components), S (d components) of
+ * the last step.  With buf == NULL, *bytes receives the size.  lbm_set_state restores
  * an image taken from a context of the same shape; a run continued after
  * restore is bitwise identical. */
 int lbm_get_state(lbm_ctx* ctx, void* buf, size_t* bytes);

@@ -19,12 +19,13 @@ c_float_p = ctypes.POINTER(ctypes.c_float)
 
 LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_PERIODIC_X, LBM_PERIODIC_Y, LBM_PERIODIC_Z = 1, 2, 4
+LBM_STORE_G_F16 = 1
 STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_EDIVERGED",
           -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE", -7: "LBM_EUNSUPPORTED"}
 
 # every symbol include/lbm.h declares
 EXPORTS = [
-    "lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy", "lbm_set_stream",
+    "lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_create_ex", "lbm_destroy", "lbm_set_stream",
     "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
     "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
     "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_kernel_time_split", "lbm_observables_noalloc",
@@ -71,6 +72,8 @@ def library():
         "lbm_create": (c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(lbm_params), ctypes.POINTER(P)]),
         "lbm_create_batch": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(lbm_params),
                                      ctypes.POINTER(P)]),
+        "lbm_create_ex": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(lbm_params), c_int,
+                                  ctypes.POINTER(P)]),
         "lbm_destroy": (None, [P]),
         "lbm_set_stream": (c_int, [P, P]),
         "lbm_set_launch": (c_int, [P, c_int, c_int]),
@@ -145,6 +148,14 @@ def lbm_create_batch(lattice, nx, ny, nz, periodic_mask, params_list):
     out = c_void_p()
     _check(library().lbm_create_batch(lattice, nx, ny, nz, periodic_mask, len(params_list), arr,
                                       ctypes.byref(out)), "lbm_create_batch")
+    return out
+
+
+def lbm_create_ex(lattice, nx, ny, nz, periodic_mask, params_list, flags):
+    arr = (lbm_params * len(params_list))(*params_list)
+    out = c_void_p()
+    _check(library().lbm_create_ex(lattice, nx, ny, nz, periodic_mask, len(params_list), arr, flags,
+                                   ctypes.byref(out)), "lbm_create_ex")
     return out
 
 
@@ -279,10 +290,13 @@ def lbm_strerror(status) -> str:
 class Context:
     """Owns one lbm_ctx; each method forwards to the C call of the same name."""
 
-    def __init__(self, lattice, nx, ny, nz=1, periodic=(True, True, True), params=None, batch=None):
+    def __init__(self, lattice, nx, ny, nz=1, periodic=(True, True, True), params=None, batch=None, flags=0):
         mask = sum(bit for bit, on in zip((1, 2, 4), periodic) if on)
         self.shape = (nx, ny, nz)
-        if batch is not None:
+        if flags:
+            plist = batch if batch is not None else [params if params is not None else lbm_default_params()]
+            self.ctx = lbm_create_ex(lattice, nx, ny, nz, mask, plist, flags)
+        elif batch is not None:
             self.ctx = lbm_create_batch(lattice, nx, ny, nz, mask, batch)
         else:
             self.ctx = lbm_create(lattice, nx, ny, nz, mask, params if params is not None else lbm_default_params())

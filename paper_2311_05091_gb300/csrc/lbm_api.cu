@@ -4,6 +4,7 @@
 // the host; the device receives one float32 InstanceConsts record per batch
 // instance.  All device work goes to the context's stream; graphs of
 // kGraphSteps steps are captured once per starting buffer and replayed.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -48,7 +49,9 @@ struct lbm_ctx {
   std::vector<InstanceConsts> hconsts;
   InstanceConsts* dconsts = nullptr;
   float* f[2] = {nullptr, nullptr};
-  float* g[2] = {nullptr, nullptr};
+  void* g[2] = {nullptr, nullptr};   // NS populations: float, or FP16 scaled by gsc (g_half)
+  int g_half = 0;
+  size_t g_elem = sizeof(float);
   float* hist[2] = {nullptr, nullptr};
   float* phi0 = nullptr;
   float* p = nullptr;
@@ -165,6 +168,9 @@ int derive(const lbm_params& p, int lattice, InstanceConsts& k, char* why) {
   k.s1c = (float)s1c;
   k.s0c = k.s2ac = k.s2bc = k.s3c = k.s4c = (float)p.s_free_ch;
   k.ch_fast = p.s_free_ch == 1.0 ? 1.0f : 0.0f;
+  // FP16 storage scale of the NS populations: 2^12 maps |g| in [1.5e-8, 16] onto normal FP16 numbers
+  k.gsc = 4096.0f;
+  k.gsci = 1.0f / 4096.0f;
   k.s1n = k.s3n = (float)p.s_free_ns;
   k.rho0 = (float)p.rho[0];
   k.rho1 = (float)p.rho[1];
@@ -227,6 +233,7 @@ StepArgs step_args(lbm_ctx* c, int from) {
   a.strip = c->strip;
   a.depth = c->depth;
   a.nodes = c->nodes;
+  a.g_half = c->g_half;
   return a;
 }
 
@@ -399,10 +406,15 @@ int lbm_default_params(lbm_params* p) {
   return LBM_OK;
 }
 
-int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, int nbatch,
-                     const lbm_params* params, lbm_ctx** out) {
+int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, int nbatch,
+                  const lbm_params* params, int flags, lbm_ctx** out) {
   if (!out) return set_err(nullptr, LBM_EINVAL, "out is NULL");
   *out = nullptr;
+  if (flags & ~LBM_STORE_G_F16) return set_err(nullptr, LBM_EINVAL, "unknown flag");
+  const int g_half = (flags & LBM_STORE_G_F16) ? 1 : 0;
+  if (g_half && lattice != LBM_D2Q9)
+    return set_err(nullptr, LBM_EUNSUPPORTED, "FP16 population storage is built for D2Q9 only");
+  if (g_half && nx % 8 != 0) return set_err(nullptr, LBM_EINVAL, "FP16 population storage needs nx % 8 == 0");
   if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return set_err(nullptr, LBM_EINVAL, "unknown lattice");
   if (!params || nbatch < 1) return set_err(nullptr, LBM_EINVAL, "need nbatch >= 1 parameter sets");
   const bool is3d = lattice == LBM_D3Q19;
@@ -442,13 +454,15 @@ int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_m
   }
   c->strip = default_strip(c);
   c->depth = is3d ? 2 : 1;
+  c->g_half = g_half;
+  c->g_elem = g_half ? sizeof(__half) : sizeof(float);
   const size_t pop = sizeof(float) * (size_t)c->q * nodes * nbatch;
   const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * nodes * nbatch;
   const size_t fld = sizeof(float) * (size_t)nodes * nbatch;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaMalloc(&c->f[i], pop);
-    if (e == cudaSuccess) e = cudaMalloc(&c->g[i], pop);
+    if (e == cudaSuccess) e = cudaMalloc(&c->g[i], pop / sizeof(float) * c->g_elem);
     if (e == cudaSuccess) e = cudaMalloc(&c->hist[i], his);
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->phi0, fld);
@@ -467,7 +481,8 @@ int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_m
   if (e == cudaSuccess && is3d && lbm::d3q19_maps_bytes() <= sizeof(c->d3maps[0])) {
     int r = 0;
     for (int i = 0; i < 2 && r == 0; ++i)
-      r = lbm::build_d3q19_maps(c->g[i], c->mom, c->hist[i], nx, ny, nz, nbatch, c->d3maps[i]);
+      r = lbm::build_d3q19_maps(static_cast<float*>(c->g[i]), c->mom, c->hist[i], nx, ny, nz, nbatch,
+                                c->d3maps[i]);
     if (r < 0) e = cudaErrorInvalidValue;   // the driver refused a tensor map
     c->d3maps_ok = r == 0;
   }
@@ -480,6 +495,11 @@ int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_m
   }
   *out = c;
   return LBM_OK;
+}
+
+int lbm_create_batch(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, int nbatch,
+                     const lbm_params* params, lbm_ctx** out) {
+  return lbm_create_ex(lattice, nx, ny, nz, periodic_mask, nbatch, params, 0, out);
 }
 
 int lbm_create(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, const lbm_params* p,
@@ -546,10 +566,12 @@ static int set_phase_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
   LBM_CK(c, cudaMemcpy2DAsync(stage, row * nh, src, row, row, c->nbatch, kind, c->stream));
   cudaError_t e;
   if (c->lattice == LBM_D2Q9)
-    e = lbm::launch_d2q9_init(c->phi0, stage, c->f[c->cur], c->g[c->cur], c->hist[c->cur], c->dconsts, c->nx,
+    e = lbm::launch_d2q9_init(c->phi0, stage, c->f[c->cur], c->g[c->cur], c->g_half, c->hist[c->cur], c->dconsts,
+                              c->nx,
                               c->ny, c->per[0], c->per[1], c->nbatch, c->stream);
   else
-    e = lbm::launch_d3q19_init(c->phi0, stage, c->f[c->cur], c->g[c->cur], c->hist[c->cur], c->dconsts, c->nx,
+    e = lbm::launch_d3q19_init(c->phi0, stage, c->f[c->cur], static_cast<float*>(c->g[c->cur]), c->hist[c->cur],
+                               c->dconsts, c->nx,
                                c->ny, c->nz, c->per[0], c->per[1], c->per[2], c->nbatch, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   LBM_CK(c, cudaMemsetAsync(c->p, 0, sizeof(float) * c->nodes * c->nbatch, c->stream));
@@ -643,17 +665,28 @@ int lbm_get_fields(lbm_ctx* c, float* phi1, float* u, float* p) {
 
 int lbm_get_populations(lbm_ctx* c, float* f, float* g) {
   if (int s = check_ready(c, true)) return s;
-  const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
-  if (f) LBM_CK(c, cudaMemcpyAsync(f, c->f[c->cur], pop, cudaMemcpyDeviceToHost, c->stream));
-  if (g) LBM_CK(c, cudaMemcpyAsync(g, c->g[c->cur], pop, cudaMemcpyDeviceToHost, c->stream));
+  const size_t n = (size_t)c->q * c->nodes * c->nbatch;
+  if (f) LBM_CK(c, cudaMemcpyAsync(f, c->f[c->cur], sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<__half> h;
+  if (g && c->g_half) {
+    h.resize(n);
+    LBM_CK(c, cudaMemcpyAsync(h.data(), c->g[c->cur], sizeof(__half) * n, cudaMemcpyDeviceToHost, c->stream));
+  } else if (g) {
+    LBM_CK(c, cudaMemcpyAsync(g, c->g[c->cur], sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+  }
   LBM_CK(c, cudaStreamSynchronize(c->stream));
+  if (g && c->g_half) {
+    // unscale per instance (every instance uses the same power-of-two scale)
+    const float inv = c->hconsts[0].gsci;
+    for (size_t i = 0; i < n; ++i) g[i] = __half2float(h[i]) * inv;
+  }
   return LBM_OK;
 }
 
 static size_t state_bytes(const lbm_ctx* c) {
-  const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
+  const size_t n = (size_t)c->q * c->nodes * c->nbatch;
   const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->nodes * c->nbatch;
-  return sizeof(StateHeader) + 2 * pop + his;
+  return sizeof(StateHeader) + sizeof(float) * n + c->g_elem * n + his;
 }
 
 int lbm_get_state(lbm_ctx* c, void* buf, size_t* bytes) {
@@ -677,14 +710,16 @@ int lbm_get_state(lbm_ctx* c, void* buf, size_t* bytes) {
   hd.d = c->d;
   hd.step = c->step;
   hd.nodes = c->nodes;
+  hd.pad[0] = c->g_half;   // storage of g: 0 float32, 1 FP16 scaled
   char* o = static_cast<char*>(buf);
   memcpy(o, &hd, sizeof hd);
   o += sizeof hd;
   const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
+  const size_t gpop = pop / sizeof(float) * c->g_elem;
   const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->nodes * c->nbatch;
   LBM_CK(c, cudaMemcpyAsync(o, c->f[c->cur], pop, cudaMemcpyDeviceToHost, c->stream));
-  LBM_CK(c, cudaMemcpyAsync(o + pop, c->g[c->cur], pop, cudaMemcpyDeviceToHost, c->stream));
-  LBM_CK(c, cudaMemcpyAsync(o + 2 * pop, c->hist[c->cur], his, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(o + pop, c->g[c->cur], gpop, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(o + pop + gpop, c->hist[c->cur], his, cudaMemcpyDeviceToHost, c->stream));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   *bytes = need;
   return LBM_OK;
@@ -696,15 +731,17 @@ int lbm_set_state(lbm_ctx* c, const void* buf, size_t bytes) {
   StateHeader hd;
   memcpy(&hd, buf, sizeof hd);
   if (hd.magic != kStateMagic || hd.lattice != c->lattice || hd.nx != c->nx || hd.ny != c->ny ||
-      hd.nz != c->nz || hd.nbatch != c->nbatch || hd.q != c->q || hd.d != c->d || bytes != state_bytes(c))
+      hd.nz != c->nz || hd.nbatch != c->nbatch || hd.q != c->q || hd.d != c->d || hd.pad[0] != c->g_half ||
+      bytes != state_bytes(c))
     return set_err(c, LBM_EINVAL, "state image does not match this context");
   if (!c->solid_set) return set_err(c, LBM_ESTATE, "call lbm_set_solid before lbm_set_state");
   const char* o = static_cast<const char*>(buf) + sizeof hd;
   const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
+  const size_t gpop = pop / sizeof(float) * c->g_elem;
   const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->nodes * c->nbatch;
   LBM_CK(c, cudaMemcpyAsync(c->f[c->cur], o, pop, cudaMemcpyHostToDevice, c->stream));
-  LBM_CK(c, cudaMemcpyAsync(c->g[c->cur], o + pop, pop, cudaMemcpyHostToDevice, c->stream));
-  LBM_CK(c, cudaMemcpyAsync(c->hist[c->cur], o + 2 * pop, his, cudaMemcpyHostToDevice, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(c->g[c->cur], o + pop, gpop, cudaMemcpyHostToDevice, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(c->hist[c->cur], o + pop + gpop, his, cudaMemcpyHostToDevice, c->stream));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   c->step = hd.step;
   c->phase_set = true;

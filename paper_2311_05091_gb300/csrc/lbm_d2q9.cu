@@ -20,6 +20,10 @@
 // Layouts: see include/lbm.h.  The NS rest population is stored minus the
 // constant rho_0 of lambda_0, so every stored g is O(p/cs2) and float32 keeps
 // its relative precision; the dynamics do not depend on that constant.
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -152,8 +156,9 @@ __device__ __forceinline__ Nat natural_of(const Her& h, float cs2, float cs4) {
 // initial state: f = f^eq(phi1, mubar_1, u = 0), g = g^eq(p = 0, u = 0) - rho_0 e_0 = 0,
 // history = (phi1, 0, 0, 0, 0)
 // ---------------------------------------------------------------------------
+template <typename GT>
 __global__ void d2q9_init(const float* __restrict__ phi0_all, const float* __restrict__ phi1_all,
-                          float* __restrict__ f_all, float* __restrict__ g_all, float* __restrict__ hist_all,
+                          float* __restrict__ f_all, GT* __restrict__ g_all, float* __restrict__ hist_all,
                           const InstanceConsts* __restrict__ consts, int nx, int ny, int per_x, int per_y) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
@@ -176,13 +181,13 @@ __global__ void d2q9_init(const float* __restrict__ phi0_all, const float* __res
   const float emb = k.eta * mubar1_of(k, mu0, mu1, mu2);
   const long long node = (long long)y * nx + x;
   float* f = f_all + (long long)b * 9 * plane;
-  float* g = g_all + (long long)b * 9 * plane;
+  GT* g = g_all + (long long)b * 9 * plane;
   float* h = hist_all + (long long)b * 5 * plane;
   f[node] = v1.c + (k.w0 - 1.f) * emb;
 #pragma unroll
   for (int i = 1; i < 9; ++i) f[(long long)i * plane + node] = (i < 5 ? k.wa : k.we) * emb;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) g[(long long)i * plane + node] = 0.f;
+  for (int i = 0; i < 9; ++i) g[(long long)i * plane + node] = GT(0.f);
   h[node] = v1.c;
 #pragma unroll
   for (int q = 1; q < 5; ++q) h[(long long)q * plane + node] = 0.f;
@@ -223,15 +228,28 @@ struct ARow {
 struct HRow {
   float rows[5][W];    // history phi1, ux, uy, Sx, Sy; one halo column each side
 };
+// g rows start 16 bytes in, like the float rows, whatever the element size
+template <typename GT>
+__host__ __device__ constexpr int gpad() { return 16 / (int)sizeof(GT); }
+template <typename GT>
 struct GRow {
-  float rows[9][W];    // g, owned columns
+  GT rows[9][BX + 2 * gpad<GT>()];   // g, owned columns (float, or FP16 scaled by gsc)
 };
 
-template <int D>
+// NS population element conversions: float storage is exact; FP16 storage
+// keeps g * gsc, gsc a power of two, rounded to nearest.
+__device__ __forceinline__ float g_load(float v, const InstanceConsts&) { return v; }
+__device__ __forceinline__ float g_load(__half v, const InstanceConsts& k) { return __half2float(v) * k.gsci; }
+__device__ __forceinline__ void g_store(float* p, float v, const InstanceConsts&) { *p = v; }
+__device__ __forceinline__ void g_store(__half* p, float v, const InstanceConsts& k) {
+  *p = __float2half_rn(v * k.gsc);
+}
+
+template <int D, typename GT>
 struct StepSmem {
   ARow a[D + 1];
   HRow h[D + 2];
-  GRow g[D + 1];
+  GRow<GT> g[D + 1];
   float phi1[RP][BX + 4];
   float phi0[RP][BX + 4];
   float mub[RM][BX + 2];
@@ -240,13 +258,14 @@ struct StepSmem {
   InstanceConsts k;
 };
 
-template <int D>
-constexpr size_t step_smem_bytes() { return sizeof(StepSmem<D>); }
+template <int D, typename GT>
+constexpr size_t step_smem_bytes() { return sizeof(StepSmem<D, GT>); }
 
-template <bool OBS, int D>
+template <bool OBS, int D, typename GT>
 __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StepSmem<D>& S = *reinterpret_cast<StepSmem<D>*>(smem_raw);
+  StepSmem<D, GT>& S = *reinterpret_cast<StepSmem<D, GT>*>(smem_raw);
+  constexpr bool kHalf = std::is_same<GT, __half>::value;
 
   const int t = threadIdx.x;
   const int x0 = blockIdx.x * BX;
@@ -261,20 +280,19 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
 
   // base pointers of the 24 source planes: f 0-8, phi0 9, history 10-14, g 15-23
   const float* __restrict__ f_in = a.f_in + (long long)b * 9 * plane;
-  const float* __restrict__ g_in = a.g_in + (long long)b * 9 * plane;
+  const GT* __restrict__ g_in = static_cast<const GT*>(a.g_in) + (long long)b * 9 * plane;
   const float* __restrict__ p0_in = a.phi0 + (long long)b * plane;
   const float* __restrict__ h_in = a.hist_in + (long long)b * 5 * plane;
   float* __restrict__ f_out = a.f_out + (long long)b * 9 * plane;
-  float* __restrict__ g_out = a.g_out + (long long)b * 9 * plane;
+  GT* __restrict__ g_out = static_cast<GT*>(a.g_out) + (long long)b * 9 * plane;
   float* __restrict__ h_out = a.hist_out + (long long)b * 5 * plane;
+  // the 15 float source planes: f 0-8, phi0 9, history 10-14 (g, 15-23, separately)
   auto src_plane = [&](int arr) -> const float* {
-    return arr < 9 ? f_in + arr * plane
-                   : (arr == 9 ? p0_in : (arr < 15 ? h_in + (arr - 10) * plane : g_in + (arr - 15) * plane));
+    return arr < 9 ? f_in + arr * plane : (arr == 9 ? p0_in : h_in + (arr - 10) * plane);
   };
-  // destination row of array arr in the slots of rows ra (f, phi0), rh (history), rg (g)
-  auto dst_row = [&](int arr, int ra, int rh, int rg) -> float* {
-    return arr < 10 ? S.a[ring(ra, D + 1)].rows[arr]
-                    : (arr < 15 ? S.h[ring(rh, D + 2)].rows[arr - 10] : S.g[ring(rg, D + 1)].rows[arr - 15]);
+  // destination row of float array arr in the slots of rows ra (f, phi0), rh (history)
+  auto dst_row = [&](int arr, int ra, int rh) -> float* {
+    return arr < 10 ? S.a[ring(ra, D + 1)].rows[arr] : S.h[ring(rh, D + 2)].rows[arr - 10];
   };
 
   const bool vec16 = (nx & 3) == 0;
@@ -313,25 +331,54 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
     const int ba = wrap_or_mirror(ra, ny, per_y) * nx;
     const int bh = wrap_or_mirror(rh, ny, per_y) * nx;
     const int bg = wrap_or_mirror(rg, ny, per_y) * nx;
-    auto need = [&](int arr) { return arr < 10 ? need_a : (arr < 15 ? need_h : need_g); };
-    auto rowb = [&](int arr) { return arr < 10 ? ba : (arr < 15 ? bh : bg); };
+    auto need = [&](int arr) { return arr < 10 ? need_a : need_h; };
+    auto rowb = [&](int arr) { return arr < 10 ? ba : bh; };
+    GT* const grow = S.g[ring(rg, D + 1)].rows[0];
+    constexpr int GP = gpad<GT>(), GW = BX + 2 * GP;
     if (vec16) {
-      // chunk m of this thread: array (t >> 5) + 4 m, columns x0 + 4 (t & 31) .. + 3
+      // float chunk m of this thread: array (t >> 5) + 4 m, columns x0 + 4 (t & 31) .. + 3
       const int j = t & 31;
       const int xc = x0 + 4 * j;
       if (xc < nx) {
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
+        for (int m = 0; m < 4; ++m) {
           const int arr = (t >> 5) + 4 * m;
-          if (need(arr)) cp_async16(dst_row(arr, ra, rh, rg) + PAD + 4 * j, src_plane(arr) + rowb(arr) + xc);
+          if (arr < 15 && need(arr)) cp_async16(dst_row(arr, ra, rh) + PAD + 4 * j, src_plane(arr) + rowb(arr) + xc);
+        }
+      }
+      if (need_g) {
+        if (!kHalf) {
+#pragma unroll
+          for (int m = 3; m < 6; ++m) {
+            const int arr = (t >> 5) + 4 * m;
+            if (arr >= 15 && xc < nx)
+              cp_async16(reinterpret_cast<float*>(grow + (arr - 15) * GW + GP + 4 * j),
+                         reinterpret_cast<const float*>(g_in + (arr - 15) * plane + bg + xc));
+          }
+        } else {
+          // FP16 rows: 16 chunks of eight columns per array, 144 chunks on 128 threads
+#pragma unroll
+          for (int m = 0; m < 2; ++m) {
+            const int id = t + BX * m;
+            const int arr = id >> 4, xh = x0 + 8 * (id & 15);
+            if (id < 144 && xh < nx)
+              cp_async16(reinterpret_cast<float*>(grow + arr * GW + GP + 8 * (id & 15)),
+                         reinterpret_cast<const float*>(g_in + arr * plane + bg + xh));
+          }
         }
       }
     } else if (x < nx) {
 #pragma unroll
-      for (int arr = 0; arr < 24; ++arr)
-        if (need(arr)) cp_async4(dst_row(arr, ra, rh, rg) + PAD + t, src_plane(arr) + rowb(arr) + x);
+      for (int arr = 0; arr < 15; ++arr)
+        if (need(arr)) cp_async4(dst_row(arr, ra, rh) + PAD + t, src_plane(arr) + rowb(arr) + x);
+      if (need_g && !kHalf) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          cp_async4(reinterpret_cast<float*>(grow + i * GW + GP + t),
+                    reinterpret_cast<const float*>(g_in + i * plane + bg + x));
+      }
     }
-    if (h_active && need(h_arr)) cp_async4(dst_row(h_arr, ra, rh, rg) + h_col, h_src + rowb(h_arr) + h_px);
+    if (h_active && need(h_arr)) cp_async4(dst_row(h_arr, ra, rh) + h_col, h_src + rowb(h_arr) + h_px);
     cp_commit();   // empty groups keep the group count uniform
   };
 
@@ -415,7 +462,7 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
 
     // ---------------- stage 3: collide and stream row y ----------------
     if (y >= ys && x < nx) {
-      const GRow& gs = S.g[ring(y, D + 1)];
+      const GRow<GT>& gs = S.g[ring(y, D + 1)];
       const HRow& hs = S.h[ring(y, D + 2)];
       const int c = t + 2, s = t + 1, col = t + PAD;
       const int node = y * nx + x;         // instance-relative, < 2^31 (checked at creation)
@@ -423,7 +470,7 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
       const float cs2 = k.cs2, cs4 = k.cs4;
       float g[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) g[i] = gs.rows[i][col];
+      for (int i = 0; i < 9; ++i) g[i] = g_load(gs.rows[i][t + gpad<GT>()], k);
       const float php = hs.rows[0][col], uxp = hs.rows[1][col], uyp = hs.rows[2][col];
       const float Sxp = hs.rows[3][col], Syp = hs.rows[4][col];
 
@@ -498,12 +545,12 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
       const bool wyp = y + 1 >= ny && !per_y, wym = y == 0 && !per_y;
       const int oxp = x + 1 < nx ? 1 : 1 - nx, oxm = x > 0 ? -1 : nx - 1;
       const int oyp = y + 1 < ny ? nx : nx - pl, oym = y > 0 ? -nx : pl - nx;
-      auto store = [&](float* __restrict__ out, int i, int io, int cx, int cy, float v) {
+      auto store = [&](auto* __restrict__ out, int i, int io, int cx, int cy, float v) {
         int off = 0;
         bool bb = false;
         if (cx) { off += cx > 0 ? oxp : oxm; bb = bb || (cx > 0 ? wxp : wxm); }
         if (cy) { off += cy > 0 ? oyp : oym; bb = bb || (cy > 0 ? wyp : wym); }
-        out[bb ? io * pl + node : i * pl + node + off] = v;
+        g_store(out + (bb ? io * pl + node : i * pl + node + off), v, k);
       };
 
       // ---- NS collision in Hermite space ----
@@ -624,37 +671,48 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
 
 }  // namespace
 
-cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, float* g, float* hist,
+cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, void* g, int g_half, float* hist,
                              const InstanceConsts* consts, int nx, int ny, int per_x, int per_y,
                              int nbatch, cudaStream_t s) {
   dim3 block(128), grid((nx + 127) / 128, ny, nbatch);
-  d2q9_init<<<grid, block, 0, s>>>(phi0, phi1, f, g, hist, consts, nx, ny, per_x, per_y);
+  if (g_half)
+    d2q9_init<__half><<<grid, block, 0, s>>>(phi0, phi1, f, static_cast<__half*>(g), hist, consts, nx, ny, per_x,
+                                             per_y);
+  else
+    d2q9_init<float><<<grid, block, 0, s>>>(phi0, phi1, f, static_cast<float*>(g), hist, consts, nx, ny, per_x,
+                                            per_y);
   return cudaGetLastError();
 }
 
-template <int D>
+template <int D, typename GT>
 cudaError_t launch_depth(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
-  const size_t smem = step_smem_bytes<D>();
+  const size_t smem = step_smem_bytes<D, GT>();
   static bool configured = false;   // attribute set once per process (both variants)
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(d2q9_step<true, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(d2q9_step<true, D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(d2q9_step<false, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(d2q9_step<false, D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   dim3 block(BX), grid((a.nx + BX - 1) / BX, (a.ny + a.strip - 1) / a.strip, nbatch);
-  if (observe) d2q9_step<true, D><<<grid, block, smem, s>>>(a);
-  else d2q9_step<false, D><<<grid, block, smem, s>>>(a);
+  if (observe) d2q9_step<true, D, GT><<<grid, block, smem, s>>>(a);
+  else d2q9_step<false, D, GT><<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+template <typename GT>
+cudaError_t launch_typed(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
   switch (a.depth) {
-    case 1: return launch_depth<1>(a, nbatch, observe, s);
-    case 3: return launch_depth<3>(a, nbatch, observe, s);
-    default: return launch_depth<2>(a, nbatch, observe, s);
+    case 1: return launch_depth<1, GT>(a, nbatch, observe, s);
+    case 3: return launch_depth<3, GT>(a, nbatch, observe, s);
+    default: return launch_depth<2, GT>(a, nbatch, observe, s);
   }
+}
+
+cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+  return a.g_half ? launch_typed<__half>(a, nbatch, observe, s) : launch_typed<float>(a, nbatch, observe, s);
 }
 
 }  // namespace lbm

@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   if (t < (int)(sizeof(InstanceConsts) / 4))
     reinterpret_cast<float*>(&S.k)[t] = reinterpret_cast<const float*>(a.consts + b)[t];
 
-  const float* __restrict__ g_in = a.g_in + (long long)b * Q * nodes;
+  const float* __restrict__ g_in = static_cast<const float*>(a.g_in) + (long long)b * Q * nodes;
   const float* __restrict__ p0_in = a.phi0 + (long long)b * nodes;
   const float* __restrict__ h_in = a.hist_in + (long long)b * NH * nodes;
   const float* __restrict__ phi1_now = a.hist_out + (long long)b * NH * nodes;   // moment pass of this step
@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   Outs o;
   o.f_in = a.f_in + (long long)b * Q * nodes;
   o.f_out = a.f_out + (long long)b * Q * nodes;
-  o.g_out = a.g_out + (long long)b * Q * nodes;
+  o.g_out = static_cast<float*>(a.g_out) + (long long)b * Q * nodes;
   o.h_out = a.hist_out + (long long)b * NH * nodes;
   o.p_out = a.p_out + (long long)b * nodes;
   o.flag = a.flag;
@@ -885,7 +885,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   Outs o;
   o.f_in = a.f_in + (long long)b * Q * nodes;
   o.f_out = a.f_out + (long long)b * Q * nodes;
-  o.g_out = a.g_out + (long long)b * Q * nodes;
+  o.g_out = static_cast<float*>(a.g_out) + (long long)b * Q * nodes;
   o.h_out = a.hist_out + (long long)b * NH * nodes;
   o.p_out = a.p_out + (long long)b * nodes;
   o.flag = a.flag;

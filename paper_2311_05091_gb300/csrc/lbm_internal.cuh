@@ -35,15 +35,16 @@ struct InstanceConsts {
   // H = K * (h0 * inv_s0 - h2 * inv_s2a + h3), pf = cs2/(1-w0), wq = w0/(1-cs2)
   float pf, wq, Kp, h0, h2, h3;
   float ch_fast;   // 1 when every free CH rate is 1: closed form f* = f^eq + first-moment part
-  float pad;
+  // FP16 storage of the NS populations: stored value = g * gsc (a power of two), g = stored * gsci
+  float gsc, gsci;
 };
 
 // Launch arguments of the fused step kernel (both lattices).
 struct StepArgs {
   const float* f_in;
   float* f_out;
-  const float* g_in;
-  float* g_out;
+  const void* g_in;       // NS populations: float, or __half scaled by gsc when g_half
+  void* g_out;
   const float* phi0;
   const float* hist_in;   // [b][k][nodes]: phi1, u (d), S (d) at the previous step
   float* hist_out;
@@ -56,10 +57,11 @@ struct StepArgs {
   int strip;              // rows (2D) or planes (3D) per CTA
   int depth;              // rows of asynchronous copies kept in flight (1..3)
   long long nodes;        // nodes per instance
+  int g_half;             // NS populations stored as FP16 (D2Q9)
 };
 
 // Kernel launchers (return cudaGetLastError of the launch).
-cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, float* g,
+cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, void* g, int g_half,
                              float* hist, const InstanceConsts* consts, int nx, int ny,
                              int per_x, int per_y, int nbatch, cudaStream_t s);
 cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s);

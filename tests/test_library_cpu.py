@@ -64,3 +64,17 @@ def test_build_targets_sm_103a():
     B = importlib.import_module("paper_2311_05091_gb300.build")
     assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
     assert "-lineinfo" in B.FLAGS
+
+
+def test_storage_options_validated_on_the_host(lbm_lib):
+    L = lbm_lib
+    p = [L.lbm_default_params()]
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_create_ex(L.LBM_D3Q19, 16, 16, 16, 7, p, L.LBM_STORE_G_F16)
+    assert e.value.status == -7          # FP16 storage is built for D2Q9 only
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_create_ex(L.LBM_D2Q9, 20, 16, 1, 3, p, L.LBM_STORE_G_F16)
+    assert e.value.status == -1          # nx % 8 != 0
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_create_ex(L.LBM_D2Q9, 16, 16, 1, 3, p, 2)
+    assert e.value.status == -1          # unknown flag
