@@ -50,6 +50,9 @@ WORKLOADS = {
     "disk1024x5": dict(lattice="D2Q9", size=1024, bytes_per_lu=188, kernel="d2q9_step", kernel_bytes_per_lu=188,
                        kernel_src="lbm_d2q9.cu", profile="d2q9_step_disk1024x5.md", launches_per_step=1,
                        oracle_us_per_node_step=2.5),
+    "batch64": dict(lattice="D2Q9", size=None, bytes_per_lu=188, kernel="d2q9_step_items", kernel_bytes_per_lu=188,
+                    kernel_src="lbm_d2q9.cu", profile="d2q9_step_items_batch64.md", launches_per_step=1,
+                    oracle_us_per_node_step=2.5),
     "porous256": dict(lattice="D3Q19", size=256, bytes_per_lu=364, kernel="d3q19_step", kernel_bytes_per_lu=284,
                       kernel_src="lbm_d3q19.cu", profile="d3q19_step_porous256.md", launches_per_step=2,
                       oracle_us_per_node_step=8.5),
@@ -159,6 +162,13 @@ def traffic_from_profile(spec, lu_per_launch):
 def make_workload(name, size=None):
     spec = WORKLOADS[name]
     n = size or spec["size"]
+    if name == "batch64":
+        from synthetic.workloads import batch_uneven
+        wl = batch_uneven(n_inst=size or 64)
+        # the oracle sample takes instance 0 in the single-lattice form
+        i0 = wl["instances"][0]
+        wl.update(nx=i0["nx"], ny=i0["ny"], nz=1, phi0=i0["phi0"][None], phi1=i0["phi1"][None], params=[i0["params"]])
+        return wl
     if name == "disk1024x5":
         from synthetic.workloads import disk_sweep
         return disk_sweep(n=n, Rs=160.0 * n / 1024, R0=120.0 * n / 1024)
@@ -331,7 +341,114 @@ def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5, flags=0):
     return out
 
 
+def run_gpu_batch(args):
+    """Many geometries of uneven size: one persistent launch per step against one context per instance."""
+    world, rank, local = dist_setup(args.gpus)
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_2311_05091_gb300.build import build
+    build()
+    from paper_2311_05091_gb300 import _lbm as L
+
+    spec = WORKLOADS["batch64"]
+    wl = make_workload("batch64", args.size)
+    inst = wl["instances"]
+    total = wl["nodes"]
+    stream = torch.cuda.Stream()
+    m = L.MultiContext([(i["nx"], i["ny"]) for i in inst], batch=[L.lbm_default_params(**i["params"]) for i in inst])
+    m.set_stream(stream.cuda_stream)
+    m.set_solid([i["phi0"] for i in inst])
+    m.set_phase([i["phi1"] for i in inst])
+    m.step(args.warmup)
+    m.sync()
+    strips = m.tune(10)
+    clocks = Clocks()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    ev0.record(stream)
+    m.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = max_over_ranks(world, ev0.elapsed_time(ev1))
+    m.sync()
+    value = world * total * args.steps / (ms * 1e-3) / 1e6
+
+    # end to end through the public API: upload, K steps, fields back
+    t0 = time.perf_counter()
+    m.set_solid([i["phi0"] for i in inst])
+    m.set_phase([i["phi1"] for i in inst])
+    m.step(args.steps)
+    m.get_fields()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = world * total * args.steps / e2e_s / 1e6
+    m.close()
+
+    # the same instances one context at a time (plain FP32 path), fewer steps each
+    seq_steps = max(50, args.steps // 10)
+    seq_ms = 0.0
+    for i in inst:
+        ctx = L.Context(L.LBM_D2Q9, i["nx"], i["ny"], 1, periodic=(True, True, False),
+                        params=L.lbm_default_params(**i["params"]))
+        ctx.set_stream(stream.cuda_stream)
+        ctx.set_solid(i["phi0"])
+        ctx.set_phase(i["phi1"])
+        ctx.step(32)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(seq_steps)
+        e1.record(stream)
+        e1.synchronize()
+        seq_ms += e0.elapsed_time(e1) / seq_steps
+        ctx.close()
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    step_ms = ms / args.steps
+    achieved = spec["bytes_per_lu"] * total / (step_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["name"], "lattice": "D2Q9", "instances": len(inst), "lu_per_step": total,
+                   "bytes_per_lu": spec["bytes_per_lu"], "strips_tuned": strips,
+                   "l2": f"no flush: each step moves about {spec['bytes_per_lu'] * total / 1e9:.2f} GB through HBM",
+                   "parallelism": f"weak, {world} x independent copies of the batch"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic_from_profile(spec, total),
+                     "peak_kind": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s", "kernel": spec["kernel"], "kernel_ms_per_launch": step_ms,
+                     "kernel_bytes_per_lu": spec["bytes_per_lu"]},
+        "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": 8 * total / args.steps,
+                "d2h_bytes_per_step": 16 * total / args.steps,
+                "note": "set_solid + set_phase from host, K steps, get_fields to host"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "sequential": {"mlups": total / (seq_ms * 1e-3) / 1e6, "ms_per_step": seq_ms,
+                       "note": "the same instances advanced one context at a time (one launch each per step)"},
+        "time_to_5000_steps_ms": {"batched": 5000 * step_ms, "sequential": 5000 * seq_ms,
+                                  "note": "every instance bitwise equal in both forms (tests/test_gpu_multi.py)"},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            mlups, secs, desc = oracle_sample(wl, 8, args.cpu_seconds, spec["oracle_us_per_node_step"])
+            line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc}
+        except Exception as e:
+            line["cpu_baseline"] = {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {str(e)[:200]}"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
+    if args.workload == "batch64":
+        return run_gpu_batch(args)
     world, rank, local = dist_setup(args.gpus)
     import numpy as np
     import torch

@@ -149,6 +149,31 @@ enum {
 int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask,
                   int nbatch, const lbm_params* params, int flags, lbm_ctx** out);
 
+/* ninst independent D2Q9 instances of different sizes nx[k] x ny[k] (same
+ * periodicity), advanced together by one persistent launch per step that
+ * walks a work list of (instance, 128-column tile, row strip) items; no
+ * pattern of the paper, a throughput form for many small geometries.
+ * Layout: instance k occupies a contiguous block of each buffer starting at
+ * node offset off_k = sum_{j<k} nx_j ny_j (lbm_get_instance_shape); fields
+ * passed to lbm_set_solid / lbm_set_phase / lbm_get_fields are the
+ * instances' blocks back to back (u: [k][a][y][x]).  Every other call works
+ * as for a batch, with instance-local shapes; lbm_get_shape reports nx = ny
+ * = 0.  Each instance's result is bitwise that of a single-instance context.
+ * D2Q9 only (LBM_EUNSUPPORTED otherwise); flags as lbm_create_ex. */
+int lbm_create_multi(lbm_lattice lattice, int ninst, const int* nx, const int* ny,
+                     int periodic_mask, const lbm_params* params, int flags, lbm_ctx** out);
+
+/* Shape and node offset of one instance (any context). */
+int lbm_get_instance_shape(const lbm_ctx* ctx, int instance, int* nx, int* ny, int64_t* offset);
+
+/* Launch autotuner: chooses the row strip (of every size class of a
+ * multi-size context, or the context's single strip) among 4, 8, 16, 32, 64
+ * by timing `trial` steps per candidate, two coordinate-descent passes.  The
+ * evolving state is saved before and restored after (bitwise), so the call can
+ * come at any point after lbm_set_phase.  strips_out (nbatch ints, may be
+ * NULL) receives the chosen strip of each instance. */
+int lbm_tune(lbm_ctx* ctx, int trial, int* strips_out);
+
 /* Free all device memory of the context.  Safe on NULL. */
 void lbm_destroy(lbm_ctx* ctx);
 

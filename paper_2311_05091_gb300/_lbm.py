@@ -25,7 +25,8 @@ STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: 
 
 # every symbol include/lbm.h declares
 EXPORTS = [
-    "lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_create_ex", "lbm_destroy", "lbm_set_stream",
+    "lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_create_ex", "lbm_create_multi",
+    "lbm_get_instance_shape", "lbm_tune", "lbm_destroy", "lbm_set_stream",
     "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
     "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
     "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_kernel_time_split", "lbm_observables_noalloc",
@@ -74,6 +75,11 @@ def library():
                                      ctypes.POINTER(P)]),
         "lbm_create_ex": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(lbm_params), c_int,
                                   ctypes.POINTER(P)]),
+        "lbm_create_multi": (c_int, [c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int,
+                                     ctypes.POINTER(lbm_params), c_int, ctypes.POINTER(P)]),
+        "lbm_get_instance_shape": (c_int, [P, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                           ctypes.POINTER(ctypes.c_int64)]),
+        "lbm_tune": (c_int, [P, c_int, ctypes.POINTER(c_int)]),
         "lbm_destroy": (None, [P]),
         "lbm_set_stream": (c_int, [P, P]),
         "lbm_set_launch": (c_int, [P, c_int, c_int]),
@@ -157,6 +163,30 @@ def lbm_create_ex(lattice, nx, ny, nz, periodic_mask, params_list, flags):
     _check(library().lbm_create_ex(lattice, nx, ny, nz, periodic_mask, len(params_list), arr, flags,
                                    ctypes.byref(out)), "lbm_create_ex")
     return out
+
+
+def lbm_create_multi(lattice, sizes, periodic_mask, params_list, flags=0):
+    n = len(sizes)
+    nx = (c_int * n)(*[int(a) for a, _ in sizes])
+    ny = (c_int * n)(*[int(b) for _, b in sizes])
+    arr = (lbm_params * n)(*params_list)
+    out = c_void_p()
+    _check(library().lbm_create_multi(lattice, n, nx, ny, periodic_mask, arr, flags, ctypes.byref(out)),
+           "lbm_create_multi")
+    return out
+
+
+def lbm_get_instance_shape(ctx, instance):
+    nx, ny, off = c_int(), c_int(), ctypes.c_int64()
+    _check(library().lbm_get_instance_shape(ctx, instance, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(off)),
+           "lbm_get_instance_shape", ctx)
+    return nx.value, ny.value, off.value
+
+
+def lbm_tune(ctx, trial, nbatch):
+    out = (c_int * nbatch)()
+    _check(library().lbm_tune(ctx, trial, out), "lbm_tune", ctx)
+    return list(out)
 
 
 def lbm_destroy(ctx):
@@ -338,3 +368,101 @@ class Context:
     def kernel_time_split(self): return lbm_kernel_time_split(self.ctx)
     def contact_angle(self, instance, mode, column, y_c=0.0, disk_radius=0.0):
         return lbm_contact_angle(self.ctx, instance, mode, column, y_c, disk_radius)
+
+
+class MultiContext:
+    """Owns one lbm_ctx of D2Q9 instances of different sizes (lbm_create_multi).
+
+    Fields go in and out per instance: lists of [ny, nx] arrays; the C calls
+    see the instances' blocks back to back.
+    """
+
+    def __init__(self, sizes, periodic=(True, True), batch=None, flags=0):
+        mask = sum(bit for bit, on in zip((1, 2), periodic) if on)
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        params = batch if batch is not None else [lbm_default_params() for _ in sizes]
+        self.ctx = lbm_create_multi(LBM_D2Q9, self.sizes, mask, params, flags)
+        self.offsets = [lbm_get_instance_shape(self.ctx, k)[2] for k in range(len(self.sizes))]
+        self.total = self.offsets[-1] + self.sizes[-1][0] * self.sizes[-1][1]
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _flat(self, fields):
+        out = np.empty(self.total, np.float32)
+        for k, ((nx, ny), off) in enumerate(zip(self.sizes, self.offsets)):
+            a = np.ascontiguousarray(fields[k], dtype=np.float32).ravel()
+            if a.size != nx * ny:
+                raise ValueError(f"instance {k}: expected {nx * ny} values, got {a.size}")
+            out[off:off + nx * ny] = a
+        return out
+
+    def set_solid(self, fields):
+        a = self._flat(fields)
+        _check(library().lbm_set_solid(self.ctx, _fptr(a)), "lbm_set_solid", self.ctx)
+
+    def set_phase(self, fields):
+        a = self._flat(fields)
+        _check(library().lbm_set_phase(self.ctx, _fptr(a)), "lbm_set_phase", self.ctx)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def sync(self):
+        lbm_sync(self.ctx)
+
+    def set_launch(self, strip, depth=0):
+        lbm_set_launch(self.ctx, strip, depth)
+
+    def set_stream(self, handle):
+        lbm_set_stream(self.ctx, handle)
+
+    def tune(self, trial=10):
+        return lbm_tune(self.ctx, trial, len(self.sizes))
+
+    def get_fields(self):
+        """Per instance: (phi1 [ny, nx], u [2, ny, nx], p [ny, nx])."""
+        phi1 = np.empty(self.total, np.float32)
+        u = np.empty(2 * self.total, np.float32)
+        p = np.empty(self.total, np.float32)
+        _check(library().lbm_get_fields(self.ctx, _fptr(phi1), _fptr(u), _fptr(p)), "lbm_get_fields", self.ctx)
+        out = []
+        for (nx, ny), off in zip(self.sizes, self.offsets):
+            n = nx * ny
+            out.append((phi1[off:off + n].reshape(ny, nx), u[2 * off:2 * off + 2 * n].reshape(2, ny, nx),
+                        p[off:off + n].reshape(ny, nx)))
+        return out
+
+    def get_populations(self):
+        """Per instance: (f [9, ny, nx], g [9, ny, nx])."""
+        f = np.empty(9 * self.total, np.float32)
+        g = np.empty(9 * self.total, np.float32)
+        _check(library().lbm_get_populations(self.ctx, _fptr(f), _fptr(g)), "lbm_get_populations", self.ctx)
+        return [(f[9 * off:9 * (off + nx * ny)].reshape(9, ny, nx), g[9 * off:9 * (off + nx * ny)].reshape(9, ny, nx))
+                for (nx, ny), off in zip(self.sizes, self.offsets)]
+
+    def get_state(self):
+        return lbm_get_state(self.ctx)
+
+    def set_state(self, image):
+        lbm_set_state(self.ctx, image)
+
+    def observables(self, instance=0):
+        return lbm_observables(self.ctx, instance)
+
+    def contact_angle(self, instance, mode, column, y_c=0.0, disk_radius=0.0):
+        return lbm_contact_angle(self.ctx, instance, mode, column, y_c, disk_radius)
+
+    def set_profiling(self, enable):
+        lbm_set_profiling(self.ctx, enable)
+
+    def kernel_time(self):
+        return lbm_kernel_time(self.ctx)

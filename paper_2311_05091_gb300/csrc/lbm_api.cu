@@ -56,6 +56,15 @@ struct lbm_ctx {
   float* phi0 = nullptr;
   float* p = nullptr;
   float* mom = nullptr;        // D3Q19 moment-pass scratch
+  // instances of different sizes (lbm_create_multi): per-instance shape, node
+  // offset into every buffer, strip; launch arguments and work items on the device
+  bool multi = false;
+  std::vector<int> inx, iny, istrip;
+  std::vector<long long> ioff;
+  long long total = 0;                 // nodes of all instances
+  StepArgs* dargs[2] = {nullptr, nullptr};
+  int4* ditems = nullptr;
+  int nitems = 0, items_cap = 0;
   // D3Q19 tensor maps of the step's input buffers, one set per starting buffer
   alignas(64) unsigned char d3maps[2][512];
   bool d3maps_ok = false;
@@ -237,9 +246,73 @@ StepArgs step_args(lbm_ctx* c, int from) {
   return a;
 }
 
+long long inst_nodes(const lbm_ctx* c, int b) { return (long long)c->inx[b] * c->iny[b] * c->nz; }
+
+void drop_graphs(lbm_ctx* c) {
+  for (int i = 0; i < 2; ++i)
+    if (c->graph[i]) {
+      cudaGraphExecDestroy(c->graph[i]);
+      c->graph[i] = nullptr;
+    }
+}
+
+// Per-instance launch arguments (both starting buffers) and the work list of a
+// multi-size context: items (instance, x0, ys) for every 128-column tile and
+// strip of every instance, largest tiles first.
+cudaError_t upload_multi(lbm_ctx* c) {
+  const int nb = c->nbatch;
+  std::vector<StepArgs> v(nb);
+  for (int from = 0; from < 2; ++from) {
+    for (int b = 0; b < nb; ++b) {
+      StepArgs a = step_args(c, from);
+      const long long o = c->ioff[b];
+      a.f_in = c->f[from] + (size_t)c->q * o;
+      a.f_out = c->f[1 - from] + (size_t)c->q * o;
+      a.g_in = static_cast<const char*>(c->g[from]) + (size_t)c->q * o * c->g_elem;
+      a.g_out = static_cast<char*>(c->g[1 - from]) + (size_t)c->q * o * c->g_elem;
+      a.phi0 = c->phi0 + o;
+      a.hist_in = c->hist[from] + (size_t)(1 + 2 * c->d) * o;
+      a.hist_out = c->hist[1 - from] + (size_t)(1 + 2 * c->d) * o;
+      a.p_out = c->p + o;
+      a.consts = c->dconsts + b;
+      a.nx = c->inx[b];
+      a.ny = c->iny[b];
+      a.nz = 1;
+      a.strip = c->istrip[b];
+      a.nodes = inst_nodes(c, b);
+      v[b] = a;
+    }
+    cudaError_t e = cudaMemcpy(c->dargs[from], v.data(), sizeof(StepArgs) * nb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  std::vector<int4> items;
+  for (int b = 0; b < nb; ++b)
+    for (int x0 = 0; x0 < c->inx[b]; x0 += 128)
+      for (int ys = 0; ys < c->iny[b]; ys += c->istrip[b]) items.push_back(make_int4(b, x0, ys, 0));
+  auto work = [&](const int4& w) {
+    return (long long)std::min(128, c->inx[w.x] - w.y) * std::min(c->istrip[w.x], c->iny[w.x] - w.z);
+  };
+  std::stable_sort(items.begin(), items.end(), [&](const int4& a, const int4& b) { return work(a) > work(b); });
+  if ((int)items.size() > c->items_cap) {
+    cudaFree(c->ditems);
+    c->ditems = nullptr;
+    c->items_cap = 0;
+    cudaError_t e = cudaMalloc(&c->ditems, sizeof(int4) * items.size());
+    if (e != cudaSuccess) return e;
+    c->items_cap = (int)items.size();
+  }
+  c->nitems = (int)items.size();
+  drop_graphs(c);
+  return cudaMemcpy(c->ditems, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+}
+
 // One time step.  D3Q19 runs its moment pass first; `mid`, when given, is
 // recorded between the moment pass and the fused kernel (D2Q9: before it).
 cudaError_t launch_step(lbm_ctx* c, int from, bool observe, cudaStream_t s, cudaEvent_t mid = nullptr) {
+  if (c->multi) {
+    if (mid) cudaEventRecord(mid, s);
+    return lbm::launch_d2q9_items(c->dargs[from], c->ditems, c->nitems, c->depth, c->g_half, 0, observe, s);
+  }
   const StepArgs a = step_args(c, from);
   if (c->lattice == LBM_D2Q9) {
     if (mid) cudaEventRecord(mid, s);
@@ -305,6 +378,9 @@ void free_all(lbm_ctx* c) {
     cudaFree(c->g[i]);
     cudaFree(c->hist[i]);
   }
+  cudaFree(c->dargs[0]);
+  cudaFree(c->dargs[1]);
+  cudaFree(c->ditems);
   cudaFree(c->phi0);
   cudaFree(c->p);
   cudaFree(c->mom);
@@ -406,41 +482,60 @@ int lbm_default_params(lbm_params* p) {
   return LBM_OK;
 }
 
-int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, int nbatch,
-                  const lbm_params* params, int flags, lbm_ctx** out) {
+static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const int* nys, int nz, int periodic_mask,
+                       const lbm_params* params, int flags, bool multi, lbm_ctx** out) {
   if (!out) return set_err(nullptr, LBM_EINVAL, "out is NULL");
   *out = nullptr;
   if (flags & ~LBM_STORE_G_F16) return set_err(nullptr, LBM_EINVAL, "unknown flag");
-  const int g_half = (flags & LBM_STORE_G_F16) ? 1 : 0;
-  if (g_half && lattice != LBM_D2Q9)
-    return set_err(nullptr, LBM_EUNSUPPORTED, "FP16 population storage is built for D2Q9 only");
-  if (g_half && nx % 8 != 0) return set_err(nullptr, LBM_EINVAL, "FP16 population storage needs nx % 8 == 0");
   if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return set_err(nullptr, LBM_EINVAL, "unknown lattice");
-  if (!params || nbatch < 1) return set_err(nullptr, LBM_EINVAL, "need nbatch >= 1 parameter sets");
+  if (!params || nbatch < 1 || !nxs || !nys) return set_err(nullptr, LBM_EINVAL, "need nbatch >= 1 parameter sets");
+  if (nbatch > 65535) return set_err(nullptr, LBM_EINVAL, "at most 65535 instances");
+  const int g_half = (flags & LBM_STORE_G_F16) ? 1 : 0;
   const bool is3d = lattice == LBM_D3Q19;
+  if (g_half && is3d) return set_err(nullptr, LBM_EUNSUPPORTED, "FP16 population storage is built for D2Q9 only");
+  if (multi && is3d) return set_err(nullptr, LBM_EUNSUPPORTED, "instances of different sizes are built for D2Q9 only");
   if (!is3d && nz != 1) return set_err(nullptr, LBM_EINVAL, "D2Q9 needs nz = 1");
-  if (nx < 1 || ny < 1 || nz < 1) return set_err(nullptr, LBM_EINVAL, "sizes must be positive");
   const int per[3] = {(periodic_mask & LBM_PERIODIC_X) ? 1 : 0, (periodic_mask & LBM_PERIODIC_Y) ? 1 : 0,
                       (periodic_mask & LBM_PERIODIC_Z) ? 1 : 0};
-  const int dims[3] = {nx, ny, nz};
-  for (int a = 0; a < (is3d ? 3 : 2); ++a)
-    if (!per[a] && dims[a] < 2) return set_err(nullptr, LBM_EINVAL, "a wall axis needs at least 2 nodes");
-  const long long nodes = (long long)nx * ny * nz;
-  // kernels index the planes of one instance with 32-bit offsets
-  if (nodes * (is3d ? 19 : 9) >= (1LL << 31)) return set_err(nullptr, LBM_EINVAL, "lattice too large for one instance");
-  if (nodes > (1LL << 40) / nbatch) return set_err(nullptr, LBM_EINVAL, "lattice too large");
+  long long total = 0, max_nodes = 0;
+  for (int b = 0; b < nbatch; ++b) {
+    const int nx = nxs[b], ny = nys[b];
+    if (nx < 1 || ny < 1 || nz < 1) return set_err(nullptr, LBM_EINVAL, "sizes must be positive");
+    if (g_half && nx % 8 != 0) return set_err(nullptr, LBM_EINVAL, "FP16 population storage needs nx % 8 == 0");
+    const int dims[3] = {nx, ny, nz};
+    for (int a = 0; a < (is3d ? 3 : 2); ++a)
+      if (!per[a] && dims[a] < 2) return set_err(nullptr, LBM_EINVAL, "a wall axis needs at least 2 nodes");
+    const long long nodes = (long long)nx * ny * nz;
+    // kernels index the planes of one instance with 32-bit offsets
+    if (nodes * (is3d ? 19 : 9) >= (1LL << 31))
+      return set_err(nullptr, LBM_EINVAL, "lattice too large for one instance");
+    total += nodes;
+    max_nodes = std::max(max_nodes, nodes);
+    if (total > (1LL << 40)) return set_err(nullptr, LBM_EINVAL, "lattice too large");
+  }
+  const int nx = nxs[0], ny = nys[0];
 
   lbm_ctx* c = new (std::nothrow) lbm_ctx();
   if (!c) return set_err(nullptr, LBM_ENOMEM, "host allocation failed");
   c->lattice = lattice;
-  c->nx = nx;
-  c->ny = ny;
+  c->multi = multi;
+  c->nx = multi ? 0 : nx;
+  c->ny = multi ? 0 : ny;
   c->nz = nz;
   c->nbatch = nbatch;
   c->q = is3d ? 19 : 9;
   c->d = is3d ? 3 : 2;
   for (int a = 0; a < 3; ++a) c->per[a] = per[a];
-  c->nodes = nodes;
+  c->nodes = multi ? 0 : (long long)nx * ny * nz;
+  c->total = total;
+  c->inx.assign(nxs, nxs + nbatch);
+  c->iny.assign(nys, nys + nbatch);
+  c->ioff.resize(nbatch);
+  long long o = 0;
+  for (int b = 0; b < nbatch; ++b) {
+    c->ioff[b] = o;
+    o += (long long)c->inx[b] * c->iny[b] * nz;
+  }
   c->hconsts.resize(nbatch);
   for (int b = 0; b < nbatch; ++b) {
     char why[128] = "";
@@ -456,9 +551,11 @@ int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask
   c->depth = is3d ? 2 : 1;
   c->g_half = g_half;
   c->g_elem = g_half ? sizeof(__half) : sizeof(float);
-  const size_t pop = sizeof(float) * (size_t)c->q * nodes * nbatch;
-  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * nodes * nbatch;
-  const size_t fld = sizeof(float) * (size_t)nodes * nbatch;
+  c->istrip.resize(nbatch);
+  for (int b = 0; b < nbatch; ++b) c->istrip[b] = std::max(1, std::min(16, c->iny[b]));
+  const size_t pop = sizeof(float) * (size_t)c->q * total;
+  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * total;
+  const size_t fld = sizeof(float) * (size_t)total;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaMalloc(&c->f[i], pop);
@@ -469,7 +566,7 @@ int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask
   if (e == cudaSuccess) e = cudaMalloc(&c->p, fld);
   if (e == cudaSuccess && is3d) e = cudaMalloc(&c->mom, 3 * fld);
   if (e == cudaSuccess) e = cudaMalloc(&c->dflag, sizeof(unsigned int));
-  if (e == cudaSuccess) e = cudaMalloc(&c->dpart, sizeof(double) * lbm::obs_partials_len(nodes));
+  if (e == cudaSuccess) e = cudaMalloc(&c->dpart, sizeof(double) * lbm::obs_partials_len(max_nodes));
   if (e == cudaSuccess) e = cudaMalloc(&c->dobs, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMalloc(&c->dconsts, sizeof(InstanceConsts) * nbatch);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
@@ -478,6 +575,11 @@ int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask
     e = cudaMemcpy(c->dconsts, c->hconsts.data(), sizeof(InstanceConsts) * nbatch, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->dflag, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(c->p, 0, fld);
+  if (e == cudaSuccess && multi) {
+    e = cudaMalloc(&c->dargs[0], sizeof(StepArgs) * nbatch);
+    if (e == cudaSuccess) e = cudaMalloc(&c->dargs[1], sizeof(StepArgs) * nbatch);
+    if (e == cudaSuccess) e = upload_multi(c);
+  }
   if (e == cudaSuccess && is3d && lbm::d3q19_maps_bytes() <= sizeof(c->d3maps[0])) {
     int r = 0;
     for (int i = 0; i < 2 && r == 0; ++i)
@@ -494,6 +596,33 @@ int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask
     return code;
   }
   *out = c;
+  return LBM_OK;
+}
+
+int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, int nbatch,
+                  const lbm_params* params, int flags, lbm_ctx** out) {
+  if (nbatch < 1 || nbatch > 65535) {
+    if (out) *out = nullptr;
+    return set_err(nullptr, LBM_EINVAL, "need 1 <= nbatch <= 65535");
+  }
+  std::vector<int> nxs(nbatch, nx), nys(nbatch, ny);
+  return create_impl(lattice, nbatch, nxs.data(), nys.data(), nz, periodic_mask, params, flags, false, out);
+}
+
+int lbm_create_multi(lbm_lattice lattice, int ninst, const int* nx, const int* ny, int periodic_mask,
+                     const lbm_params* params, int flags, lbm_ctx** out) {
+  if (ninst < 1 || ninst > 65535) {
+    if (out) *out = nullptr;
+    return set_err(nullptr, LBM_EINVAL, "need 1 <= ninst <= 65535");
+  }
+  return create_impl(lattice, ninst, nx, ny, 1, periodic_mask, params, flags, true, out);
+}
+
+int lbm_get_instance_shape(const lbm_ctx* c, int instance, int* nx, int* ny, int64_t* offset) {
+  if (!c || instance < 0 || instance >= c->nbatch) return LBM_EINVAL;
+  if (nx) *nx = c->inx[instance];
+  if (ny) *ny = c->iny[instance];
+  if (offset) *offset = c->ioff[instance];
   return LBM_OK;
 }
 
@@ -533,18 +662,111 @@ int lbm_set_launch(lbm_ctx* c, int strip, int depth) {
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   c->strip = strip;
   if (depth > 0) c->depth = depth;
-  for (int i = 0; i < 2; ++i)
-    if (c->graph[i]) {
-      cudaGraphExecDestroy(c->graph[i]);
-      c->graph[i] = nullptr;
+  drop_graphs(c);
+  if (c->multi) {
+    for (int b = 0; b < c->nbatch; ++b) c->istrip[b] = std::min(strip, c->iny[b]);
+    LBM_CK(c, upload_multi(c));
+  }
+  return LBM_OK;
+}
+
+// Autotuner: strip per size class by coordinate descent on the measured time
+// of `trial` steps (after one untimed step), two passes over the classes.
+// The evolving state is saved before and restored after, bitwise.
+int lbm_tune(lbm_ctx* c, int trial, int* strips_out) {
+  if (int s = check_ready(c, true)) return s;
+  if (trial < 1) return set_err(c, LBM_EINVAL, "trial must be >= 1");
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  const size_t pop = sizeof(float) * (size_t)c->q * c->total;
+  const size_t gpop = pop / sizeof(float) * c->g_elem;
+  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->total;
+  void *sf = nullptr, *sg = nullptr, *sh = nullptr;
+  cudaError_t e = cudaMalloc(&sf, pop);
+  if (e == cudaSuccess) e = cudaMalloc(&sg, gpop);
+  if (e == cudaSuccess) e = cudaMalloc(&sh, his);
+  const int cur0 = c->cur;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sf, c->f[cur0], pop, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sg, c->g[cur0], gpop, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sh, c->hist[cur0], his, cudaMemcpyDeviceToDevice, c->stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // size classes: instances of equal (nx, ny)
+  std::vector<std::vector<int>> classes;
+  for (int b = 0; b < c->nbatch; ++b) {
+    bool placed = false;
+    for (auto& cl : classes)
+      if (c->inx[cl[0]] == c->inx[b] && c->iny[cl[0]] == c->iny[b]) {
+        cl.push_back(b);
+        placed = true;
+        break;
+      }
+    if (!placed) classes.push_back({b});
+  }
+  auto apply = [&](int cl, int strip) -> cudaError_t {
+    if (c->multi) {
+      for (int b : classes[cl]) c->istrip[b] = std::min(strip, c->iny[b]);
+      return upload_multi(c);
     }
+    c->strip = strip;
+    drop_graphs(c);
+    return cudaSuccess;
+  };
+  auto measure = [&](float& ms) -> cudaError_t {
+    cudaError_t r = launch_step(c, c->cur, false, c->stream);
+    c->cur = 1 - c->cur;
+    if (r == cudaSuccess) r = cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < trial && r == cudaSuccess; ++i) {
+      r = launch_step(c, c->cur, false, c->stream);
+      c->cur = 1 - c->cur;
+    }
+    if (r == cudaSuccess) r = cudaEventRecord(e1, c->stream);
+    if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+    return r;
+  };
+  static const int cand[] = {4, 8, 16, 32, 64};
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+    for (int cl = 0; cl < (int)classes.size() && e == cudaSuccess; ++cl) {
+      const int rows = c->multi ? c->iny[classes[cl][0]] : (c->lattice == LBM_D2Q9 ? c->ny : c->nz);
+      int best = c->multi ? c->istrip[classes[cl][0]] : c->strip;
+      float best_ms = 1e30f;
+      for (int sidx = 0; sidx < 5 && e == cudaSuccess; ++sidx) {
+        const int strip = cand[sidx];
+        if (strip > rows && sidx > 0 && cand[sidx - 1] >= rows) break;   // larger strips change nothing
+        float ms = 0.f;
+        e = apply(cl, strip);
+        if (e == cudaSuccess) e = measure(ms);
+        if (e == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best = strip;
+        }
+      }
+      if (e == cudaSuccess) e = apply(cl, best);
+      if (!c->multi) break;   // one strip for the whole context
+    }
+  }
+  // restore the state the tuner found
+  c->cur = cur0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->f[cur0], sf, pop, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->g[cur0], sg, gpop, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->hist[cur0], sh, his, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(sf);
+  cudaFree(sg);
+  cudaFree(sh);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotuner");
+  if (strips_out)
+    for (int b = 0; b < c->nbatch; ++b) strips_out[b] = c->multi ? c->istrip[b] : c->strip;
   return LBM_OK;
 }
 
 static int set_solid_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
   if (int s = check_ready(c, false)) return s;
   if (!src) return set_err(c, LBM_EINVAL, "phi0 is NULL");
-  LBM_CK(c, cudaMemcpyAsync(c->phi0, src, sizeof(float) * c->nodes * c->nbatch, kind, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(c->phi0, src, sizeof(float) * c->total, kind, c->stream));
   if (kind == cudaMemcpyHostToDevice) LBM_CK(c, cudaStreamSynchronize(c->stream));
   c->solid_set = true;
   return LBM_OK;
@@ -560,11 +782,28 @@ static int set_phase_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
   if (!src) return set_err(c, LBM_EINVAL, "phi1 is NULL");
   if (!c->solid_set) return set_err(c, LBM_ESTATE, "call lbm_set_solid before lbm_set_phase");
   const int nh = 1 + 2 * c->d;
-  const size_t row = sizeof(float) * c->nodes;
   // stage phi1 in plane 0 of the spare history buffer, then initialise the current one
   float* stage = c->hist[1 - c->cur];
+  cudaError_t e = cudaSuccess;
+  if (c->multi) {
+    for (int b = 0; b < c->nbatch && e == cudaSuccess; ++b) {
+      const long long o = c->ioff[b];
+      e = cudaMemcpyAsync(stage + nh * o, src + o, sizeof(float) * inst_nodes(c, b), kind, c->stream);
+      if (e == cudaSuccess)
+        e = lbm::launch_d2q9_init(c->phi0 + o, stage + nh * o, c->f[c->cur] + c->q * o,
+                                  static_cast<char*>(c->g[c->cur]) + c->q * o * c->g_elem, c->g_half,
+                                  c->hist[c->cur] + nh * o, c->dconsts + b, c->inx[b], c->iny[b], c->per[0],
+                                  c->per[1], 1, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    LBM_CK(c, cudaMemsetAsync(c->p, 0, sizeof(float) * c->total, c->stream));
+    if (kind == cudaMemcpyHostToDevice) LBM_CK(c, cudaStreamSynchronize(c->stream));
+    c->phase_set = true;
+    c->step = 0;
+    return LBM_OK;
+  }
+  const size_t row = sizeof(float) * c->nodes;
   LBM_CK(c, cudaMemcpy2DAsync(stage, row * nh, src, row, row, c->nbatch, kind, c->stream));
-  cudaError_t e;
   if (c->lattice == LBM_D2Q9)
     e = lbm::launch_d2q9_init(c->phi0, stage, c->f[c->cur], c->g[c->cur], c->g_half, c->hist[c->cur], c->dconsts,
                               c->nx,
@@ -574,7 +813,7 @@ static int set_phase_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
                                c->dconsts, c->nx,
                                c->ny, c->nz, c->per[0], c->per[1], c->per[2], c->nbatch, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
-  LBM_CK(c, cudaMemsetAsync(c->p, 0, sizeof(float) * c->nodes * c->nbatch, c->stream));
+  LBM_CK(c, cudaMemsetAsync(c->p, 0, sizeof(float) * c->total, c->stream));
   if (kind == cudaMemcpyHostToDevice) LBM_CK(c, cudaStreamSynchronize(c->stream));
   c->phase_set = true;
   c->step = 0;
@@ -652,8 +891,21 @@ int lbm_sync(lbm_ctx* c) {
 int lbm_get_fields(lbm_ctx* c, float* phi1, float* u, float* p) {
   if (int s = check_ready(c, true)) return s;
   const int nh = 1 + 2 * c->d;
-  const size_t row = sizeof(float) * c->nodes;
   const float* h = c->hist[c->cur];
+  if (c->multi) {
+    for (int b = 0; b < c->nbatch; ++b) {
+      const long long o = c->ioff[b], n = inst_nodes(c, b);
+      if (phi1)
+        LBM_CK(c, cudaMemcpyAsync(phi1 + o, h + nh * o, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+      if (u)
+        LBM_CK(c, cudaMemcpyAsync(u + c->d * o, h + nh * o + n, sizeof(float) * c->d * n, cudaMemcpyDeviceToHost,
+                                  c->stream));
+    }
+    if (p) LBM_CK(c, cudaMemcpyAsync(p, c->p, sizeof(float) * c->total, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return check_flag(c);
+  }
+  const size_t row = sizeof(float) * c->nodes;
   if (phi1) LBM_CK(c, cudaMemcpy2DAsync(phi1, row, h, row * nh, row, c->nbatch, cudaMemcpyDeviceToHost, c->stream));
   if (u)
     LBM_CK(c, cudaMemcpy2DAsync(u, row * c->d, h + c->nodes, row * nh, row * c->d, c->nbatch,
@@ -665,7 +917,7 @@ int lbm_get_fields(lbm_ctx* c, float* phi1, float* u, float* p) {
 
 int lbm_get_populations(lbm_ctx* c, float* f, float* g) {
   if (int s = check_ready(c, true)) return s;
-  const size_t n = (size_t)c->q * c->nodes * c->nbatch;
+  const size_t n = (size_t)c->q * c->total;
   if (f) LBM_CK(c, cudaMemcpyAsync(f, c->f[c->cur], sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
   std::vector<__half> h;
   if (g && c->g_half) {
@@ -684,8 +936,8 @@ int lbm_get_populations(lbm_ctx* c, float* f, float* g) {
 }
 
 static size_t state_bytes(const lbm_ctx* c) {
-  const size_t n = (size_t)c->q * c->nodes * c->nbatch;
-  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->nodes * c->nbatch;
+  const size_t n = (size_t)c->q * c->total;
+  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->total;
   return sizeof(StateHeader) + sizeof(float) * n + c->g_elem * n + his;
 }
 
@@ -709,14 +961,14 @@ int lbm_get_state(lbm_ctx* c, void* buf, size_t* bytes) {
   hd.q = c->q;
   hd.d = c->d;
   hd.step = c->step;
-  hd.nodes = c->nodes;
+  hd.nodes = c->total;
   hd.pad[0] = c->g_half;   // storage of g: 0 float32, 1 FP16 scaled
   char* o = static_cast<char*>(buf);
   memcpy(o, &hd, sizeof hd);
   o += sizeof hd;
-  const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
+  const size_t pop = sizeof(float) * (size_t)c->q * c->total;
   const size_t gpop = pop / sizeof(float) * c->g_elem;
-  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->nodes * c->nbatch;
+  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->total;
   LBM_CK(c, cudaMemcpyAsync(o, c->f[c->cur], pop, cudaMemcpyDeviceToHost, c->stream));
   LBM_CK(c, cudaMemcpyAsync(o + pop, c->g[c->cur], gpop, cudaMemcpyDeviceToHost, c->stream));
   LBM_CK(c, cudaMemcpyAsync(o + pop + gpop, c->hist[c->cur], his, cudaMemcpyDeviceToHost, c->stream));
@@ -732,13 +984,14 @@ int lbm_set_state(lbm_ctx* c, const void* buf, size_t bytes) {
   memcpy(&hd, buf, sizeof hd);
   if (hd.magic != kStateMagic || hd.lattice != c->lattice || hd.nx != c->nx || hd.ny != c->ny ||
       hd.nz != c->nz || hd.nbatch != c->nbatch || hd.q != c->q || hd.d != c->d || hd.pad[0] != c->g_half ||
+      hd.nodes != c->total ||
       bytes != state_bytes(c))
     return set_err(c, LBM_EINVAL, "state image does not match this context");
   if (!c->solid_set) return set_err(c, LBM_ESTATE, "call lbm_set_solid before lbm_set_state");
   const char* o = static_cast<const char*>(buf) + sizeof hd;
-  const size_t pop = sizeof(float) * (size_t)c->q * c->nodes * c->nbatch;
+  const size_t pop = sizeof(float) * (size_t)c->q * c->total;
   const size_t gpop = pop / sizeof(float) * c->g_elem;
-  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->nodes * c->nbatch;
+  const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->total;
   LBM_CK(c, cudaMemcpyAsync(c->f[c->cur], o, pop, cudaMemcpyHostToDevice, c->stream));
   LBM_CK(c, cudaMemcpyAsync(c->g[c->cur], o + pop, gpop, cudaMemcpyHostToDevice, c->stream));
   LBM_CK(c, cudaMemcpyAsync(c->hist[c->cur], o + pop + gpop, his, cudaMemcpyHostToDevice, c->stream));
@@ -752,9 +1005,9 @@ int lbm_observables(lbm_ctx* c, int instance, lbm_obs* out) {
   if (int s = check_ready(c, true)) return s;
   if (!out || instance < 0 || instance >= c->nbatch) return set_err(c, LBM_EINVAL, "bad instance or output");
   const int nh = 1 + 2 * c->d;
-  const float* h = c->hist[c->cur] + (size_t)instance * nh * c->nodes;
-  cudaError_t e = lbm::launch_observables(c->phi0 + (size_t)instance * c->nodes, h, h + c->nodes, c->d,
-                                          c->p + (size_t)instance * c->nodes, c->nodes, c->dpart, c->dobs,
+  const long long o = c->ioff[instance], n = inst_nodes(c, instance);
+  const float* h = c->hist[c->cur] + (size_t)nh * o;
+  cudaError_t e = lbm::launch_observables(c->phi0 + o, h, h + n, c->d, c->p + o, n, c->dpart, c->dobs,
                                           c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "observables kernel");
   double r[8];
@@ -777,18 +1030,19 @@ int lbm_contact_angle(lbm_ctx* c, int instance, int mode, int column, double y_c
                       double* theta_deg, double* height) {
   if (int s = check_ready(c, true)) return s;
   if (c->lattice != LBM_D2Q9) return set_err(c, LBM_EUNSUPPORTED, "contact angle is measured on 2D lattices");
-  if (instance < 0 || instance >= c->nbatch || column < 0 || column >= c->nx || (mode != 0 && mode != 1))
+  if (instance < 0 || instance >= c->nbatch || column < 0 || column >= c->inx[instance] || (mode != 0 && mode != 1))
     return set_err(c, LBM_EINVAL, "bad instance, column or mode");
   if (mode == 1 && !(disk_radius > 0)) return set_err(c, LBM_EINVAL, "disk radius must be > 0");
   lbm_obs ob;
   if (int s = lbm_observables(c, instance, &ob)) return s;
   const int nh = 1 + 2 * c->d;
-  std::vector<float> col1(c->ny), col0(c->ny);
-  const float* h = c->hist[c->cur] + (size_t)instance * nh * c->nodes + column;
-  const float* s0 = c->phi0 + (size_t)instance * c->nodes + column;
-  LBM_CK(c, cudaMemcpy2DAsync(col1.data(), sizeof(float), h, sizeof(float) * c->nx, sizeof(float), c->ny,
+  const int inx = c->inx[instance], iny = c->iny[instance];
+  std::vector<float> col1(iny), col0(iny);
+  const float* h = c->hist[c->cur] + (size_t)nh * c->ioff[instance] + column;
+  const float* s0 = c->phi0 + c->ioff[instance] + column;
+  LBM_CK(c, cudaMemcpy2DAsync(col1.data(), sizeof(float), h, sizeof(float) * inx, sizeof(float), iny,
                               cudaMemcpyDeviceToHost, c->stream));
-  LBM_CK(c, cudaMemcpy2DAsync(col0.data(), sizeof(float), s0, sizeof(float) * c->nx, sizeof(float), c->ny,
+  LBM_CK(c, cudaMemcpy2DAsync(col0.data(), sizeof(float), s0, sizeof(float) * inx, sizeof(float), iny,
                               cudaMemcpyDeviceToHost, c->stream));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   const double ytop = crossing_from_top(col1, 0.5);

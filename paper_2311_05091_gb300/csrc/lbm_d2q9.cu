@@ -261,18 +261,15 @@ struct StepSmem {
 template <int D, typename GT>
 constexpr size_t step_smem_bytes() { return sizeof(StepSmem<D, GT>); }
 
+// One CTA's work: columns x0 .. x0+127 and rows ys .. ys+strip-1 of instance b.
 template <bool OBS, int D, typename GT>
-__global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  StepSmem<D, GT>& S = *reinterpret_cast<StepSmem<D, GT>*>(smem_raw);
+__device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S, const int x0, const int ys,
+                                          const int b) {
   constexpr bool kHalf = std::is_same<GT, __half>::value;
 
   const int t = threadIdx.x;
-  const int x0 = blockIdx.x * BX;
   const int nx = a.nx, ny = a.ny, per_x = a.per_x, per_y = a.per_y;
-  const int ys = blockIdx.y * a.strip;
   const int ye = min(ys + a.strip, ny);
-  const int b = blockIdx.z;
   const long long plane = a.nodes;
   static_assert(sizeof(InstanceConsts) / 4 <= BX, "constants copied one word per thread");
   if (t < (int)(sizeof(InstanceConsts) / 4))
@@ -669,6 +666,30 @@ __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
   cp_wait<0>();
 }
 
+// one tile per CTA: grid (column tiles, row strips, instances)
+template <bool OBS, int D, typename GT>
+__global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem<D, GT>& S = *reinterpret_cast<StepSmem<D, GT>*>(smem_raw);
+  step_tile<OBS, D, GT>(a, S, blockIdx.x * BX, blockIdx.y * a.strip, blockIdx.z);
+}
+
+// Persistent form for instances of different sizes: CTA k takes work items
+// k, k + gridDim.x, ...; item = (instance, x0, ys), with per-instance launch
+// arguments (base pointers of that instance, its sizes and strip).
+template <bool OBS, int D, typename GT>
+__global__ void __launch_bounds__(BX, 5) d2q9_step_items(const StepArgs* __restrict__ args,
+                                                      const int4* __restrict__ items, int nitems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem<D, GT>& S = *reinterpret_cast<StepSmem<D, GT>*>(smem_raw);
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 w = items[it];
+    const StepArgs a = args[w.x];
+    step_tile<OBS, D, GT>(a, S, w.y, w.z, 0);
+    __syncthreads();   // shared memory is reused by the next item
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, void* g, int g_half, float* hist,
@@ -713,6 +734,51 @@ cudaError_t launch_typed(const StepArgs& a, int nbatch, bool observe, cudaStream
 
 cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
   return a.g_half ? launch_typed<__half>(a, nbatch, observe, s) : launch_typed<float>(a, nbatch, observe, s);
+}
+
+template <int D, typename GT>
+cudaError_t items_depth(const StepArgs* args, const int4* items, int nitems, int grid, bool observe,
+                        cudaStream_t s) {
+  const size_t smem = step_smem_bytes<D, GT>();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(d2q9_step_items<true, D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(d2q9_step_items<false, D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (grid <= 0) {
+    // persistent grid: every SM filled to its occupancy, no more CTAs than items
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, d2q9_step_items<false, D, GT>, BX, smem);
+    grid = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  if (grid > nitems) grid = nitems;
+  if (grid < 1) return cudaSuccess;
+  if (observe) d2q9_step_items<true, D, GT><<<grid, BX, smem, s>>>(args, items, nitems);
+  else d2q9_step_items<false, D, GT><<<grid, BX, smem, s>>>(args, items, nitems);
+  return cudaGetLastError();
+}
+
+template <typename GT>
+cudaError_t items_typed(const StepArgs* args, const int4* items, int nitems, int depth, int grid, bool observe,
+                        cudaStream_t s) {
+  switch (depth) {
+    case 1: return items_depth<1, GT>(args, items, nitems, grid, observe, s);
+    case 3: return items_depth<3, GT>(args, items, nitems, grid, observe, s);
+    default: return items_depth<2, GT>(args, items, nitems, grid, observe, s);
+  }
+}
+
+cudaError_t launch_d2q9_items(const StepArgs* args, const int4* items, int nitems, int depth, int g_half, int grid,
+                              bool observe, cudaStream_t s) {
+  return g_half ? items_typed<__half>(args, items, nitems, depth, grid, observe, s)
+                : items_typed<float>(args, items, nitems, depth, grid, observe, s);
 }
 
 }  // namespace lbm

@@ -65,6 +65,11 @@ cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, voi
                              float* hist, const InstanceConsts* consts, int nx, int ny,
                              int per_x, int per_y, int nbatch, cudaStream_t s);
 cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s);
+// Work-list form for instances of different sizes: args[inst] holds the
+// instance's own base pointers, sizes and strip (device memory), items[k] =
+// (inst, x0, ys, 0).  grid <= 0 picks a persistent grid of SMs x occupancy.
+cudaError_t launch_d2q9_items(const StepArgs* args, const int4* items, int nitems, int depth, int g_half, int grid,
+                              bool observe, cudaStream_t s);
 
 cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, float* g,
                               float* hist, const InstanceConsts* consts, int nx, int ny, int nz,

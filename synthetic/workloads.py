@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .geometry import cylinder_droplet, porous_inlet_slab, wall_droplet
+from .geometry import cylinder_droplet, porous_inlet_slab, random_disks_droplet, splitmix64, wall_droplet
 
 # Disk + droplet on a 1024^2 periodic lattice, contact angle swept over five
 # values, density and viscosity ratio 10 (fluid 1 heavier and more viscous;
@@ -48,3 +48,26 @@ def porous_slab(n=256, seed=0, W=4.0, slab=32.0, rmin=10.0, rmax=20.0, target_so
                 lattice="D3Q19", nx=n, ny=n, nz=n, periodic=(True, True, True),
                 phi0=geo.phi0.astype(np.float32)[None], phi1=geo.phi1.astype(np.float32)[None],
                 params=params, geometry=geo)
+
+
+BATCH_SIDES = (64, 128, 256, 512)
+
+
+def batch_uneven(n_inst=64, seed=0, W=4.0):
+    """Many independent D2Q9 geometries of uneven size: each instance is a
+    square lattice with side drawn uniformly from 64 / 128 / 256 / 512, 1-6
+    seeded random disks (radii 8-40), one droplet (radius 10-60) on the
+    largest disk, contact angle uniform in 30-150 deg, kappa = R0 / max R_s;
+    density / viscosity ratio 1, d0 = 1/2, all sides periodic."""
+    u = splitmix64(seed * 31 + 5)
+    inst = []
+    for k in range(n_inst):
+        side = BATCH_SIDES[min(int(u() * len(BATCH_SIDES)), len(BATCH_SIDES) - 1)]
+        geo, theta = random_disks_droplet(n=side, seed=seed * 1000 + k, W=W)
+        prm = dict(W=W, M_deg=0.1, theta_deg=theta, kappa=geo.kappa, sigma=0.01, d0=0.5)
+        inst.append(dict(nx=side, ny=side, phi0=geo.phi0.astype(np.float32), phi1=geo.phi1.astype(np.float32),
+                         params=prm, geometry=geo))
+    nodes = sum(i["nx"] * i["ny"] for i in inst)
+    return dict(name=f"D2Q9 batch of {n_inst} instances, sides in {BATCH_SIDES}, 1-6 disks, droplet, "
+                     f"theta in 30-150 deg (seed {seed}), {nodes} nodes",
+                lattice="D2Q9", instances=inst, nodes=nodes, periodic=(True, True))
