@@ -188,6 +188,9 @@ def oracle_sample(wl, steps, cpu_seconds, us_per_node_step):
     nodes = cpu_seconds / (us_per_node_step * 1e-6 * max(steps, 1))
     full = wl["nx"]
     side = int(max(8, min(full, nodes ** (1.0 / d))))
+    if side == full:
+        # the whole lattice is smaller than the sample: run more steps instead
+        steps = int(min(2000, max(steps, cpu_seconds / (us_per_node_step * 1e-6 * full ** d))))
     if d == 2:
         side = max(8, side - side % 8)
         sl = (slice(0, side), slice(0, side))
