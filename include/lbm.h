@@ -32,6 +32,11 @@
  * D3Q19 directions: 0 rest; 1..6 (+x,-x,+y,-y,+z,-z); 7..18 edges
  *   (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
  *   (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1).
+ * D3Q15 directions (the paper's printed M0): 0 rest; 1..6 as D3Q19; 7..14
+ *   corners (1,1,1) (-1,1,1) (1,-1,1) (-1,-1,1) (1,1,-1) (-1,1,-1) (1,-1,-1)
+ *   (-1,-1,-1).  Both 3D lattices use the D3Q19 isotropic stencil for
+ *   gradients and Laplacians; a D3Q19 / D3Q15 step is two launches (moment
+ *   pass, fused kernel).
  *
  * Ownership.  A context owns all of its device memory (allocated in
  * lbm_create*, freed in lbm_destroy).  Host pointers passed in are read or
@@ -78,7 +83,8 @@ typedef enum {
 
 typedef enum {
   LBM_D2Q9 = 0,   /* 2D, Appendix A weights and matrices                     */
-  LBM_D3Q19 = 1   /* 3D, weights from the same moment conditions (d0 < 1/2)  */
+  LBM_D3Q19 = 1,  /* 3D, weights from the same moment conditions (d0 < 1/2)  */
+  LBM_D3Q15 = 2   /* 3D, Appendix A weights and matrices (d0 < 1/2)          */
 } lbm_lattice;
 
 /* Periodicity bit mask; a clear bit means half-way bounce-back walls (no-flux
@@ -95,7 +101,7 @@ typedef struct {
   double sigma;         /* fluid-fluid tension sigma_12, > 0                        */
   double rho[3];        /* densities of solid, fluid 1, fluid 2, > 0                */
   double mu[3];         /* dynamic viscosities of solid, fluid 1, fluid 2, > 0      */
-  double d0;            /* scale factor cs^2 = d0: (0,1) for D2Q9, (0,1/2) D3Q19    */
+  double d0;            /* scale factor cs^2 = d0: (0,1) for D2Q9, (0,1/2) in 3D    */
   double eta_hat;       /* CH parameter eta_1 = eta_hat / gamma_1, > 0 (0.1)        */
   double s_free_ch;     /* CH rates s0, s2a, s2b, s3, s4, in (0,2) (1)              */
   double s_free_ns;     /* NS rates s1, s3, in (0,2) (1)                            */

@@ -17,7 +17,7 @@ from .build import LIB
 c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 c_float_p = ctypes.POINTER(ctypes.c_float)
 
-LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_D2Q9, LBM_D3Q19, LBM_D3Q15 = 0, 1, 2
 LBM_PERIODIC_X, LBM_PERIODIC_Y, LBM_PERIODIC_Z = 1, 2, 4
 LBM_STORE_G_F16 = 1
 STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_EDIVERGED",
@@ -330,7 +330,7 @@ class Context:
             self.ctx = lbm_create_batch(lattice, nx, ny, nz, mask, batch)
         else:
             self.ctx = lbm_create(lattice, nx, ny, nz, mask, params if params is not None else lbm_default_params())
-        self.q = 9 if lattice == LBM_D2Q9 else 19
+        self.q = {LBM_D2Q9: 9, LBM_D3Q19: 19, LBM_D3Q15: 15}[lattice]
         self.d = 2 if lattice == LBM_D2Q9 else 3
 
     def close(self):

@@ -108,7 +108,7 @@ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 // Model constants of one instance (Sec. 2.2 Eq. kk and gamma_p; Sec. 3
 // relations for s1, the viscosity relation and the pressure constants).
 int derive(const lbm_params& p, int lattice, InstanceConsts& k, char* why) {
-  const bool is3d = lattice == LBM_D3Q19;
+  const bool is3d = lattice != LBM_D2Q9;
   const double d0 = p.d0;
   if (!finite_pos(p.W)) return snprintf(why, 128, "W must be > 0"), LBM_EINVAL;
   if (!(p.M_deg >= 0.0) || !(p.M_cst >= 0.0) || !finite_pos(p.M_deg + p.M_cst))
@@ -146,10 +146,14 @@ int derive(const lbm_params& p, int lattice, InstanceConsts& k, char* why) {
   const double eta = p.eta_hat / g1;
   const double s1c = 1.0 / (0.5 + (p.M_cst + p.M_deg) / (g1 * eta * cs2));
   double w0, wa, we;
-  if (is3d) {
+  if (lattice == LBM_D3Q19) {
     w0 = 1.0 - 3.0 * df + 3.0 * df * df;
     wa = (df - 2.0 * df * df) / 2.0;
     we = df * df / 4.0;
+  } else if (lattice == LBM_D3Q15) {   // Appendix A: corner weight d0^2 / 8
+    w0 = 1.0 - 3.0 * df + 2.0 * df * df;
+    wa = (df - df * df) / 2.0;
+    we = df * df / 8.0;
   } else {
     w0 = (1.0 - df) * (1.0 - df);
     wa = (df - df * df) / 2.0;
@@ -243,6 +247,7 @@ StepArgs step_args(lbm_ctx* c, int from) {
   a.depth = c->depth;
   a.nodes = c->nodes;
   a.g_half = c->g_half;
+  a.q = c->q;
   return a;
 }
 
@@ -487,11 +492,13 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
   if (!out) return set_err(nullptr, LBM_EINVAL, "out is NULL");
   *out = nullptr;
   if (flags & ~LBM_STORE_G_F16) return set_err(nullptr, LBM_EINVAL, "unknown flag");
-  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return set_err(nullptr, LBM_EINVAL, "unknown lattice");
+  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19 && lattice != LBM_D3Q15)
+    return set_err(nullptr, LBM_EINVAL, "unknown lattice");
   if (!params || nbatch < 1 || !nxs || !nys) return set_err(nullptr, LBM_EINVAL, "need nbatch >= 1 parameter sets");
   if (nbatch > 65535) return set_err(nullptr, LBM_EINVAL, "at most 65535 instances");
   const int g_half = (flags & LBM_STORE_G_F16) ? 1 : 0;
-  const bool is3d = lattice == LBM_D3Q19;
+  const bool is3d = lattice != LBM_D2Q9;
+  const int q = lattice == LBM_D3Q19 ? 19 : (lattice == LBM_D3Q15 ? 15 : 9);
   if (g_half && is3d) return set_err(nullptr, LBM_EUNSUPPORTED, "FP16 population storage is built for D2Q9 only");
   if (multi && is3d) return set_err(nullptr, LBM_EUNSUPPORTED, "instances of different sizes are built for D2Q9 only");
   if (!is3d && nz != 1) return set_err(nullptr, LBM_EINVAL, "D2Q9 needs nz = 1");
@@ -507,7 +514,7 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
       if (!per[a] && dims[a] < 2) return set_err(nullptr, LBM_EINVAL, "a wall axis needs at least 2 nodes");
     const long long nodes = (long long)nx * ny * nz;
     // kernels index the planes of one instance with 32-bit offsets
-    if (nodes * (is3d ? 19 : 9) >= (1LL << 31))
+    if (nodes * q >= (1LL << 31))
       return set_err(nullptr, LBM_EINVAL, "lattice too large for one instance");
     total += nodes;
     max_nodes = std::max(max_nodes, nodes);
@@ -523,7 +530,7 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
   c->ny = multi ? 0 : ny;
   c->nz = nz;
   c->nbatch = nbatch;
-  c->q = is3d ? 19 : 9;
+  c->q = q;
   c->d = is3d ? 3 : 2;
   for (int a = 0; a < 3; ++a) c->per[a] = per[a];
   c->nodes = multi ? 0 : (long long)nx * ny * nz;
@@ -583,7 +590,7 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
   if (e == cudaSuccess && is3d && lbm::d3q19_maps_bytes() <= sizeof(c->d3maps[0])) {
     int r = 0;
     for (int i = 0; i < 2 && r == 0; ++i)
-      r = lbm::build_d3q19_maps(static_cast<float*>(c->g[i]), c->mom, c->hist[i], nx, ny, nz, nbatch,
+      r = lbm::build_d3q19_maps(static_cast<float*>(c->g[i]), c->mom, c->hist[i], nx, ny, nz, nbatch, q,
                                 c->d3maps[i]);
     if (r < 0) e = cudaErrorInvalidValue;   // the driver refused a tensor map
     c->d3maps_ok = r == 0;
@@ -811,7 +818,7 @@ static int set_phase_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
   else
     e = lbm::launch_d3q19_init(c->phi0, stage, c->f[c->cur], static_cast<float*>(c->g[c->cur]), c->hist[c->cur],
                                c->dconsts, c->nx,
-                               c->ny, c->nz, c->per[0], c->per[1], c->per[2], c->nbatch, c->stream);
+                               c->ny, c->nz, c->per[0], c->per[1], c->per[2], c->nbatch, c->q, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   LBM_CK(c, cudaMemsetAsync(c->p, 0, sizeof(float) * c->total, c->stream));
   if (kind == cudaMemcpyHostToDevice) LBM_CK(c, cudaStreamSynchronize(c->stream));

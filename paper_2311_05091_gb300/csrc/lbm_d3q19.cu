@@ -48,7 +48,7 @@
 namespace lbm {
 namespace {
 
-constexpr int Q = 19;
+constexpr int NS = 19;                       // points of the isotropic stencil (D3Q19 velocities)
 constexpr int NH = 7;                        // history planes: phi1, u (3), S (3)
 constexpr int TX = 32, TY = 8, NT = TX * TY; // owned column tile, one thread per column
 constexpr int HX2 = TX + 4, HY2 = TY + 4, N2 = HX2 * HY2;   // tile with two halo columns
@@ -57,21 +57,45 @@ constexpr int RP = 4;                        // phi ring planes: z-1 .. z+2
 constexpr int RM = 3;                        // mubar / product ring planes: z-1 .. z+1
 constexpr float kOneMinusPhi0Floor = 5.9604644775390625e-8f;  // 2^-24
 
-// direction table (include/lbm.h): 0 rest, 1-6 axes, 7-18 edges
-__host__ __device__ constexpr int CX(int i) {
+// Stencil points (the D3Q19 velocities of include/lbm.h): 0 centre, 1-6 axes, 7-18 edges.
+__host__ __device__ constexpr int SX(int i) {
   return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
          : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
 }
-__host__ __device__ constexpr int CY(int i) {
+__host__ __device__ constexpr int SY(int i) {
   return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
          : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
 }
-__host__ __device__ constexpr int CZ(int i) {
+__host__ __device__ constexpr int SZ(int i) {
   return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
          : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
 }
-__host__ __device__ constexpr int OPP(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
-__host__ __device__ constexpr int CA(int i, int a) { return a == 0 ? CX(i) : (a == 1 ? CY(i) : CZ(i)); }
+__host__ __device__ constexpr int SA(int i, int a) { return a == 0 ? SX(i) : (a == 1 ? SY(i) : SZ(i)); }
+
+// Lattice velocities of the two 3D lattices (include/lbm.h).  D3Q19: as the
+// stencil points.  D3Q15 (the order of the printed M0, Appendix A): 0 rest,
+// 1-6 axes (+x, -x, +y, -y, +z, -z), 7-14 corners (1,1,1) (-1,1,1) (1,-1,1)
+// (-1,-1,1) (1,1,-1) (-1,1,-1) (1,-1,-1) (-1,-1,-1).
+template <int QL>
+__host__ __device__ constexpr int LX(int i) {
+  return QL == 19 ? SX(i) : (i == 1 || (i >= 7 && (i & 1))) ? 1 : ((i == 2 || (i >= 7 && !(i & 1))) ? -1 : 0);
+}
+template <int QL>
+__host__ __device__ constexpr int LY(int i) {
+  return QL == 19 ? SY(i)
+                  : (i == 3 || i == 7 || i == 8 || i == 11 || i == 12)
+                        ? 1
+                        : ((i == 4 || i == 9 || i == 10 || i == 13 || i == 14) ? -1 : 0);
+}
+template <int QL>
+__host__ __device__ constexpr int LZ(int i) {
+  return QL == 19 ? SZ(i) : (i == 5 || (i >= 7 && i <= 10)) ? 1 : ((i == 6 || i >= 11) ? -1 : 0);
+}
+// opposite direction
+template <int QL>
+__host__ __device__ constexpr int LOPP(int i) {
+  return i == 0 ? 0 : (i < 7 || QL == 19) ? ((i & 1) ? i + 1 : i - 1) : 21 - i;
+}
 
 __device__ __forceinline__ int wrap_or_mirror(int i, int n, int per) {
   if (per) {
@@ -87,8 +111,8 @@ __device__ __forceinline__ int ring(int r, int n) { return ((r % n) + n) % n; }
 
 // value of a ring-stored field at x + c_d: planes pm (z-1), p0 (z), pp (z+1), row stride sw
 __device__ __forceinline__ float nb(const float* pm, const float* p0, const float* pp, int i, int sw, int d) {
-  const float* pl = CZ(d) > 0 ? pp : (CZ(d) < 0 ? pm : p0);
-  return pl[i + CY(d) * sw + CX(d)];
+  const float* pl = SZ(d) > 0 ? pp : (SZ(d) < 0 ? pm : p0);
+  return pl[i + SY(d) * sw + SX(d)];
 }
 
 // Isotropic central derivative along axis A with the D3Q19 weights of d0 = 1/3
@@ -97,8 +121,8 @@ template <int A>
 __device__ __forceinline__ float dgrad(const float* pm, const float* p0, const float* pp, int i, int sw) {
   float axis = 0.f, edge = 0.f;
 #pragma unroll
-  for (int d = 1; d < Q; ++d) {
-    const int c = CA(d, A);
+  for (int d = 1; d < NS; ++d) {
+    const int c = SA(d, A);
     if (c == 0) continue;
     const float v = nb(pm, p0, pp, i, sw, d);
     if (d < 7) axis += c > 0 ? v : -v;
@@ -112,7 +136,7 @@ __device__ __forceinline__ float lap3(const float* pm, const float* p0, const fl
   const float c = p0[i];
   float axis = 0.f, edge = 0.f;
 #pragma unroll
-  for (int d = 1; d < Q; ++d) {
+  for (int d = 1; d < NS; ++d) {
     const float v = nb(pm, p0, pp, i, sw, d) - c;
     if (d < 7) axis += v;
     else edge += v;
@@ -122,17 +146,17 @@ __device__ __forceinline__ float lap3(const float* pm, const float* p0, const fl
 
 // The same two operators on the 19 values v[d] = v(x + c_d), gathered once.
 __device__ __forceinline__ void gather19(const float* pm, const float* p0, const float* pp, int i, int sw,
-                                         float (&v)[Q]) {
+                                         float (&v)[NS]) {
 #pragma unroll
-  for (int d = 0; d < Q; ++d) v[d] = nb(pm, p0, pp, i, sw, d);
+  for (int d = 0; d < NS; ++d) v[d] = nb(pm, p0, pp, i, sw, d);
 }
 
 template <int A>
-__device__ __forceinline__ float dgrad_v(const float (&v)[Q]) {
+__device__ __forceinline__ float dgrad_v(const float (&v)[NS]) {
   float axis = 0.f, edge = 0.f;
 #pragma unroll
-  for (int d = 1; d < Q; ++d) {
-    const int c = CA(d, A);
+  for (int d = 1; d < NS; ++d) {
+    const int c = SA(d, A);
     if (c == 0) continue;
     if (d < 7) axis += c > 0 ? v[d] : -v[d];
     else edge += c > 0 ? v[d] : -v[d];
@@ -140,10 +164,10 @@ __device__ __forceinline__ float dgrad_v(const float (&v)[Q]) {
   return axis * (1.f / 6.f) + edge * (1.f / 12.f);
 }
 
-__device__ __forceinline__ float lap_v(const float (&v)[Q]) {
+__device__ __forceinline__ float lap_v(const float (&v)[NS]) {
   float axis = 0.f, edge = 0.f;
 #pragma unroll
-  for (int d = 1; d < Q; ++d) {
+  for (int d = 1; d < NS; ++d) {
     const float w = v[d] - v[0];
     if (d < 7) axis += w;
     else edge += w;
@@ -177,6 +201,7 @@ __device__ __forceinline__ float weight(const InstanceConsts& k, int i) {
 // initial state: f = f^eq(phi1, mubar_1, u = 0), g = g^eq(p = 0, u = 0) - rho_0 e_0 = 0,
 // history = (phi1, 0, ..., 0).  phi1 arrives staged in plane 0 of a spare history buffer.
 // ---------------------------------------------------------------------------
+template <int QL>
 __global__ void d3q19_init(const float* __restrict__ phi0_all, const float* __restrict__ phi1_all,
                            float* __restrict__ f_all, float* __restrict__ g_all, float* __restrict__ hist_all,
                            const InstanceConsts* __restrict__ consts, int nx, int ny, int nz, int per_x,
@@ -192,15 +217,15 @@ __global__ void d3q19_init(const float* __restrict__ phi0_all, const float* __re
     const float* phi0 = phi0_all + (long long)b * nodes;
     const float* phi1 = phi1_all + (long long)b * NH * nodes;
     auto at = [&](const float* a, int d) {
-      const int xx = wrap_or_mirror(x + CX(d), nx, per_x);
-      const int yy = wrap_or_mirror(y + CY(d), ny, per_y);
-      const int zz = wrap_or_mirror(z + CZ(d), nz, per_z);
+      const int xx = wrap_or_mirror(x + SX(d), nx, per_x);
+      const int yy = wrap_or_mirror(y + SY(d), ny, per_y);
+      const int zz = wrap_or_mirror(z + SZ(d), nz, per_z);
       return a[((long long)zz * ny + yy) * nx + xx];
     };
     const float c0 = phi0[node], c1 = phi1[node];
     float a0 = 0.f, e0 = 0.f, a1 = 0.f, e1 = 0.f;
 #pragma unroll
-    for (int d = 1; d < Q; ++d) {
+    for (int d = 1; d < NS; ++d) {
       const float v0 = at(phi0, d) - c0, v1 = at(phi1, d) - c1;
       if (d < 7) {
         a0 += v0;
@@ -215,14 +240,14 @@ __global__ void d3q19_init(const float* __restrict__ phi0_all, const float* __re
     float mu0, mu1, mu2;
     chem_pot(k, c0, c1, lap0, lap1, mu0, mu1, mu2);
     const float emb = k.eta * mubar1_of(k, mu0, mu1, mu2);
-    float* f = f_all + (long long)b * Q * nodes;
-    float* g = g_all + (long long)b * Q * nodes;
+    float* f = f_all + (long long)b * QL * nodes;
+    float* g = g_all + (long long)b * QL * nodes;
     float* h = hist_all + (long long)b * NH * nodes;
     f[node] = c1 + (k.w0 - 1.f) * emb;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) f[(long long)i * nodes + node] = (i < 7 ? k.wa : k.we) * emb;
+    for (int i = 1; i < QL; ++i) f[(long long)i * nodes + node] = (i < 7 ? k.wa : k.we) * emb;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[(long long)i * nodes + node] = 0.f;
+    for (int i = 0; i < QL; ++i) g[(long long)i * nodes + node] = 0.f;
     h[node] = c1;
 #pragma unroll
     for (int q = 1; q < NH; ++q) h[(long long)q * nodes + node] = 0.f;
@@ -232,48 +257,50 @@ __global__ void d3q19_init(const float* __restrict__ phi0_all, const float* __re
 // ---------------------------------------------------------------------------
 // moment pass: phi1 = sum_i f_i -> history plane 0, j = sum_i c_i f_i -> scratch
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void moments19(const float (&v)[Q], float& s, float& jx, float& jy, float& jz) {
+template <int QL>
+__device__ __forceinline__ void moments_q(const float (&v)[QL], float& s, float& jx, float& jy, float& jz) {
   s = v[0];
   jx = 0.f;
   jy = 0.f;
   jz = 0.f;
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
+  for (int i = 1; i < QL; ++i) {
     s += v[i];
-    if (CX(i)) jx += CX(i) > 0 ? v[i] : -v[i];
-    if (CY(i)) jy += CY(i) > 0 ? v[i] : -v[i];
-    if (CZ(i)) jz += CZ(i) > 0 ? v[i] : -v[i];
+    if (LX<QL>(i)) jx += LX<QL>(i) > 0 ? v[i] : -v[i];
+    if (LY<QL>(i)) jy += LY<QL>(i) > 0 ? v[i] : -v[i];
+    if (LZ<QL>(i)) jz += LZ<QL>(i) > 0 ? v[i] : -v[i];
   }
 }
 
-__global__ void __launch_bounds__(256) d3q19_moments(const float* __restrict__ f_all, float* __restrict__ hist_all,
+template <int QL>
+__global__ void __launch_bounds__(256) d3q_moments(const float* __restrict__ f_all, float* __restrict__ hist_all,
                                                      float* __restrict__ mom_all, int nodes, int vec4) {
   const int b = blockIdx.y;
-  const float* f = f_all + (long long)b * Q * nodes;
+  const float* f = f_all + (long long)b * QL * nodes;
   float* h = hist_all + (long long)b * NH * nodes;
   float* m = mom_all + (long long)b * 3 * nodes;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (vec4) {
     const int n4 = nodes >> 2;
     if (t >= n4) return;
-    float4 v[Q];
+    float4 v[QL];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] = __ldcs(reinterpret_cast<const float4*>(f + (long long)i * nodes) + t);
+    for (int i = 0; i < QL; ++i) v[i] = __ldcs(reinterpret_cast<const float4*>(f + (long long)i * nodes) + t);
     float4 s, jx, jy, jz;
     {
-      float a[Q];
+      float a[QL];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) a[i] = v[i].x;
-      moments19(a, s.x, jx.x, jy.x, jz.x);
+      for (int i = 0; i < QL; ++i) a[i] = v[i].x;
+      moments_q<QL>(a, s.x, jx.x, jy.x, jz.x);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) a[i] = v[i].y;
-      moments19(a, s.y, jx.y, jy.y, jz.y);
+      for (int i = 0; i < QL; ++i) a[i] = v[i].y;
+      moments_q<QL>(a, s.y, jx.y, jy.y, jz.y);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) a[i] = v[i].z;
-      moments19(a, s.z, jx.z, jy.z, jz.z);
+      for (int i = 0; i < QL; ++i) a[i] = v[i].z;
+      moments_q<QL>(a, s.z, jx.z, jy.z, jz.z);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) a[i] = v[i].w;
-      moments19(a, s.w, jx.w, jy.w, jz.w);
+      for (int i = 0; i < QL; ++i) a[i] = v[i].w;
+      moments_q<QL>(a, s.w, jx.w, jy.w, jz.w);
     }
     reinterpret_cast<float4*>(h)[t] = s;
     reinterpret_cast<float4*>(m)[t] = jx;
@@ -281,11 +308,11 @@ __global__ void __launch_bounds__(256) d3q19_moments(const float* __restrict__ f
     reinterpret_cast<float4*>(m + 2 * (long long)nodes)[t] = jz;
   } else {
     if (t >= nodes) return;
-    float a[Q];
+    float a[QL];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) a[i] = __ldcs(f + (long long)i * nodes + t);
+    for (int i = 0; i < QL; ++i) a[i] = __ldcs(f + (long long)i * nodes + t);
     float s, jx, jy, jz;
-    moments19(a, s, jx, jy, jz);
+    moments_q<QL>(a, s, jx, jy, jz);
     h[t] = s;
     m[t] = jx;
     m[nodes + t] = jy;
@@ -298,8 +325,9 @@ __global__ void __launch_bounds__(256) d3q19_moments(const float* __restrict__ f
 // ---------------------------------------------------------------------------
 // Inputs of one node that do not come from a stencil: its NS populations, the
 // first moment j of its CH populations and its previous-step history.
+template <int QL>
 struct OwnIn {
-  float g[Q];
+  float g[QL];
   float jx, jy, jz;
   float php, upx, upy, upz, spx, spy, spz;
 };
@@ -326,8 +354,8 @@ struct Outs {
   int nx, ny, nz, per_x, per_y, per_z, nodes, plane;
 };
 
-template <bool OBS>
-__device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings& R, const OwnIn& in,
+template <int QL, bool OBS>
+__device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings& R, const OwnIn<QL>& in,
                                             const Outs& o, int x, int y, int z) {
   const int nx = o.nx, ny = o.ny, nz = o.nz, nodes = o.nodes, plane = o.plane;
   const int node = z * plane + y * nx + x;
@@ -337,7 +365,7 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
   // stencils of phi0, phi1 and mubar_1, products; each neighbourhood is read once
   float ph0, ph1, g0x, g0y, g0z, g1x, g1y, g1z, lap0, lap1;
   {
-    float v[Q];
+    float v[NS];
     gather19(R.p0[0], R.p0[1], R.p0[2], i2, s2, v);
     ph0 = v[0];
     g0x = dgrad_v<0>(v);
@@ -357,7 +385,7 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
   const float d02 = mu0 - mu2, d12 = mu1 - mu2;
   float mub, gmx, gmy, gmz, dAxy_x, dAxy_y, dAxz_x, dAxz_z, dAyz_y, dAyz_z;
   {
-    float v[Q];
+    float v[NS];
     gather19(R.mu[0], R.mu[1], R.mu[2], i1, s1, v);
     mub = v[0];
     gmx = dgrad_v<0>(v);
@@ -403,8 +431,8 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
   float sum_nz = 0.f, mx = 0.f, my = 0.f, mz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
   float ex = 0.f, ey = 0.f, ez = 0.f, bxm = 0.f, bym = 0.f, bzm = 0.f;
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int cx = CX(i), cy = CY(i), cz = CZ(i);
+  for (int i = 1; i < QL; ++i) {
+    const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
     const float v = g[i];
     sum_nz += v;
     if (cx) mx += cx > 0 ? v : -v;
@@ -413,19 +441,22 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
     if (cx && cy) pxy += cx * cy > 0 ? v : -v;
     if (cx && cz) pxz += cx * cz > 0 ? v : -v;
     if (cy && cz) pyz += cy * cz > 0 ? v : -v;
-    // third-order sums: sum c_a (c_b^2 + c_c^2) g and sum c_a (c_b^2 - c_c^2) g (cyclic a, b, c)
+    // third-order sums.  D3Q19: sum c_a (c_b^2 + c_c^2) g and sum c_a (c_b^2 - c_c^2) g (cyclic a, b, c);
+    // D3Q15: the corner sums sum_corner c_a g and sum cx cy cz g (in bxm)
     if (cx && (cy || cz)) {
       ex += cx > 0 ? v : -v;
-      bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v;
+      if constexpr (QL == 19) bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v;
     }
     if (cy && (cz || cx)) {
       ey += cy > 0 ? v : -v;
-      bym += ((cz ? 1 : -1) * cy > 0) ? v : -v;
+      if constexpr (QL == 19) bym += ((cz ? 1 : -1) * cy > 0) ? v : -v;
     }
     if (cz && (cx || cy)) {
       ez += cz > 0 ? v : -v;
-      bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v;
+      if constexpr (QL == 19) bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v;
     }
+    if constexpr (QL == 15)
+      if (cx && cy && cz) bxm += cx * cy * cz > 0 ? v : -v;
   }
 
   // velocity with the solid penalisation force (u_w = 0)
@@ -461,13 +492,13 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
   const int oyp = y + 1 < ny ? nx : nx - plane, oym = y > 0 ? -nx : plane - nx;
   const int ozp = z + 1 < nz ? plane : plane - nodes, ozm = z > 0 ? -plane : nodes - plane;
   auto store = [&](float* __restrict__ out, int i, float v) {
-    const int cx = CX(i), cy = CY(i), cz = CZ(i);
+    const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
     int off = 0;
     bool bb = false;
     if (cx) { off += cx > 0 ? oxp : oxm; bb = bb || (cx > 0 ? wxp : wxm); }
     if (cy) { off += cy > 0 ? oyp : oym; bb = bb || (cy > 0 ? wyp : wym); }
     if (cz) { off += cz > 0 ? ozp : ozm; bb = bb || (cz > 0 ? wzp : wzm); }
-    out[bb ? OPP(i) * nodes + node : i * nodes + node + off] = v;
+    out[bb ? LOPP<QL>(i) * nodes + node : i * nodes + node + off] = v;
   };
 
   // ---- NS collision: g* = (1 - s2a) g + w_i X_i (see the file header) ----
@@ -502,12 +533,14 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
     const float Oxy = (s2a * exy + om2a * Mxy - db * (pxy - exy + 0.5f * Mxy)) * ic4;
     const float Oxz = (s2a * exz + om2a * Mxz - db * (pxz - exz + 0.5f * Mxz)) * ic4;
     const float Oyz = (s2a * eyz + om2a * Myz - db * (pyz - eyz + 0.5f * Myz)) * ic4;
-    // third-order group: T_a = (s3 - s2a) m_A,a / |A|^2, U_a = (s3 - s2a) m_B,a / |B|^2
+    // third-order group: T_a = (s3 - s2a) m_A,a / |A|^2, U_a = (s3 - s2a) m_B,a / |B|^2.  D3Q15: A_a =
+    // corner c_a - cs2 c_a with |A|^2 = cs2^2 (1 - cs2), one B = cx cy cz with |B|^2 = cs2^2 (in Ux)
     const float d3 = k.s3n - s2a;
-    const float iB = __frcp_rn(2.f * cs4), iA = __frcp_rn(2.f * cs4 * (1.f - 2.f * cs2));
-    const float k3 = 1.f - 2.f * cs2;
-    const float Tx = d3 * (ex - 2.f * cs2 * mx) * iA, Ty = d3 * (ey - 2.f * cs2 * my) * iA,
-                Tz = d3 * (ez - 2.f * cs2 * mz) * iA;
+    const float iB = __frcp_rn(QL == 19 ? 2.f * cs4 : cs4);
+    const float iA = __frcp_rn(QL == 19 ? 2.f * cs4 * (1.f - 2.f * cs2) : cs4 * (1.f - cs2));
+    const float k3 = QL == 19 ? 1.f - 2.f * cs2 : 1.f - cs2;
+    const float cA = QL == 19 ? 2.f * cs2 : cs2;
+    const float Tx = d3 * (ex - cA * mx) * iA, Ty = d3 * (ey - cA * my) * iA, Tz = d3 * (ez - cA * mz) * iA;
     const float Ux = d3 * bxm * iB, Uy = d3 * bym * iB, Uz = d3 * bzm * iB;
     const float Px = k3 * Tx + Ux, Qx = k3 * Tx - Ux;   // edge factors per axis: B_a = +c_a or -c_a
     const float Py = k3 * Ty + Uy, Qy = k3 * Ty - Uy;
@@ -515,8 +548,8 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
     const float om1 = 1.f - s2a;
     store(o.g_out, 0, om1 * g[0] + k.w0 * base - s2a * p * ic2);
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int cx = CX(i), cy = CY(i), cz = CZ(i);
+    for (int i = 1; i < QL; ++i) {
+      const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
       float X = base;
       if (cx) X += cx > 0 ? Dx + Vx : Dx - Vx;
       if (cy) X += cy > 0 ? Dy + Vy : Dy - Vy;
@@ -525,15 +558,19 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
       if (cx && cz) X += cx * cz > 0 ? Oxz : -Oxz;
       if (cy && cz) X += cy * cz > 0 ? Oyz : -Oyz;
       if (i < 7) {
-        // axis: A_a(c) = -2 cs2 c_a, B_a(c) = 0
+        // axis: A_a(c) = -2 cs2 c_a (D3Q19), -cs2 c_a (D3Q15); B = 0
         const float T = cx ? Tx : (cy ? Ty : Tz);
         const int c = cx + cy + cz;
-        X += c > 0 ? 2.f * cs2 * T : -2.f * cs2 * T;
-      } else {
+        X += c > 0 ? cA * T : -cA * T;
+      } else if constexpr (QL == 19) {
         // edge: -c_a [(1 - 2 cs2) T_a + B_a U_a / c_a] over its two axes
         if (cx) { const float e = cy ? Px : Qx; X -= cx > 0 ? e : -e; }
         if (cy) { const float e = cz ? Py : Qy; X -= cy > 0 ? e : -e; }
         if (cz) { const float e = cx ? Pz : Qz; X -= cz > 0 ? e : -e; }
+      } else {
+        // corner: -(1 - cs2) c.T - cx cy cz U
+        const float ct = (cx > 0 ? Tx : -Tx) + (cy > 0 ? Ty : -Ty) + (cz > 0 ? Tz : -Tz);
+        X -= k3 * ct + (cx * cy * cz > 0 ? Ux : -Ux);
       }
       store(o.g_out, i, om1 * g[i] + weight(k, i) * X);
     }
@@ -556,8 +593,8 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
       const float az = (ph1 * uz + (1.f - k.s1c) * (jz - ph1 * uz) + (1.f - 0.5f * k.s1c) * Rz) * ic2;
       float rest = ph1;
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int cx = CX(i), cy = CY(i), cz = CZ(i);
+      for (int i = 1; i < QL; ++i) {
+        const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
         float s = emb;
         if (cx) s += cx > 0 ? ax : -ax;
         if (cy) s += cy > 0 ? ay : -ay;
@@ -568,14 +605,14 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
       }
       store(o.f_out, 0, rest);   // the rest population closes the zeroth moment
     } else {
-      float f[Q];
+      float f[QL];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) f[i] = o.f_in[i * nodes + node];
+      for (int i = 0; i < QL; ++i) f[i] = o.f_in[i * nodes + node];
       float jx = 0.f, jy = 0.f, jz = 0.f, qxx = 0.f, qyy = 0.f, qzz = 0.f, qxy = 0.f, qxz = 0.f, qyz = 0.f;
       float ex = 0.f, ey = 0.f, ez = 0.f, bxm = 0.f, bym = 0.f, bzm = 0.f;
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int cx = CX(i), cy = CY(i), cz = CZ(i);
+      for (int i = 1; i < QL; ++i) {
+        const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
         const float v = f[i];
         if (cx) { jx += cx > 0 ? v : -v; qxx += v; }
         if (cy) { jy += cy > 0 ? v : -v; qyy += v; }
@@ -583,9 +620,11 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
         if (cx && cy) qxy += cx * cy > 0 ? v : -v;
         if (cx && cz) qxz += cx * cz > 0 ? v : -v;
         if (cy && cz) qyz += cy * cz > 0 ? v : -v;
-        if (cx && (cy || cz)) { ex += cx > 0 ? v : -v; bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v; }
-        if (cy && (cz || cx)) { ey += cy > 0 ? v : -v; bym += ((cz ? 1 : -1) * cy > 0) ? v : -v; }
-        if (cz && (cx || cy)) { ez += cz > 0 ? v : -v; bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v; }
+        if (cx && (cy || cz)) { ex += cx > 0 ? v : -v; if constexpr (QL == 19) bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v; }
+        if (cy && (cz || cx)) { ey += cy > 0 ? v : -v; if constexpr (QL == 19) bym += ((cz ? 1 : -1) * cy > 0) ? v : -v; }
+        if (cz && (cx || cy)) { ez += cz > 0 ? v : -v; if constexpr (QL == 19) bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v; }
+        if constexpr (QL == 15)
+          if (cx && cy && cz) bxm += cx * cy * cz > 0 ? v : -v;
       }
       const float s4 = k.s4c, om4 = 1.f - s4, oh4 = 1.f - 0.5f * s4;
       const float d1 = (k.s1c - s4) * ic2;
@@ -594,10 +633,11 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
       const float m2x = qxx - cs2 * emb, m2y = qyy - cs2 * emb, m2z = qzz - cs2 * emb;
       const float d2b = (k.s2bc - s4) * __frcp_rn(cs4);
       const float d3 = k.s3c - s4;
-      const float iB = __frcp_rn(2.f * cs4), iA = __frcp_rn(2.f * cs4 * (1.f - 2.f * cs2));
-      const float k3 = 1.f - 2.f * cs2;
-      const float Tx = d3 * (ex - 2.f * cs2 * jx) * iA, Ty = d3 * (ey - 2.f * cs2 * jy) * iA,
-                  Tz = d3 * (ez - 2.f * cs2 * jz) * iA;
+      const float iB = __frcp_rn(QL == 19 ? 2.f * cs4 : cs4);
+      const float iA = __frcp_rn(QL == 19 ? 2.f * cs4 * (1.f - 2.f * cs2) : cs4 * (1.f - cs2));
+      const float k3 = QL == 19 ? 1.f - 2.f * cs2 : 1.f - cs2;
+      const float cA = QL == 19 ? 2.f * cs2 : cs2;
+      const float Tx = d3 * (ex - cA * jx) * iA, Ty = d3 * (ey - cA * jy) * iA, Tz = d3 * (ez - cA * jz) * iA;
       const float Ux = d3 * bxm * iB, Uy = d3 * bym * iB, Uz = d3 * bzm * iB;
       const float Px = k3 * Tx + Ux, Qx = k3 * Tx - Ux;
       const float Py = k3 * Ty + Uy, Qy = k3 * Ty - Uy;
@@ -608,8 +648,8 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
       const float ux1 = ph1 * ux * ic2, uy1 = ph1 * uy * ic2, uz1 = ph1 * uz * ic2;
       const float rx = Rx * ic2, ry = Ry * ic2, rz = Rz * ic2;
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int cx = CX(i), cy = CY(i), cz = CZ(i);
+      for (int i = 1; i < QL; ++i) {
+        const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
         // f^eq_i / w_i = eta mubar + c.phi u / cs2;  R_i / w_i = c.R / cs2
         float feq = emb, Rc = 0.f, L = p2;
         if (cx) { feq += cx > 0 ? ux1 : -ux1; Rc += cx > 0 ? rx : -rx; L += (cx > 0 ? m1x : -m1x) * d1 + d2a * m2x; }
@@ -621,11 +661,14 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
         if (i < 7) {
           const float T = cx ? Tx : (cy ? Ty : Tz);
           const int c = cx + cy + cz;
-          L -= c > 0 ? 2.f * cs2 * T : -2.f * cs2 * T;
-        } else {
+          L -= c > 0 ? cA * T : -cA * T;
+        } else if constexpr (QL == 19) {
           if (cx) { const float e = cy ? Px : Qx; L += cx > 0 ? e : -e; }
           if (cy) { const float e = cz ? Py : Qy; L += cy > 0 ? e : -e; }
           if (cz) { const float e = cx ? Pz : Qz; L += cz > 0 ? e : -e; }
+        } else {
+          const float ct = (cx > 0 ? Tx : -Tx) + (cy > 0 ? Ty : -Ty) + (cz > 0 ? Tz : -Tz);
+          L += k3 * ct + (cx * cy * cz > 0 ? Ux : -Ux);
         }
         const float w = weight(k, i);
         store(o.f_out, i, om4 * f[i] + w * (s4 * feq + oh4 * Rc - L));
@@ -658,7 +701,7 @@ struct StepSmem3 {
   InstanceConsts k;
 };
 
-template <bool OBS>
+template <int QL, bool OBS>
 __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   StepSmem3& S = *reinterpret_cast<StepSmem3*>(smem_raw);
@@ -679,15 +722,15 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   if (t < (int)(sizeof(InstanceConsts) / 4))
     reinterpret_cast<float*>(&S.k)[t] = reinterpret_cast<const float*>(a.consts + b)[t];
 
-  const float* __restrict__ g_in = static_cast<const float*>(a.g_in) + (long long)b * Q * nodes;
+  const float* __restrict__ g_in = static_cast<const float*>(a.g_in) + (long long)b * QL * nodes;
   const float* __restrict__ p0_in = a.phi0 + (long long)b * nodes;
   const float* __restrict__ h_in = a.hist_in + (long long)b * NH * nodes;
   const float* __restrict__ phi1_now = a.hist_out + (long long)b * NH * nodes;   // moment pass of this step
   const float* __restrict__ j_in = a.mom + (long long)b * 3 * nodes;
   Outs o;
-  o.f_in = a.f_in + (long long)b * Q * nodes;
-  o.f_out = a.f_out + (long long)b * Q * nodes;
-  o.g_out = static_cast<float*>(a.g_out) + (long long)b * Q * nodes;
+  o.f_in = a.f_in + (long long)b * QL * nodes;
+  o.f_out = a.f_out + (long long)b * QL * nodes;
+  o.g_out = static_cast<float*>(a.g_out) + (long long)b * QL * nodes;
   o.h_out = a.hist_out + (long long)b * NH * nodes;
   o.p_out = a.p_out + (long long)b * nodes;
   o.flag = a.flag;
@@ -757,9 +800,9 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
     if (!own) continue;
 
     const int node = z * plane + y * nx + x;
-    OwnIn in;
+    OwnIn<QL> in;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) in.g[i] = __ldcs(g_in + i * nodes + node);
+    for (int i = 0; i < QL; ++i) in.g[i] = __ldcs(g_in + i * nodes + node);
     in.jx = j_in[node];
     in.jy = j_in[nodes + node];
     in.jz = j_in[2 * nodes + node];
@@ -785,7 +828,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
     R.sw2 = HX2;
     R.i1 = (ty + 1) * HX1 + (tx + 1);
     R.sw1 = HX1;
-    node_update<OBS>(k, R, in, o, x, y, z);
+    node_update<QL, OBS>(k, R, in, o, x, y, z);
   }
 }
 
@@ -800,16 +843,17 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
 constexpr int PW = 40;                       // halo tile row: columns x0-4 .. x0+35 (16-byte aligned chunks)
 constexpr int PR2 = TY + 4, PR1 = TY + 2;    // rows of the two-halo and one-halo tiles
 constexpr int RP5 = 5;                       // phi ring: z-1 .. z+2 in use, z+3 in flight
-constexpr int NOWN = Q + 3 + NH;             // owned planes per z: g, j, history
-constexpr unsigned kOwnBytes = NOWN * NT * 4;
+template <int QL>
+__host__ __device__ constexpr int nown() { return QL + 3 + NH; }   // owned planes per z: g, j, history
 constexpr int kSpinLimit = 1 << 22;          // try_wait polls before a TMA wait gives up
 
 struct TmaMaps {
-  CUtensorMap g, j, h;   // g: (nx, ny, nz, 19 nb), j: (.., 3 nb), h: (.., 7 nb); boxes 32 x 8 x 1 x {19, 3, 7}
+  CUtensorMap g, j, h;   // g: (nx, ny, nz, QL nb), j: (.., 3 nb), h: (.., 7 nb); boxes 32 x 8 x 1 x {QL, 3, 7}
 };
 
+template <int QL>
 struct alignas(128) PipeSmem3 {
-  float own[NOWN][NT];              // TMA destination: g 0-18, j 19-21, history 22-28
+  float own[nown<QL>()][NT];        // TMA destination: g 0..QL-1, j QL..QL+2, history QL+3..QL+9
   float phi1[RP5][PR2 * PW];
   float phi0[RP5][PR2 * PW];
   float hus[2][6][PR1 * PW];        // history u, S (planes 1-6) on the one-halo tile
@@ -859,10 +903,11 @@ __device__ __forceinline__ void tma_load4(float* dst, const CUtensorMap* map, in
       : "memory");
 }
 
-template <bool OBS>
+template <int QL, bool OBS>
 __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const __grid_constant__ TmaMaps maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  PipeSmem3& S = *reinterpret_cast<PipeSmem3*>(smem_raw);
+  PipeSmem3<QL>& S = *reinterpret_cast<PipeSmem3<QL>*>(smem_raw);
+  constexpr unsigned kOwnBytes = nown<QL>() * NT * 4;
 
   const int t = threadIdx.x;
   const int tx = t % TX, ty = t / TX;
@@ -883,9 +928,9 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   const float* __restrict__ h_in = a.hist_in + (long long)b * NH * nodes;
   const float* __restrict__ phi1_now = a.hist_out + (long long)b * NH * nodes;   // moment pass of this step
   Outs o;
-  o.f_in = a.f_in + (long long)b * Q * nodes;
-  o.f_out = a.f_out + (long long)b * Q * nodes;
-  o.g_out = static_cast<float*>(a.g_out) + (long long)b * Q * nodes;
+  o.f_in = a.f_in + (long long)b * QL * nodes;
+  o.f_out = a.f_out + (long long)b * QL * nodes;
+  o.g_out = static_cast<float*>(a.g_out) + (long long)b * QL * nodes;
   o.h_out = a.hist_out + (long long)b * NH * nodes;
   o.p_out = a.p_out + (long long)b * nodes;
   o.flag = a.flag;
@@ -961,9 +1006,9 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   auto issue_own = [&](int z) {   // one thread
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     bar_expect(&S.bar, kOwnBytes);
-    tma_load4(S.own[0], &maps.g, x0, y0, z, b * Q, &S.bar);
-    tma_load4(S.own[Q], &maps.j, x0, y0, z, b * 3, &S.bar);
-    tma_load4(S.own[Q + 3], &maps.h, x0, y0, z, b * NH, &S.bar);
+    tma_load4(S.own[0], &maps.g, x0, y0, z, b * QL, &S.bar);
+    tma_load4(S.own[QL], &maps.j, x0, y0, z, b * 3, &S.bar);
+    tma_load4(S.own[QL + 3], &maps.h, x0, y0, z, b * NH, &S.bar);
   };
 
   const InstanceConsts& k = S.k;
@@ -1042,19 +1087,19 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
     __syncthreads();
 
     // owned inputs of plane z into registers, then the slot takes plane z+1
-    OwnIn in;
+    OwnIn<QL> in;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) in.g[i] = S.own[i][t];
-    in.jx = S.own[Q][t];
-    in.jy = S.own[Q + 1][t];
-    in.jz = S.own[Q + 2][t];
-    in.php = S.own[Q + 3][t];
-    in.upx = S.own[Q + 4][t];
-    in.upy = S.own[Q + 5][t];
-    in.upz = S.own[Q + 6][t];
-    in.spx = S.own[Q + 7][t];
-    in.spy = S.own[Q + 8][t];
-    in.spz = S.own[Q + 9][t];
+    for (int i = 0; i < QL; ++i) in.g[i] = S.own[i][t];
+    in.jx = S.own[QL][t];
+    in.jy = S.own[QL + 1][t];
+    in.jz = S.own[QL + 2][t];
+    in.php = S.own[QL + 3][t];
+    in.upx = S.own[QL + 4][t];
+    in.upy = S.own[QL + 5][t];
+    in.upz = S.own[QL + 6][t];
+    in.spx = S.own[QL + 7][t];
+    in.spy = S.own[QL + 8][t];
+    in.spz = S.own[QL + 9][t];
     __syncthreads();
     if (t == 0 && z + 1 < ze) issue_own(z + 1);
     if (!own) continue;
@@ -1072,7 +1117,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
     R.sw2 = PW;
     R.i1 = (ty + 1) * HX1 + (tx + 1);
     R.sw1 = HX1;
-    node_update<OBS>(k, R, in, o, x, y, z);
+    node_update<QL, OBS>(k, R, in, o, x, y, z);
   }
   // leave no copy in flight: asynchronous copies, and a TMA load issued for a plane not processed
   cp_wait_all();
@@ -1083,11 +1128,15 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
 
 cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, float* g, float* hist,
                               const InstanceConsts* consts, int nx, int ny, int nz, int per_x, int per_y,
-                              int per_z, int nbatch, cudaStream_t s) {
+                              int per_z, int nbatch, int q, cudaStream_t s) {
   const long long total = (long long)nx * ny * nz * nbatch;
   const long long blocks = std::min<long long>((total + 255) / 256, 1LL << 20);
-  d3q19_init<<<(unsigned)blocks, 256, 0, s>>>(phi0, phi1, f, g, hist, consts, nx, ny, nz, per_x, per_y, per_z,
-                                               nbatch);
+  if (q == 15)
+    d3q19_init<15><<<(unsigned)blocks, 256, 0, s>>>(phi0, phi1, f, g, hist, consts, nx, ny, nz, per_x, per_y, per_z,
+                                                     nbatch);
+  else
+    d3q19_init<19><<<(unsigned)blocks, 256, 0, s>>>(phi0, phi1, f, g, hist, consts, nx, ny, nz, per_x, per_y, per_z,
+                                                     nbatch);
   return cudaGetLastError();
 }
 
@@ -1096,21 +1145,23 @@ cudaError_t launch_d3q19_moments(const StepArgs& a, int nbatch, cudaStream_t s) 
   const int vec4 = (nodes & 3) == 0;
   const int per_thread = vec4 ? 4 : 1;
   const int mblocks = (nodes / per_thread + 255) / 256;
-  d3q19_moments<<<dim3(mblocks, nbatch), 256, 0, s>>>(a.f_in, a.hist_out, a.mom, nodes, vec4);
+  const float* f = static_cast<const float*>(a.f_in);
+  if (a.q == 15) d3q_moments<15><<<dim3(mblocks, nbatch), 256, 0, s>>>(f, a.hist_out, a.mom, nodes, vec4);
+  else d3q_moments<19><<<dim3(mblocks, nbatch), 256, 0, s>>>(f, a.hist_out, a.mom, nodes, vec4);
   return cudaGetLastError();
 }
 
 size_t d3q19_maps_bytes() { return sizeof(TmaMaps); }
 
-int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx, int ny, int nz, int nbatch,
+int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx, int ny, int nz, int nbatch, int q,
                      void* out) {
   if (nx % 4 != 0) return 1;   // TMA strides must be multiples of 16 bytes
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess || !fn)
       return -1;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
@@ -1124,12 +1175,13 @@ int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  if (!one(&m.g, g, Q) || !one(&m.j, mom, 3) || !one(&m.h, hist, NH)) return -1;
+  if (!one(&m.g, g, q) || !one(&m.j, mom, 3) || !one(&m.h, hist, NH)) return -1;
   memcpy(out, &m, sizeof m);
   return 0;
 }
 
-cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s, const void* maps) {
+template <int QL>
+cudaError_t launch_step_q(const StepArgs& a, int nbatch, bool observe, cudaStream_t s, const void* maps) {
   cudaError_t e = cudaSuccess;
   const int ntx = (a.nx + TX - 1) / TX;
   const int nstrips = (a.nz + a.strip - 1) / a.strip;
@@ -1137,31 +1189,35 @@ cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaS
   if (maps) {
     TmaMaps m;
     memcpy(&m, maps, sizeof m);
-    const size_t smem = sizeof(PipeSmem3);
+    const size_t smem = sizeof(PipeSmem3<QL>);
     static bool configured = false;
     if (!configured) {
-      e = cudaFuncSetAttribute(d3q19_step_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(d3q19_step_pipe<QL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(d3q19_step_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(d3q19_step_pipe<QL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       configured = true;
     }
-    if (observe) d3q19_step_pipe<true><<<grid, NT, smem, s>>>(a, m);
-    else d3q19_step_pipe<false><<<grid, NT, smem, s>>>(a, m);
+    if (observe) d3q19_step_pipe<QL, true><<<grid, NT, smem, s>>>(a, m);
+    else d3q19_step_pipe<QL, false><<<grid, NT, smem, s>>>(a, m);
     return cudaGetLastError();
   }
   const size_t smem = sizeof(StepSmem3);
   static bool configured = false;   // attribute set once per process (both variants)
   if (!configured) {
-    e = cudaFuncSetAttribute(d3q19_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(d3q19_step<QL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(d3q19_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(d3q19_step<QL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  if (observe) d3q19_step<true><<<grid, NT, smem, s>>>(a);
-  else d3q19_step<false><<<grid, NT, smem, s>>>(a);
+  if (observe) d3q19_step<QL, true><<<grid, NT, smem, s>>>(a);
+  else d3q19_step<QL, false><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s, const void* maps) {
+  return a.q == 15 ? launch_step_q<15>(a, nbatch, observe, s, maps) : launch_step_q<19>(a, nbatch, observe, s, maps);
 }
 
 }  // namespace lbm

@@ -58,6 +58,7 @@ struct StepArgs {
   int depth;              // rows of asynchronous copies kept in flight (1..3)
   long long nodes;        // nodes per instance
   int g_half;             // NS populations stored as FP16 (D2Q9)
+  int q;                  // lattice directions (9, 15 or 19)
 };
 
 // Kernel launchers (return cudaGetLastError of the launch).
@@ -71,9 +72,10 @@ cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaSt
 cudaError_t launch_d2q9_items(const StepArgs* args, const int4* items, int nitems, int depth, int g_half, int grid,
                               bool observe, cudaStream_t s);
 
+// 3D lattices (D3Q19, D3Q15 by q) share these launchers.
 cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, float* g,
                               float* hist, const InstanceConsts* consts, int nx, int ny, int nz,
-                              int per_x, int per_y, int per_z, int nbatch, cudaStream_t s);
+                              int per_x, int per_y, int per_z, int nbatch, int q, cudaStream_t s);
 // D3Q19 steps are two launches: the moment pass, then the fused kernel.
 cudaError_t launch_d3q19_moments(const StepArgs& a, int nbatch, cudaStream_t s);
 // maps: tensor maps of the buffers the step reads (from build_d3q19_maps), or
@@ -84,7 +86,7 @@ cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaS
 // -1 on a driver error.  out receives d3q19_maps_bytes() bytes and must be
 // 64-byte aligned.
 size_t d3q19_maps_bytes();
-int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx, int ny, int nz, int nbatch,
+int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx, int ny, int nz, int nbatch, int q,
                      void* out);
 
 // Observables: deterministic two-pass reduction of one instance.

@@ -34,7 +34,7 @@ def gpu_run(L, lattice, phi0, phi1, prm: dict, periodic, steps, strip=None):
         per = (periodic[0], periodic[1], False)
     else:
         nz, ny, nx = shape
-        lat = L.LBM_D3Q19
+        lat = L.LBM_D3Q19 if lattice == "D3Q19" else L.LBM_D3Q15
         per = tuple(periodic)
     ctx = L.Context(lat, nx, ny, nz, periodic=per, params=L.lbm_default_params(**prm))
     if strip is not None:
