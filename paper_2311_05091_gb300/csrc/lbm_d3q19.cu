@@ -97,17 +97,21 @@ __host__ __device__ constexpr int LOPP(int i) {
   return i == 0 ? 0 : (i < 7 || QL == 19) ? ((i & 1) ? i + 1 : i - 1) : 21 - i;
 }
 
+// Index i, a few nodes outside [0, n) at most, folded back: periodic wrap, or
+// the mirror ghost across the half-way wall (bounded loops, no division).
 __device__ __forceinline__ int wrap_or_mirror(int i, int n, int per) {
   if (per) {
-    i %= n;
-    return i < 0 ? i + n : i;
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
   }
-  if (i < 0) return -1 - i;          // mirror ghost across the half-way wall
+  if (i < 0) return -1 - i;
   if (i >= n) return 2 * n - 1 - i;
   return i;
 }
 
-__device__ __forceinline__ int ring(int r, int n) { return ((r % n) + n) % n; }
+// slot of logical plane r in a ring of n slots (r >= -8 n)
+__device__ __forceinline__ int ring(int r, int n) { return (r + 8 * n) % n; }
 
 // value of a ring-stored field at x + c_d: planes pm (z-1), p0 (z), pp (z+1), row stride sw
 __device__ __forceinline__ float nb(const float* pm, const float* p0, const float* pp, int i, int sw, int d) {
