@@ -34,21 +34,17 @@ constexpr int RP = 5;     // ring depth of phi0 / phi1 rows
 constexpr int RM = 3;     // ring depth of mubar / history rows
 constexpr float kOneMinusPhi0Floor = 5.9604644775390625e-8f;  // 2^-24
 
-// Index i, a few nodes outside [0, n) at most, folded back: periodic wrap, or
-// the mirror ghost across the half-way wall (bounded loops, no division).
 __device__ __forceinline__ int wrap_or_mirror(int i, int n, int per) {
   if (per) {
-    while (i < 0) i += n;
-    while (i >= n) i -= n;
-    return i;
+    i %= n;
+    return i < 0 ? i + n : i;
   }
-  if (i < 0) return -1 - i;
+  if (i < 0) return -1 - i;          // mirror ghost across the half-way wall
   if (i >= n) return 2 * n - 1 - i;
   return i;
 }
 
-// slot of logical row r in a ring of n slots (r >= -8 n; n is a compile-time constant at every use)
-__device__ __forceinline__ int ring(int r, int n) { return (r + 8 * n) % n; }
+__device__ __forceinline__ int ring(int r, int n) { return ((r % n) + n) % n; }
 
 // 3x3 neighbourhood: centre, axis (e, n, w, s) and diagonal (ne, nw, sw, se).
 struct P9 {
@@ -291,6 +287,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
   auto src_plane = [&](int arr) -> const float* {
     return arr < 9 ? f_in + arr * plane : (arr == 9 ? p0_in : h_in + (arr - 10) * plane);
   };
+  // destination row of float array arr in the slots of rows ra (f, phi0), rh (history)
+  auto dst_row = [&](int arr, int ra, int rh) -> float* {
+    return arr < 10 ? S.a[ring(ra, D + 1)].rows[arr] : S.h[ring(rh, D + 2)].rows[arr - 10];
+  };
 
   const bool vec16 = (nx & 3) == 0;
   const int x = x0 + t;
@@ -318,44 +318,6 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
   const int h_px = wrap_or_mirror(h_xl, nx, per_x);
   const float* __restrict__ h_src = h_arr >= 0 ? src_plane(h_arr) : f_in;
 
-  // This thread's 16-byte chunks of every staged row, fixed for the sweep:
-  // float chunk m is array (t >> 5) + 4 m (f, phi0: A slot; history: H slot;
-  // g: G slot), columns x0 + 4 (t & 31) .. + 3; FP16 g chunk m is array
-  // (t + 128 m) >> 4, columns x0 + 8 ((t + 128 m) & 15) .. + 7.
-  constexpr int GP = gpad<GT>(), GW = BX + 2 * GP;
-  const int cj = t & 31;
-  const int xc = x0 + 4 * cj;
-  const float* c_src[6];
-  int c_dst[6], c_kind[6];   // kind 0 A, 1 H, 2 G, -1 none
-#pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    const int arr = (t >> 5) + 4 * m;
-    c_kind[m] = -1;
-    c_src[m] = f_in;
-    c_dst[m] = 0;
-    if (!vec16 || xc >= nx) continue;
-    if (arr < 15) {
-      c_kind[m] = arr < 10 ? 0 : 1;
-      c_src[m] = src_plane(arr) + xc;
-      c_dst[m] = (arr < 10 ? arr : arr - 10) * W + PAD + 4 * cj;
-    } else if (!kHalf) {
-      c_kind[m] = 2;
-      c_src[m] = reinterpret_cast<const float*>(g_in + (arr - 15) * plane + xc);
-      c_dst[m] = ((arr - 15) * GW + GP + 4 * cj) * (int)sizeof(GT) / 4;
-    }
-  }
-  const float* h16_src[2];
-  int h16_dst[2];
-  bool h16_on[2];
-#pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    const int id = t + BX * m;
-    const int arr = id >> 4, xh = x0 + 8 * (id & 15);
-    h16_on[m] = kHalf && vec16 && id < 144 && xh < nx;
-    h16_src[m] = reinterpret_cast<const float*>(g_in + (h16_on[m] ? arr * plane + xh : 0));
-    h16_dst[m] = (arr * GW + GP + 8 * (id & 15)) * (int)sizeof(GT) / 4;
-  }
-
   // The copies issued for iteration target q: f / phi0 of row q+2, history of
   // row q+1, g of row q -- each only where a later stage reads it.
   auto issue = [&](int q) {
@@ -366,35 +328,54 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
     const int ba = wrap_or_mirror(ra, ny, per_y) * nx;
     const int bh = wrap_or_mirror(rh, ny, per_y) * nx;
     const int bg = wrap_or_mirror(rg, ny, per_y) * nx;
-    float* const sa = S.a[ring(ra, D + 1)].rows[0];
-    float* const sh = S.h[ring(rh, D + 2)].rows[0];
-    float* const sg = reinterpret_cast<float*>(S.g[ring(rg, D + 1)].rows[0]);
+    auto need = [&](int arr) { return arr < 10 ? need_a : need_h; };
+    auto rowb = [&](int arr) { return arr < 10 ? ba : bh; };
+    GT* const grow = S.g[ring(rg, D + 1)].rows[0];
+    constexpr int GP = gpad<GT>(), GW = BX + 2 * GP;
     if (vec16) {
+      // float chunk m of this thread: array (t >> 5) + 4 m, columns x0 + 4 (t & 31) .. + 3
+      const int j = t & 31;
+      const int xc = x0 + 4 * j;
+      if (xc < nx) {
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        const int kd = c_kind[m];
-        const bool on = kd == 0 ? need_a : (kd == 1 ? need_h : (kd == 2 && need_g));
-        if (on)
-          cp_async16((kd == 0 ? sa : (kd == 1 ? sh : sg)) + c_dst[m], c_src[m] + (kd == 0 ? ba : (kd == 1 ? bh : bg)));
+        for (int m = 0; m < 4; ++m) {
+          const int arr = (t >> 5) + 4 * m;
+          if (arr < 15 && need(arr)) cp_async16(dst_row(arr, ra, rh) + PAD + 4 * j, src_plane(arr) + rowb(arr) + xc);
+        }
       }
-      if (kHalf && need_g) {
+      if (need_g) {
+        if (!kHalf) {
 #pragma unroll
-        for (int m = 0; m < 2; ++m)
-          if (h16_on[m]) cp_async16(sg + h16_dst[m], h16_src[m] + bg / 2);
+          for (int m = 3; m < 6; ++m) {
+            const int arr = (t >> 5) + 4 * m;
+            if (arr >= 15 && xc < nx)
+              cp_async16(reinterpret_cast<float*>(grow + (arr - 15) * GW + GP + 4 * j),
+                         reinterpret_cast<const float*>(g_in + (arr - 15) * plane + bg + xc));
+          }
+        } else {
+          // FP16 rows: 16 chunks of eight columns per array, 144 chunks on 128 threads
+#pragma unroll
+          for (int m = 0; m < 2; ++m) {
+            const int id = t + BX * m;
+            const int arr = id >> 4, xh = x0 + 8 * (id & 15);
+            if (id < 144 && xh < nx)
+              cp_async16(reinterpret_cast<float*>(grow + arr * GW + GP + 8 * (id & 15)),
+                         reinterpret_cast<const float*>(g_in + arr * plane + bg + xh));
+          }
+        }
       }
     } else if (x < nx) {
-      auto dst_row = [&](int arr) { return arr < 10 ? sa + arr * W : sh + (arr - 10) * W; };
 #pragma unroll
       for (int arr = 0; arr < 15; ++arr)
-        if (arr < 10 ? need_a : need_h) cp_async4(dst_row(arr) + PAD + t, src_plane(arr) + (arr < 10 ? ba : bh) + x);
+        if (need(arr)) cp_async4(dst_row(arr, ra, rh) + PAD + t, src_plane(arr) + rowb(arr) + x);
       if (need_g && !kHalf) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-          cp_async4(sg + i * GW + GP + t, reinterpret_cast<const float*>(g_in + i * plane + bg + x));
+          cp_async4(reinterpret_cast<float*>(grow + i * GW + GP + t),
+                    reinterpret_cast<const float*>(g_in + i * plane + bg + x));
       }
     }
-    if (h_active && (h_arr < 10 ? need_a : need_h))
-      cp_async4((h_arr < 10 ? sa + h_arr * W : sh + (h_arr - 10) * W) + h_col, h_src + (h_arr < 10 ? ba : bh) + h_px);
+    if (h_active && need(h_arr)) cp_async4(dst_row(h_arr, ra, rh) + h_col, h_src + rowb(h_arr) + h_px);
     cp_commit();   // empty groups keep the group count uniform
   };
 
