@@ -474,11 +474,11 @@ def run_gpu(args):
     spec = dict(WORKLOADS[args.workload])
     flags = 0
     if args.g_f16:
-        if spec["lattice"] != "D2Q9":
-            raise SystemExit("--g-f16 is built for the D2Q9 workload")
         flags = L.LBM_STORE_G_F16
-        # NS populations 2 bytes: f, g read + write 72 + 36; phi0 4; history 40
-        spec.update(bytes_per_lu=152, kernel_bytes_per_lu=152, profile="d2q9_step_f16_disk1024x5.md")
+        # NS populations in 2 bytes: their read + write halves
+        q = {"D2Q9": 9, "D3Q19": 19, "D3Q15": 15}[spec["lattice"]]
+        spec.update(bytes_per_lu=spec["bytes_per_lu"] - 4 * q, kernel_bytes_per_lu=spec["kernel_bytes_per_lu"] - 4 * q,
+                    profile=spec["profile"].replace("_step_", "_step_f16_"))
     wl = make_workload(args.workload, args.size)
     nb = len(wl["params"])
     nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]

@@ -145,9 +145,10 @@ enum {
   /* NS populations g stored in HBM as IEEE FP16 holding g * 2^12 (the rest
    * population already shifted by rho_0), arithmetic in float32; the CH
    * populations stay float32, so the conserved phase field keeps float32
-   * rounding.  D2Q9 only, nx % 8 == 0 (LBM_EUNSUPPORTED / LBM_EINVAL
-   * otherwise).  Relative storage error 2^-11 per value per step; no pattern
-   * of the paper, a bandwidth option: 188 -> 152 bytes per lattice update. */
+   * rounding.  Every lattice, nx % 8 == 0 (LBM_EINVAL otherwise).  Relative
+   * storage error 2^-11 per value per step; no pattern of the paper, a
+   * bandwidth option: bytes per lattice update 188 -> 152 (D2Q9),
+   * 364 -> 288 (D3Q19), 300 -> 240 (D3Q15). */
   LBM_STORE_G_F16 = 1
 };
 

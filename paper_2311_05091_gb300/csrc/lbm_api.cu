@@ -499,7 +499,6 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
   const int g_half = (flags & LBM_STORE_G_F16) ? 1 : 0;
   const bool is3d = lattice != LBM_D2Q9;
   const int q = lattice == LBM_D3Q19 ? 19 : (lattice == LBM_D3Q15 ? 15 : 9);
-  if (g_half && is3d) return set_err(nullptr, LBM_EUNSUPPORTED, "FP16 population storage is built for D2Q9 only");
   if (multi && is3d) return set_err(nullptr, LBM_EUNSUPPORTED, "instances of different sizes are built for D2Q9 only");
   if (!is3d && nz != 1) return set_err(nullptr, LBM_EINVAL, "D2Q9 needs nz = 1");
   const int per[3] = {(periodic_mask & LBM_PERIODIC_X) ? 1 : 0, (periodic_mask & LBM_PERIODIC_Y) ? 1 : 0,
@@ -590,8 +589,7 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
   if (e == cudaSuccess && is3d && lbm::d3q19_maps_bytes() <= sizeof(c->d3maps[0])) {
     int r = 0;
     for (int i = 0; i < 2 && r == 0; ++i)
-      r = lbm::build_d3q19_maps(static_cast<float*>(c->g[i]), c->mom, c->hist[i], nx, ny, nz, nbatch, q,
-                                c->d3maps[i]);
+      r = lbm::build_d3q19_maps(c->g[i], g_half, c->mom, c->hist[i], nx, ny, nz, nbatch, q, c->d3maps[i]);
     if (r < 0) e = cudaErrorInvalidValue;   // the driver refused a tensor map
     c->d3maps_ok = r == 0;
   }
@@ -816,7 +814,7 @@ static int set_phase_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
                               c->nx,
                               c->ny, c->per[0], c->per[1], c->nbatch, c->stream);
   else
-    e = lbm::launch_d3q19_init(c->phi0, stage, c->f[c->cur], static_cast<float*>(c->g[c->cur]), c->hist[c->cur],
+    e = lbm::launch_d3q19_init(c->phi0, stage, c->f[c->cur], c->g[c->cur], c->g_half, c->hist[c->cur],
                                c->dconsts, c->nx,
                                c->ny, c->nz, c->per[0], c->per[1], c->per[2], c->nbatch, c->q, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");

@@ -38,10 +38,12 @@
 //
 // The NS rest population is stored minus the constant rho_0 of lambda_0.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "lbm_internal.cuh"
 
@@ -201,13 +203,21 @@ __device__ __forceinline__ float weight(const InstanceConsts& k, int i) {
   return i == 0 ? k.w0 : (i < 7 ? k.wa : k.we);
 }
 
+// NS population storage: float32, or FP16 holding g * gsc (gsc a power of two)
+__device__ __forceinline__ float g_load(float v, const InstanceConsts&) { return v; }
+__device__ __forceinline__ float g_load(__half v, const InstanceConsts& k) { return __half2float(v) * k.gsci; }
+__device__ __forceinline__ void g_store(float* p, float v, const InstanceConsts&) { *p = v; }
+__device__ __forceinline__ void g_store(__half* p, float v, const InstanceConsts& k) {
+  *p = __float2half_rn(v * k.gsc);
+}
+
 // ---------------------------------------------------------------------------
 // initial state: f = f^eq(phi1, mubar_1, u = 0), g = g^eq(p = 0, u = 0) - rho_0 e_0 = 0,
 // history = (phi1, 0, ..., 0).  phi1 arrives staged in plane 0 of a spare history buffer.
 // ---------------------------------------------------------------------------
-template <int QL>
+template <int QL, typename GT>
 __global__ void d3q19_init(const float* __restrict__ phi0_all, const float* __restrict__ phi1_all,
-                           float* __restrict__ f_all, float* __restrict__ g_all, float* __restrict__ hist_all,
+                           float* __restrict__ f_all, GT* __restrict__ g_all, float* __restrict__ hist_all,
                            const InstanceConsts* __restrict__ consts, int nx, int ny, int nz, int per_x,
                            int per_y, int per_z, int nbatch) {
   const long long nodes = (long long)nx * ny * nz;
@@ -245,13 +255,13 @@ __global__ void d3q19_init(const float* __restrict__ phi0_all, const float* __re
     chem_pot(k, c0, c1, lap0, lap1, mu0, mu1, mu2);
     const float emb = k.eta * mubar1_of(k, mu0, mu1, mu2);
     float* f = f_all + (long long)b * QL * nodes;
-    float* g = g_all + (long long)b * QL * nodes;
+    GT* g = g_all + (long long)b * QL * nodes;
     float* h = hist_all + (long long)b * NH * nodes;
     f[node] = c1 + (k.w0 - 1.f) * emb;
 #pragma unroll
     for (int i = 1; i < QL; ++i) f[(long long)i * nodes + node] = (i < 7 ? k.wa : k.we) * emb;
 #pragma unroll
-    for (int i = 0; i < QL; ++i) g[(long long)i * nodes + node] = 0.f;
+    for (int i = 0; i < QL; ++i) g[(long long)i * nodes + node] = GT(0.f);
     h[node] = c1;
 #pragma unroll
     for (int q = 1; q < NH; ++q) h[(long long)q * nodes + node] = 0.f;
@@ -351,14 +361,14 @@ struct Rings {
 struct Outs {
   const float* f_in;   // instance base, read by the general CH path
   float* f_out;
-  float* g_out;
+  void* g_out;            // float, or FP16 scaled by gsc
   float* h_out;
   float* p_out;
   unsigned int* flag;
   int nx, ny, nz, per_x, per_y, per_z, nodes, plane;
 };
 
-template <int QL, bool OBS>
+template <int QL, bool OBS, typename GT>
 __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings& R, const OwnIn<QL>& in,
                                             const Outs& o, int x, int y, int z) {
   const int nx = o.nx, ny = o.ny, nz = o.nz, nodes = o.nodes, plane = o.plane;
@@ -495,14 +505,14 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
   const int oxp = x + 1 < nx ? 1 : 1 - nx, oxm = x > 0 ? -1 : nx - 1;
   const int oyp = y + 1 < ny ? nx : nx - plane, oym = y > 0 ? -nx : plane - nx;
   const int ozp = z + 1 < nz ? plane : plane - nodes, ozm = z > 0 ? -plane : nodes - plane;
-  auto store = [&](float* __restrict__ out, int i, float v) {
+  auto store = [&](auto* __restrict__ out, int i, float v) {
     const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
     int off = 0;
     bool bb = false;
     if (cx) { off += cx > 0 ? oxp : oxm; bb = bb || (cx > 0 ? wxp : wxm); }
     if (cy) { off += cy > 0 ? oyp : oym; bb = bb || (cy > 0 ? wyp : wym); }
     if (cz) { off += cz > 0 ? ozp : ozm; bb = bb || (cz > 0 ? wzp : wzm); }
-    out[bb ? LOPP<QL>(i) * nodes + node : i * nodes + node + off] = v;
+    g_store(out + (bb ? LOPP<QL>(i) * nodes + node : i * nodes + node + off), v, k);
   };
 
   // ---- NS collision: g* = (1 - s2a) g + w_i X_i (see the file header) ----
@@ -550,7 +560,8 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
     const float Py = k3 * Ty + Uy, Qy = k3 * Ty - Uy;
     const float Pz = k3 * Tz + Uz, Qz = k3 * Tz - Uz;
     const float om1 = 1.f - s2a;
-    store(o.g_out, 0, om1 * g[0] + k.w0 * base - s2a * p * ic2);
+    GT* const g_out = static_cast<GT*>(o.g_out);
+    store(g_out, 0, om1 * g[0] + k.w0 * base - s2a * p * ic2);
 #pragma unroll
     for (int i = 1; i < QL; ++i) {
       const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
@@ -576,7 +587,7 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
         const float ct = (cx > 0 ? Tx : -Tx) + (cy > 0 ? Ty : -Ty) + (cz > 0 ? Tz : -Tz);
         X -= k3 * ct + (cx * cy * cz > 0 ? Ux : -Ux);
       }
-      store(o.g_out, i, om1 * g[i] + weight(k, i) * X);
+      store(g_out, i, om1 * g[i] + weight(k, i) * X);
     }
   }
 
@@ -705,7 +716,7 @@ struct StepSmem3 {
   InstanceConsts k;
 };
 
-template <int QL, bool OBS>
+template <int QL, bool OBS, typename GT>
 __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   StepSmem3& S = *reinterpret_cast<StepSmem3*>(smem_raw);
@@ -726,7 +737,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   if (t < (int)(sizeof(InstanceConsts) / 4))
     reinterpret_cast<float*>(&S.k)[t] = reinterpret_cast<const float*>(a.consts + b)[t];
 
-  const float* __restrict__ g_in = static_cast<const float*>(a.g_in) + (long long)b * QL * nodes;
+  const GT* __restrict__ g_in = static_cast<const GT*>(a.g_in) + (long long)b * QL * nodes;
   const float* __restrict__ p0_in = a.phi0 + (long long)b * nodes;
   const float* __restrict__ h_in = a.hist_in + (long long)b * NH * nodes;
   const float* __restrict__ phi1_now = a.hist_out + (long long)b * NH * nodes;   // moment pass of this step
@@ -734,7 +745,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
   Outs o;
   o.f_in = a.f_in + (long long)b * QL * nodes;
   o.f_out = a.f_out + (long long)b * QL * nodes;
-  o.g_out = static_cast<float*>(a.g_out) + (long long)b * QL * nodes;
+  o.g_out = static_cast<GT*>(a.g_out) + (long long)b * QL * nodes;
   o.h_out = a.hist_out + (long long)b * NH * nodes;
   o.p_out = a.p_out + (long long)b * nodes;
   o.flag = a.flag;
@@ -806,7 +817,10 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
     const int node = z * plane + y * nx + x;
     OwnIn<QL> in;
 #pragma unroll
-    for (int i = 0; i < QL; ++i) in.g[i] = __ldcs(g_in + i * nodes + node);
+    for (int i = 0; i < QL; ++i) {
+      if constexpr (std::is_same<GT, float>::value) in.g[i] = __ldcs(g_in + i * nodes + node);
+      else in.g[i] = g_load(g_in[i * nodes + node], k);
+    }
     in.jx = j_in[node];
     in.jy = j_in[nodes + node];
     in.jz = j_in[2 * nodes + node];
@@ -832,7 +846,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
     R.sw2 = HX2;
     R.i1 = (ty + 1) * HX1 + (tx + 1);
     R.sw1 = HX1;
-    node_update<QL, OBS>(k, R, in, o, x, y, z);
+    node_update<QL, OBS, GT>(k, R, in, o, x, y, z);
   }
 }
 
@@ -847,17 +861,16 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
 constexpr int PW = 40;                       // halo tile row: columns x0-4 .. x0+35 (16-byte aligned chunks)
 constexpr int PR2 = TY + 4, PR1 = TY + 2;    // rows of the two-halo and one-halo tiles
 constexpr int RP5 = 5;                       // phi ring: z-1 .. z+2 in use, z+3 in flight
-template <int QL>
-__host__ __device__ constexpr int nown() { return QL + 3 + NH; }   // owned planes per z: g, j, history
 constexpr int kSpinLimit = 1 << 22;          // try_wait polls before a TMA wait gives up
 
 struct TmaMaps {
   CUtensorMap g, j, h;   // g: (nx, ny, nz, QL nb), j: (.., 3 nb), h: (.., 7 nb); boxes 32 x 8 x 1 x {QL, 3, 7}
 };
 
-template <int QL>
+template <int QL, typename GT>
 struct alignas(128) PipeSmem3 {
-  float own[nown<QL>()][NT];        // TMA destination: g 0..QL-1, j QL..QL+2, history QL+3..QL+9
+  GT gown[QL][NT];                  // TMA destinations: g of the owned columns,
+  float own[3 + NH][NT];            // then j 0-2 and history 3-9
   float phi1[RP5][PR2 * PW];
   float phi0[RP5][PR2 * PW];
   float hus[2][6][PR1 * PW];        // history u, S (planes 1-6) on the one-halo tile
@@ -898,7 +911,7 @@ __device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parit
   }
   return false;
 }
-__device__ __forceinline__ void tma_load4(float* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                           unsigned long long* bar) {
   asm volatile(
       "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
@@ -907,11 +920,11 @@ __device__ __forceinline__ void tma_load4(float* dst, const CUtensorMap* map, in
       : "memory");
 }
 
-template <int QL, bool OBS>
+template <int QL, bool OBS, typename GT>
 __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const __grid_constant__ TmaMaps maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  PipeSmem3<QL>& S = *reinterpret_cast<PipeSmem3<QL>*>(smem_raw);
-  constexpr unsigned kOwnBytes = nown<QL>() * NT * 4;
+  PipeSmem3<QL, GT>& S = *reinterpret_cast<PipeSmem3<QL, GT>*>(smem_raw);
+  constexpr unsigned kOwnBytes = QL * NT * sizeof(GT) + (3 + NH) * NT * 4;
 
   const int t = threadIdx.x;
   const int tx = t % TX, ty = t / TX;
@@ -934,7 +947,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   Outs o;
   o.f_in = a.f_in + (long long)b * QL * nodes;
   o.f_out = a.f_out + (long long)b * QL * nodes;
-  o.g_out = static_cast<float*>(a.g_out) + (long long)b * QL * nodes;
+  o.g_out = static_cast<GT*>(a.g_out) + (long long)b * QL * nodes;
   o.h_out = a.hist_out + (long long)b * NH * nodes;
   o.p_out = a.p_out + (long long)b * nodes;
   o.flag = a.flag;
@@ -1010,9 +1023,9 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   auto issue_own = [&](int z) {   // one thread
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     bar_expect(&S.bar, kOwnBytes);
-    tma_load4(S.own[0], &maps.g, x0, y0, z, b * QL, &S.bar);
-    tma_load4(S.own[QL], &maps.j, x0, y0, z, b * 3, &S.bar);
-    tma_load4(S.own[QL + 3], &maps.h, x0, y0, z, b * NH, &S.bar);
+    tma_load4(S.gown[0], &maps.g, x0, y0, z, b * QL, &S.bar);
+    tma_load4(S.own[0], &maps.j, x0, y0, z, b * 3, &S.bar);
+    tma_load4(S.own[3], &maps.h, x0, y0, z, b * NH, &S.bar);
   };
 
   const InstanceConsts& k = S.k;
@@ -1093,17 +1106,17 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
     // owned inputs of plane z into registers, then the slot takes plane z+1
     OwnIn<QL> in;
 #pragma unroll
-    for (int i = 0; i < QL; ++i) in.g[i] = S.own[i][t];
-    in.jx = S.own[QL][t];
-    in.jy = S.own[QL + 1][t];
-    in.jz = S.own[QL + 2][t];
-    in.php = S.own[QL + 3][t];
-    in.upx = S.own[QL + 4][t];
-    in.upy = S.own[QL + 5][t];
-    in.upz = S.own[QL + 6][t];
-    in.spx = S.own[QL + 7][t];
-    in.spy = S.own[QL + 8][t];
-    in.spz = S.own[QL + 9][t];
+    for (int i = 0; i < QL; ++i) in.g[i] = g_load(S.gown[i][t], k);
+    in.jx = S.own[0][t];
+    in.jy = S.own[1][t];
+    in.jz = S.own[2][t];
+    in.php = S.own[3][t];
+    in.upx = S.own[4][t];
+    in.upy = S.own[5][t];
+    in.upz = S.own[6][t];
+    in.spx = S.own[7][t];
+    in.spy = S.own[8][t];
+    in.spz = S.own[9][t];
     __syncthreads();
     if (t == 0 && z + 1 < ze) issue_own(z + 1);
     if (!own) continue;
@@ -1121,7 +1134,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
     R.sw2 = PW;
     R.i1 = (ty + 1) * HX1 + (tx + 1);
     R.sw1 = HX1;
-    node_update<QL, OBS>(k, R, in, o, x, y, z);
+    node_update<QL, OBS, GT>(k, R, in, o, x, y, z);
   }
   // leave no copy in flight: asynchronous copies, and a TMA load issued for a plane not processed
   cp_wait_all();
@@ -1130,17 +1143,22 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
 
 }  // namespace
 
-cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, float* g, float* hist,
+cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, void* g, int g_half, float* hist,
                               const InstanceConsts* consts, int nx, int ny, int nz, int per_x, int per_y,
                               int per_z, int nbatch, int q, cudaStream_t s) {
   const long long total = (long long)nx * ny * nz * nbatch;
-  const long long blocks = std::min<long long>((total + 255) / 256, 1LL << 20);
-  if (q == 15)
-    d3q19_init<15><<<(unsigned)blocks, 256, 0, s>>>(phi0, phi1, f, g, hist, consts, nx, ny, nz, per_x, per_y, per_z,
-                                                     nbatch);
-  else
-    d3q19_init<19><<<(unsigned)blocks, 256, 0, s>>>(phi0, phi1, f, g, hist, consts, nx, ny, nz, per_x, per_y, per_z,
-                                                     nbatch);
+  const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 1LL << 20);
+  auto run = [&](auto qtag, auto* gp) {
+    constexpr int QL = decltype(qtag)::value;
+    d3q19_init<QL><<<blocks, 256, 0, s>>>(phi0, phi1, f, gp, hist, consts, nx, ny, nz, per_x, per_y, per_z, nbatch);
+  };
+  if (q == 15) {
+    if (g_half) run(std::integral_constant<int, 15>(), static_cast<__half*>(g));
+    else run(std::integral_constant<int, 15>(), static_cast<float*>(g));
+  } else {
+    if (g_half) run(std::integral_constant<int, 19>(), static_cast<__half*>(g));
+    else run(std::integral_constant<int, 19>(), static_cast<float*>(g));
+  }
   return cudaGetLastError();
 }
 
@@ -1157,9 +1175,9 @@ cudaError_t launch_d3q19_moments(const StepArgs& a, int nbatch, cudaStream_t s) 
 
 size_t d3q19_maps_bytes() { return sizeof(TmaMaps); }
 
-int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx, int ny, int nz, int nbatch, int q,
-                     void* out) {
-  if (nx % 4 != 0) return 1;   // TMA strides must be multiples of 16 bytes
+int build_d3q19_maps(const void* g, int g_half, const float* mom, const float* hist, int nx, int ny, int nz,
+                     int nbatch, int q, void* out) {
+  if (nx % (g_half ? 8 : 4) != 0) return 1;   // TMA strides must be multiples of 16 bytes
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -1170,21 +1188,23 @@ int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   TmaMaps m;
-  auto one = [&](CUtensorMap* map, const float* base, int planes) {
+  auto one = [&](CUtensorMap* map, const void* base, int planes, bool half) {
+    const cuuint64_t es = half ? 2 : 4;
     const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)planes * nbatch};
-    const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nz * 4};
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
     const cuuint32_t box[4] = {TX, TY, 1, (cuuint32_t)planes};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    return encode(map, half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                  const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  if (!one(&m.g, g, q) || !one(&m.j, mom, 3) || !one(&m.h, hist, NH)) return -1;
+  if (!one(&m.g, g, q, g_half != 0) || !one(&m.j, mom, 3, false) || !one(&m.h, hist, NH, false)) return -1;
   memcpy(out, &m, sizeof m);
   return 0;
 }
 
-template <int QL>
+template <int QL, typename GT>
 cudaError_t launch_step_q(const StepArgs& a, int nbatch, bool observe, cudaStream_t s, const void* maps) {
   cudaError_t e = cudaSuccess;
   const int ntx = (a.nx + TX - 1) / TX;
@@ -1193,35 +1213,40 @@ cudaError_t launch_step_q(const StepArgs& a, int nbatch, bool observe, cudaStrea
   if (maps) {
     TmaMaps m;
     memcpy(&m, maps, sizeof m);
-    const size_t smem = sizeof(PipeSmem3<QL>);
+    const size_t smem = sizeof(PipeSmem3<QL, GT>);
     static bool configured = false;
     if (!configured) {
-      e = cudaFuncSetAttribute(d3q19_step_pipe<QL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(d3q19_step_pipe<QL, true, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(d3q19_step_pipe<QL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(d3q19_step_pipe<QL, false, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
       if (e != cudaSuccess) return e;
       configured = true;
     }
-    if (observe) d3q19_step_pipe<QL, true><<<grid, NT, smem, s>>>(a, m);
-    else d3q19_step_pipe<QL, false><<<grid, NT, smem, s>>>(a, m);
+    if (observe) d3q19_step_pipe<QL, true, GT><<<grid, NT, smem, s>>>(a, m);
+    else d3q19_step_pipe<QL, false, GT><<<grid, NT, smem, s>>>(a, m);
     return cudaGetLastError();
   }
   const size_t smem = sizeof(StepSmem3);
   static bool configured = false;   // attribute set once per process (both variants)
   if (!configured) {
-    e = cudaFuncSetAttribute(d3q19_step<QL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(d3q19_step<QL, true, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(d3q19_step<QL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(d3q19_step<QL, false, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  if (observe) d3q19_step<QL, true><<<grid, NT, smem, s>>>(a);
-  else d3q19_step<QL, false><<<grid, NT, smem, s>>>(a);
+  if (observe) d3q19_step<QL, true, GT><<<grid, NT, smem, s>>>(a);
+  else d3q19_step<QL, false, GT><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s, const void* maps) {
-  return a.q == 15 ? launch_step_q<15>(a, nbatch, observe, s, maps) : launch_step_q<19>(a, nbatch, observe, s, maps);
+  if (a.q == 15)
+    return a.g_half ? launch_step_q<15, __half>(a, nbatch, observe, s, maps)
+                    : launch_step_q<15, float>(a, nbatch, observe, s, maps);
+  return a.g_half ? launch_step_q<19, __half>(a, nbatch, observe, s, maps)
+                  : launch_step_q<19, float>(a, nbatch, observe, s, maps);
 }
 
 }  // namespace lbm

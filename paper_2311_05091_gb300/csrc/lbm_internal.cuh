@@ -57,7 +57,7 @@ struct StepArgs {
   int strip;              // rows (2D) or planes (3D) per CTA
   int depth;              // rows of asynchronous copies kept in flight (1..3)
   long long nodes;        // nodes per instance
-  int g_half;             // NS populations stored as FP16 (D2Q9)
+  int g_half;             // NS populations stored as FP16
   int q;                  // lattice directions (9, 15 or 19)
 };
 
@@ -73,7 +73,7 @@ cudaError_t launch_d2q9_items(const StepArgs* args, const int4* items, int nitem
                               bool observe, cudaStream_t s);
 
 // 3D lattices (D3Q19, D3Q15 by q) share these launchers.
-cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, float* g,
+cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, void* g, int g_half,
                               float* hist, const InstanceConsts* consts, int nx, int ny, int nz,
                               int per_x, int per_y, int per_z, int nbatch, int q, cudaStream_t s);
 // D3Q19 steps are two launches: the moment pass, then the fused kernel.
@@ -82,12 +82,12 @@ cudaError_t launch_d3q19_moments(const StepArgs& a, int nbatch, cudaStream_t s);
 // nullptr for the generic kernel (any nx)
 cudaError_t launch_d3q19_step(const StepArgs& a, int nbatch, bool observe, cudaStream_t s, const void* maps);
 // Tensor maps of one set of input buffers (g, j scratch, history) for the
-// pipelined D3Q19 kernel: 0 on success, 1 if nx % 4 != 0 (not supported),
+// pipelined 3D kernel: 0 on success, 1 if nx % 4 (FP16 g: 8) != 0 (not supported),
 // -1 on a driver error.  out receives d3q19_maps_bytes() bytes and must be
 // 64-byte aligned.
 size_t d3q19_maps_bytes();
-int build_d3q19_maps(const float* g, const float* mom, const float* hist, int nx, int ny, int nz, int nbatch, int q,
-                     void* out);
+int build_d3q19_maps(const void* g, int g_half, const float* mom, const float* hist, int nx, int ny, int nz,
+                     int nbatch, int q, void* out);
 
 // Observables: deterministic two-pass reduction of one instance.
 //   phi0, phi1, u (d planes), p: device fields of one instance, n nodes.

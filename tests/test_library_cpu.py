@@ -70,8 +70,11 @@ def test_storage_options_validated_on_the_host(lbm_lib):
     L = lbm_lib
     p = [L.lbm_default_params()]
     with pytest.raises(L.LbmError) as e:
-        L.lbm_create_ex(L.LBM_D3Q19, 16, 16, 16, 7, p, L.LBM_STORE_G_F16)
-    assert e.value.status == -7          # FP16 storage is built for D2Q9 only
+        L.lbm_create_ex(L.LBM_D3Q19, 20, 16, 16, 7, p, L.LBM_STORE_G_F16)
+    assert e.value.status == -1          # nx % 8 != 0 (3D)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_create_multi(L.LBM_D3Q19, [(16, 16), (32, 16)], 3, p * 2)
+    assert e.value.status == -7          # instances of different sizes: D2Q9 only
     with pytest.raises(L.LbmError) as e:
         L.lbm_create_ex(L.LBM_D2Q9, 20, 16, 1, 3, p, L.LBM_STORE_G_F16)
     assert e.value.status == -1          # nx % 8 != 0
