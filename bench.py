@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=60.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS) + ["warmstart256"])
     ap.add_argument("--size", type=int, default=None, help="lattice side (default: the workload's)")
     ap.add_argument("--g-f16", action="store_true",
                     help="store the NS populations as FP16 (D2Q9; float32 arithmetic and CH populations)")
@@ -83,6 +83,14 @@ def parse():
     ap.add_argument("--tte-steps", type=int, default=150000,
                     help="steps of the time-to-equilibrium run (disk workload; 0 skips it)")
     ap.add_argument("--tte-every", type=int, default=2500, help="contact-angle sampling interval")
+    ap.add_argument("--ws-train", type=int, default=2000, help="warm start: training samples")
+    ap.add_argument("--ws-eval", type=int, default=200, help="warm start: held-out samples")
+    ap.add_argument("--ws-iters", type=int, default=3000, help="warm start: training iterations")
+    ap.add_argument("--ws-batch", type=int, default=16, help="warm start: images per training iteration")
+    ap.add_argument("--ws-label-steps", type=int, default=20000, help="warm start: plain steps of the labels")
+    ap.add_argument("--ws-relax-steps", type=int, default=2000, help="warm start: relaxation steps after inference")
+    ap.add_argument("--ws-every", type=int, default=250, help="warm start: contact-angle sampling interval")
+    ap.add_argument("--ws-lr", type=float, default=2e-3)
     return ap.parse_args()
 
 
@@ -607,10 +615,183 @@ def run_gpu(args):
     return 0
 
 
+def _ws_context(L, s, lo, hi, stream):
+    n = s["n"]
+    ctx = L.Context(L.LBM_D2Q9, n, n, 1, periodic=(True, True, False),
+                    batch=[L.lbm_default_params(**p) for p in s["params"][lo:hi]])
+    ctx.set_stream(stream.cuda_stream)
+    ctx.set_solid(s["phi0"][lo:hi])
+    return ctx
+
+
+def _ws_theta(L, ctx, s, lo, i):
+    cx, cy, Rs = s["disk"][lo + i]
+    try:
+        return ctx.contact_angle(i, 1, int(round(cx)), float(cy), float(Rs))[0]
+    except L.LbmError:
+        return float("nan")
+
+
+def run_warmstart(args):
+    """Learned warm start (not in the paper), measured end to end on one GPU.
+
+    Labels: the plain method run for ``ws_label_steps`` steps on training
+    samples of the batched distribution at 256^2 (synthetic.workloads.
+    warmstart_set).  Training: the U-Net of paper_2311_05091_gb300.warmstart
+    on those labels, every forward and backward operation in the library's
+    BF16 tensor-core kernels.  Evaluation on held-out seeds: each sample runs
+    the plain method from its initial field for ws_label_steps steps (the
+    reference, theta sampled every ws_every steps) and, separately, from the
+    warm-start field for ws_relax_steps steps.  Reported: relative L2 error of
+    c against the reference for the initial field, the plain run after
+    ws_relax_steps, the warm-start field and the warm start after
+    ws_relax_steps; the same for the contact angle; the steps (and time) each
+    form needs to come within 0.5 deg of the reference angle.
+    """
+    import numpy as np
+    import torch
+    from paper_2311_05091_gb300 import _lbm as L
+    from paper_2311_05091_gb300.warmstart import WarmStartNet, fit, predict_all
+    from synthetic.workloads import warmstart_set
+    n = args.size or 256
+    T, K, every, B = args.ws_label_steps, args.ws_relax_steps, args.ws_every, args.ws_batch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    L.library()
+    t0 = time.time()
+    train = warmstart_set(range(100000, 100000 + args.ws_train), n)
+    ev = warmstart_set(range(200000, 200000 + args.ws_eval), n)
+    log(f"warm start: samples generated in {time.time() - t0:.1f} s")
+    # -- labels ---------------------------------------------------------------------------
+    t0 = time.time()
+    target = np.empty_like(train["phi1"])
+    chunk = 500
+    for lo in range(0, args.ws_train, chunk):
+        hi = min(args.ws_train, lo + chunk)
+        ctx = _ws_context(L, train, lo, hi, stream)
+        try:
+            ctx.set_phase(train["phi1"][lo:hi])
+            ctx.step(T)
+            target[lo:hi] = ctx.get_fields()[0].reshape(hi - lo, n, n)
+        finally:
+            ctx.close()
+    label_s = time.time() - t0
+    bad = ~np.isfinite(target).all(axis=(1, 2))
+    log(f"warm start: {args.ws_train} labels x {T} steps in {label_s:.1f} s ({int(bad.sum())} non-finite)")
+    keep = np.flatnonzero(~bad)
+    todev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    p0, p1, tg = todev(train["phi0"][keep]), todev(train["phi1"][keep]), todev(target[keep])
+    ct = todev(np.cos(np.radians(train["theta_deg"][keep])).astype(np.float32))
+    # -- training ---------------------------------------------------------------------------
+    net = WarmStartNet(n=B, h=n, w=n, seed=0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(stream)
+    curve = fit(net, p0, p1, ct, tg, args.ws_iters, lr=args.ws_lr, log_every=100)
+    e1.record(stream)
+    e1.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    log(f"warm start: {args.ws_iters} iterations in {time.time() - t0:.1f} s; loss {curve[0][1]:.3e} -> "
+        f"{curve[-1][1]:.3e}")
+    del p0, p1, tg, ct
+    # -- evaluation -------------------------------------------------------------------------
+    NE = args.ws_eval
+    e0d, e1d = todev(ev["phi0"]), todev(ev["phi1"])
+    ecd = todev(np.cos(np.radians(ev["theta_deg"])).astype(np.float32))
+    warm = torch.empty_like(e1d)
+    predict_all(net, e0d, e1d, ecd, warm)          # warm-up
+    e0.record(stream)
+    predict_all(net, e0d, e1d, ecd, warm)
+    e1.record(stream)
+    e1.synchronize()
+    infer_ms_per_sample = e0.elapsed_time(e1) / NE
+    warm_h = warm.cpu().numpy()
+    nsamp = T // every
+    th_plain = np.full((NE, nsamp), np.nan)
+    th_warm = np.full((NE, K // every), np.nan)
+    c_plain_K = np.empty_like(ev["phi1"])
+    c_ref = np.empty_like(ev["phi1"])
+    c_warm_K = np.empty_like(ev["phi1"])
+    ctx = _ws_context(L, ev, 0, NE, stream)
+    try:
+        ctx.set_phase(ev["phi1"])
+        ctx.step(16)
+        e0.record(stream)
+        ctx.step(512)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms = e0.elapsed_time(e1) / 512          # one step of all NE instances
+        ctx.set_phase(ev["phi1"])
+        for k in range(nsamp):
+            ctx.step(every)
+            for i in range(NE):
+                th_plain[i, k] = _ws_theta(L, ctx, ev, 0, i)
+            if (k + 1) * every == K:
+                c_plain_K[:] = ctx.get_fields()[0].reshape(NE, n, n)
+        c_ref[:] = ctx.get_fields()[0].reshape(NE, n, n)
+        ctx.set_phase_device(warm.data_ptr())
+        for k in range(K // every):
+            ctx.step(every)
+            for i in range(NE):
+                th_warm[i, k] = _ws_theta(L, ctx, ev, 0, i)
+        c_warm_K[:] = ctx.get_fields()[0].reshape(NE, n, n)
+    finally:
+        ctx.close()
+    rel = lambda a: np.linalg.norm((a - c_ref).reshape(NE, -1), axis=1) / np.linalg.norm(c_ref.reshape(NE, -1), axis=1)
+    th_ref = th_plain[:, -1]
+    kK = K // every - 1
+
+    def first_within(th, tol=0.5):
+        out = np.full(th.shape[0], np.nan)
+        for i in range(th.shape[0]):
+            hit = np.flatnonzero(np.abs(th[i] - th_ref[i]) <= tol)
+            if hit.size:
+                out[i] = (hit[0] + 1) * every
+        return out
+
+    steps_plain = first_within(th_plain)
+    steps_warm = first_within(th_warm)
+    ms_per_inst_step = step_ms / NE
+    ok = np.isfinite(th_ref)
+    med = lambda a: float(np.nanmedian(a)) if np.isfinite(a).any() else None
+    errs = {name: rel(a) for name, a in (("initial", ev["phi1"]), ("plain_K", c_plain_K), ("warm_0", warm_h),
+                                          ("warm_K", c_warm_K))}
+    dth_plain = np.abs(th_plain[:, kK] - th_ref)
+    dth_warm = np.abs(th_warm[:, kK] - th_ref)
+    t_plain_ref = T * ms_per_inst_step
+    t_warm = infer_ms_per_sample + K * ms_per_inst_step
+    line = {
+        "metric": "learned warm start: error against the plain run and time per geometry",
+        "value": t_plain_ref / t_warm, "unit": "x (time of the plain reference run / warm start time)",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "bf16 network (fp32 accumulate), f32 lattice",
+        "data": "synthetic", "config": {"workload": f"warm start {n}^2, batched distribution (1-6 disks, droplet, "
+                                                    f"theta 30-150)", "train": int(keep.size), "eval": NE,
+                                        "label_steps": T, "relax_steps": K, "iters": args.ws_iters, "batch": B},
+        "label_seconds": label_s, "train_ms": train_ms, "train_ms_per_iter": train_ms / args.ws_iters,
+        "loss_curve": curve[::max(1, len(curve) // 10)] + [curve[-1]],
+        "infer_ms_per_sample": infer_ms_per_sample, "lbm_ms_per_instance_step": ms_per_inst_step,
+        "ms_plain_reference": t_plain_ref, "ms_warm_start": t_warm,
+        "l2_rel_median": {k: float(np.median(v)) for k, v in errs.items()},
+        "l2_rel_mean": {k: float(np.mean(v)) for k, v in errs.items()},
+        "theta_measured": int(ok.sum()),
+        "theta_err_deg_median": {"plain_K": med(dth_plain[ok]), "warm_K": med(dth_warm[ok])},
+        "theta_within_0.5_at_K": {"plain": float(np.mean(dth_plain[ok] <= 0.5)),
+                                  "warm": float(np.mean(dth_warm[ok] <= 0.5))},
+        "steps_to_0.5deg_median": {"plain": med(steps_plain[ok]), "warm": med(steps_warm[ok])},
+        "warm_within_0.5deg_by_K": float(np.mean(np.isfinite(steps_warm[ok]))),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "warmstart256":
+        return run_warmstart(args)
     return run_gpu(args)
 
 

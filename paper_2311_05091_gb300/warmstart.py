@@ -239,3 +239,44 @@ class WarmStartNet:
             self.W[k].copy_(torch.from_numpy(st["W"][k]))
             self.b[k].copy_(torch.from_numpy(st["b"][k]))
         self.refresh()
+
+
+def fit(net, phi0, phi1, costh, target, iters, lr=2e-3, lr_end=1e-4, warmup=50, seed=0, log_every=50):
+    """Train ``net`` on device tensors phi0, phi1, target (N, h, w) and costh (N,).
+
+    Mini-batches of net.n samples are drawn without replacement per epoch
+    (seeded), Adam with a linear warm-up of ``warmup`` iterations and then a
+    cosine decay from lr to lr_end.  Returns [(iteration, mean squared error
+    per pixel of the batch)] every ``log_every`` iterations."""
+    N = phi0.shape[0]
+    B = net.n
+    assert N >= B
+    rng = np.random.default_rng(seed)
+    bufs = [torch.empty((B,) + tuple(t.shape[1:]), dtype=t.dtype, device=t.device) for t in (phi0, phi1, costh, target)]
+    perm, pos, log = rng.permutation(N), 0, []
+    P = B * net.h * net.w
+    for it in range(iters):
+        if pos + B > N:
+            perm, pos = rng.permutation(N), 0
+        idx = torch.from_numpy(perm[pos:pos + B]).to(phi0.device)
+        pos += B
+        for src, dst in zip((phi0, phi1, costh, target), bufs):
+            torch.index_select(src, 0, idx, out=dst)
+        if it < warmup:
+            rate = lr * (it + 1) / warmup
+        else:
+            x = (it - warmup) / max(1, iters - warmup)
+            rate = lr_end + 0.5 * (lr - lr_end) * (1.0 + np.cos(np.pi * x))
+        loss = net.train_step(bufs[0], bufs[1], bufs[2], bufs[3], rate)
+        if (it + 1) % log_every == 0 or it == iters - 1:
+            log.append((it + 1, loss.item() / P))
+    return log
+
+
+def predict_all(net, phi0, phi1, costh, out):
+    """Warm-start fields for every sample, net.n at a time; out (N, h, w) device tensor.  N % net.n == 0."""
+    N, B = phi0.shape[0], net.n
+    assert N % B == 0
+    for lo in range(0, N, B):
+        net.predict(phi0[lo:lo + B], phi1[lo:lo + B], costh[lo:lo + B], out[lo:lo + B])
+    return out

@@ -71,3 +71,34 @@ def batch_uneven(n_inst=64, seed=0, W=4.0):
     return dict(name=f"D2Q9 batch of {n_inst} instances, sides in {BATCH_SIDES}, 1-6 disks, droplet, "
                      f"theta in 30-150 deg (seed {seed}), {nodes} nodes",
                 lattice="D2Q9", instances=inst, nodes=nodes, periodic=(True, True))
+
+
+def warmstart_set(seeds, n=256, W=4.0):
+    """Samples of the learned warm start: the distribution of ``batch_uneven``
+    (1-6 disks of radii 8-40, one droplet of radius 10-60 on the largest disk,
+    theta uniform in 30-150 deg, d0 = 1/2, ratios 1) at one side n.  Each
+    sample is rolled by whole nodes (an exact symmetry of the periodic
+    lattice) so that the droplet's initial centre sits at (n/2, n/2) and its
+    disk right below it, which keeps the droplet away from the image border
+    that the network's zero padding sees.
+
+    Returns phi0, phi1 (N, n, n) float32, theta_deg (N,), the rolled disk
+    (N, 3: cx, cy, Rs) and the per-instance parameter dictionaries."""
+    N = len(seeds)
+    phi0 = np.empty((N, n, n), np.float32)
+    phi1 = np.empty((N, n, n), np.float32)
+    theta = np.empty(N)
+    disk = np.empty((N, 3))
+    params = []
+    for i, s in enumerate(seeds):
+        geo, th = random_disks_droplet(n=n, seed=int(s), W=W)
+        cx, cy = geo.disk_center
+        Rs = geo.disk_radius
+        sx = int(round(n / 2 - cx))
+        sy = int(round(n / 2 - (cy + Rs)))
+        phi0[i] = np.roll(geo.phi0, (sy, sx), axis=(0, 1))
+        phi1[i] = np.roll(geo.phi1, (sy, sx), axis=(0, 1))
+        theta[i] = th
+        disk[i] = ((cx + sx) % n, (cy + sy) % n, Rs)
+        params.append(dict(W=W, M_deg=0.1, theta_deg=th, kappa=geo.kappa, sigma=0.01, d0=0.5))
+    return dict(phi0=phi0, phi1=phi1, theta_deg=theta, disk=disk, params=params, n=n)

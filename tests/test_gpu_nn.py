@@ -2,9 +2,9 @@
 
 The reference applies the kernels' BF16 rounding to the same float32 inputs,
 so the only differences left are the float32 accumulation order (bounded
-relative to the sum of absolute products) and, in a whole network, the rare
-BF16 rounding decision that the float32 activations take on the other side
-of a midpoint."""
+relative to the sum of absolute products) and, in a whole network, the BF16
+rounding decisions that float32-sized differences flip (measured against
+the reference's own sensitivity)."""
 import numpy as np
 import pytest
 import torch
@@ -123,26 +123,28 @@ def test_pooling_upsampling_relu_add_pack(nn):
     r = _rng(4)
     n, h, w, c = 2, 10, 14, 32
     x = r.normal(0, 1, (n, h, w, c)).astype(np.float32)
+    xd = _dev(x)                       # every device input is held by a name while kernels use it
     y = torch.empty((n, h // 2, w // 2, c), device="cuda")
-    nn.pool2(_dev(x).data_ptr(), y.data_ptr(), n, h, w, c)
+    nn.pool2(xd.data_ptr(), y.data_ptr(), n, h, w, c)
     np.testing.assert_allclose(y.cpu().numpy(), onn.pool2(x.astype(np.float64)), rtol=1e-6, atol=1e-7)
     g = r.normal(0, 1, (n, h // 2, w // 2, c)).astype(np.float32)
+    gd = _dev(g)
     gx = torch.empty((n, h, w, c), device="cuda")
-    nn.pool2(_dev(g).data_ptr(), gx.data_ptr(), n, h, w, c, backward=True)
+    nn.pool2(gd.data_ptr(), gx.data_ptr(), n, h, w, c, backward=True)
     np.testing.assert_allclose(gx.cpu().numpy(), onn.pool2_adj(g.astype(np.float64)), rtol=1e-7)
     u = torch.empty((n, h, w, c), device="cuda")
-    nn.up2(_dev(g).data_ptr(), u.data_ptr(), n, h // 2, w // 2, c)
+    nn.up2(gd.data_ptr(), u.data_ptr(), n, h // 2, w // 2, c)
     np.testing.assert_array_equal(u.cpu().numpy(), onn.up2(g))
     ua = torch.empty((n, h // 2, w // 2, c), device="cuda")
-    nn.up2(_dev(x).data_ptr(), ua.data_ptr(), n, h // 2, w // 2, c, backward=True)
+    nn.up2(xd.data_ptr(), ua.data_ptr(), n, h // 2, w // 2, c, backward=True)
     np.testing.assert_allclose(ua.cpu().numpy(), onn.up2_adj(x.astype(np.float64)), rtol=1e-6, atol=1e-6)
     # ReLU adjoint, out of place and in place
     yv = r.normal(0, 1, 1000).astype(np.float32)
     dy = r.normal(0, 1, 1000).astype(np.float32)
-    dyd, out = _dev(dy), torch.empty(1000, device="cuda")
-    nn.relu_bwd(dyd.data_ptr(), _dev(yv).data_ptr(), out.data_ptr(), 1000)
+    dyd, yvd, out = _dev(dy), _dev(yv), torch.empty(1000, device="cuda")
+    nn.relu_bwd(dyd.data_ptr(), yvd.data_ptr(), out.data_ptr(), 1000)
     np.testing.assert_array_equal(out.cpu().numpy(), np.where(yv > 0, dy, 0.0))
-    nn.relu_bwd(dyd.data_ptr(), _dev(yv).data_ptr(), dyd.data_ptr(), 1000)
+    nn.relu_bwd(dyd.data_ptr(), yvd.data_ptr(), dyd.data_ptr(), 1000)
     np.testing.assert_array_equal(dyd.cpu().numpy(), np.where(yv > 0, dy, 0.0))
     a, b = _dev(dy), _dev(yv)
     nn.add(a.data_ptr(), a.data_ptr(), b.data_ptr(), -0.5, 1000)
@@ -151,8 +153,9 @@ def test_pooling_upsampling_relu_add_pack(nn):
     phi0 = r.uniform(0, 1, (n, h, w)).astype(np.float32)
     phi1 = r.uniform(0, 1, (n, h, w)).astype(np.float32)
     ct = np.array([0.5, -0.25], np.float32)
+    p0d, p1d, ctd = _dev(phi0), _dev(phi1), _dev(ct)
     xin = torch.full((n, h, w, 16), np.nan, device="cuda")
-    nn.pack_input(_dev(phi0).data_ptr(), _dev(phi1).data_ptr(), _dev(ct).data_ptr(), xin.data_ptr(), n, h, w)
+    nn.pack_input(p0d.data_ptr(), p1d.data_ptr(), ctd.data_ptr(), xin.data_ptr(), n, h, w)
     xi = xin.cpu().numpy()
     np.testing.assert_array_equal(xi[..., 0], phi0)
     np.testing.assert_array_equal(xi[..., 1], phi1)
@@ -170,8 +173,9 @@ def test_mse_adam_projection(nn):
     dout = torch.full((n, h, w, cp), np.nan, device="cuda")
     work = torch.empty(4096, dtype=torch.float64, device="cuda")
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
-    nn.mse_residual(_dev(out).data_ptr(), cp, _dev(base).data_ptr(), _dev(target).data_ptr(), dout.data_ptr(),
-                    work.data_ptr(), 4096, loss.data_ptr(), P)
+    outd, based, tgd = _dev(out), _dev(base), _dev(target)
+    nn.mse_residual(outd.data_ptr(), cp, based.data_ptr(), tgd.data_ptr(), dout.data_ptr(), work.data_ptr(), 4096,
+                    loss.data_ptr(), P)
     l_ref, d_ref = onn.mse_residual(out.astype(np.float64), base.astype(np.float64), target.astype(np.float64))
     assert abs(loss.item() - l_ref) <= 1e-6 * l_ref
     np.testing.assert_allclose(dout.cpu().numpy(), d_ref, rtol=1e-5, atol=1e-9)
@@ -183,8 +187,9 @@ def test_mse_adam_projection(nn):
     wr, mr, vr = wv.astype(np.float64), np.zeros(m0), np.zeros(m0)
     for t in range(1, 4):
         gv = r.normal(0, 1, m0).astype(np.float32)
-        nn.adam(wd.data_ptr(), md.data_ptr(), vd.data_ptr(), _dev(gv).data_ptr(), wb.data_ptr(), m0, 1e-2, 0.9, 0.999,
-                1e-8, t)
+        gvd = _dev(gv)
+        nn.adam(wd.data_ptr(), md.data_ptr(), vd.data_ptr(), gvd.data_ptr(), wb.data_ptr(), m0, 1e-2, 0.9, 0.999, 1e-8,
+                t)
         wr, mr, vr = onn.adam(wr, mr, vr, gv.astype(np.float64), 1e-2, 0.9, 0.999, 1e-8, t)
     np.testing.assert_allclose(wd.cpu().numpy(), wr, rtol=1e-6, atol=3e-7)
     np.testing.assert_allclose(md.cpu().numpy(), mr, rtol=1e-5, atol=1e-7)
@@ -192,9 +197,9 @@ def test_mse_adam_projection(nn):
     # projection onto [0, 1 - phi0] with the initial phase mass
     phi0 = np.clip(r.normal(0, 0.4, (n, h, w)), 0, 1).astype(np.float32)
     phi1 = np.clip(r.uniform(0, 1, (n, h, w)), 0, 1 - phi0).astype(np.float32)
+    p0d, p1d = _dev(phi0), _dev(phi1)
     field = torch.empty((n, h, w), device="cuda")
-    nn.project(_dev(out).data_ptr(), cp, _dev(phi0).data_ptr(), _dev(phi1).data_ptr(), field.data_ptr(),
-               work.data_ptr(), 4096, n, h, w)
+    nn.project(outd.data_ptr(), cp, p0d.data_ptr(), p1d.data_ptr(), field.data_ptr(), work.data_ptr(), 4096, n, h, w)
     ref = onn.project(out[..., 0].astype(np.float64), phi0.astype(np.float64), phi1.astype(np.float64))
     got = field.cpu().numpy()
     np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-6)
@@ -225,13 +230,26 @@ def test_network_forward_backward(nn, widths, n, h, w):
 
     params = [(W.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)) for W, b in zip(net.W, net.b)]
     xr = x.cpu().numpy().astype(np.float64)
-    out_ref, cache = onn.forward(xr, params, list(widths), bf16=True)
-    loss_ref, dout_ref = onn.mse_residual(out_ref, phi1.astype(np.float64), target.astype(np.float64))
-    grads = onn.backward(dout_ref, params, list(widths), cache, bf16=True)
 
+    def reference(prm):
+        o, cache = onn.forward(xr, prm, list(widths), bf16=True)
+        lo, do = onn.mse_residual(o, phi1.astype(np.float64), target.astype(np.float64))
+        return o, lo, onn.backward(do, prm, list(widths), cache, bf16=True)
+
+    out_ref, loss_ref, grads = reference(params)
+    # The BF16 roundings make a deep network's output a discontinuous function
+    # of its inputs: float32-sized differences flip a few roundings, and the
+    # changed outputs flip more in the next layer.  The reference's own spread
+    # under a 1e-7 relative perturbation of the weights measures that; the
+    # kernels must stay within a few times it (and within 1e-4 / 1e-3 when it
+    # is smaller).
+    rp = np.random.default_rng(7)
+    out_p, _, grads_p = reference([(W * (1 + 1e-7 * rp.normal(0, 1, W.shape)), b) for W, b in params])
     rel = lambda a, b: np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-    assert rel(out.cpu().numpy(), out_ref) < 1e-4
-    assert abs(net.loss.item() - loss_ref) < 1e-4 * loss_ref
+    assert rel(out.cpu().numpy(), out_ref) < max(1e-4, 4 * rel(out_p, out_ref))
+    assert abs(net.loss.item() - loss_ref) < max(1e-4, 4 * rel(out_p, out_ref)) * loss_ref
     for k, (dW, db) in enumerate(grads):
-        assert rel(net.dW[k].cpu().numpy(), dW) < 1e-3, k
-        assert rel(net.db[k].cpu().numpy(), db) < 1e-3, k
+        assert rel(net.dW[k].cpu().numpy(), dW) < max(1e-3, 4 * rel(grads_p[k][0], dW)), k
+        assert rel(net.db[k].cpu().numpy(), db) < max(1e-3, 4 * rel(grads_p[k][1], db)), k
+    if len(widths) == 2:          # a short network has no cascade: the tight bars hold outright
+        assert rel(out.cpu().numpy(), out_ref) < 1e-4
