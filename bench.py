@@ -91,6 +91,7 @@ def parse():
     ap.add_argument("--ws-relax-steps", type=int, default=2000, help="warm start: relaxation steps after inference")
     ap.add_argument("--ws-every", type=int, default=250, help="warm start: contact-angle sampling interval")
     ap.add_argument("--ws-lr", type=float, default=2e-3)
+    ap.add_argument("--ws-save", default=None, help="warm start: write the trained weights (.npz) here")
     return ap.parse_args()
 
 
@@ -695,6 +696,10 @@ def run_warmstart(args):
     train_ms = e0.elapsed_time(e1)
     log(f"warm start: {args.ws_iters} iterations in {time.time() - t0:.1f} s; loss {curve[0][1]:.3e} -> "
         f"{curve[-1][1]:.3e}")
+    if args.ws_save:
+        st = net.state()
+        np.savez(args.ws_save, widths=np.array(st["widths"]), **{f"W{k}": W for k, W in enumerate(st["W"])},
+                 **{f"b{k}": b for k, b in enumerate(st["b"])})
     del p0, p1, tg, ct
     # -- evaluation -------------------------------------------------------------------------
     NE = args.ws_eval
@@ -740,6 +745,10 @@ def run_warmstart(args):
     finally:
         ctx.close()
     rel = lambda a: np.linalg.norm((a - c_ref).reshape(NE, -1), axis=1) / np.linalg.norm(c_ref.reshape(NE, -1), axis=1)
+    finite_warm = np.isfinite(c_warm_K).all(axis=(1, 2))
+    hi = np.maximum(1.0 - ev["phi0"], 0.0)
+    below = (warm_h < -1e-6).any(axis=(1, 2))
+    above = (warm_h > hi + 1e-6).any(axis=(1, 2))
     th_ref = th_plain[:, -1]
     kK = K // every - 1
 
@@ -754,7 +763,7 @@ def run_warmstart(args):
     steps_plain = first_within(th_plain)
     steps_warm = first_within(th_warm)
     ms_per_inst_step = step_ms / NE
-    ok = np.isfinite(th_ref)
+    ok = np.isfinite(th_ref) & finite_warm
     med = lambda a: float(np.nanmedian(a)) if np.isfinite(a).any() else None
     errs = {name: rel(a) for name, a in (("initial", ev["phi1"]), ("plain_K", c_plain_K), ("warm_0", warm_h),
                                           ("warm_K", c_warm_K))}
@@ -773,8 +782,11 @@ def run_warmstart(args):
         "loss_curve": curve[::max(1, len(curve) // 10)] + [curve[-1]],
         "infer_ms_per_sample": infer_ms_per_sample, "lbm_ms_per_instance_step": ms_per_inst_step,
         "ms_plain_reference": t_plain_ref, "ms_warm_start": t_warm,
-        "l2_rel_median": {k: float(np.median(v)) for k, v in errs.items()},
-        "l2_rel_mean": {k: float(np.mean(v)) for k, v in errs.items()},
+        "warm_runs_non_finite": int((~finite_warm).sum()),
+        "warm_fields_out_of_bounds": {"below_0": int(below.sum()), "above_1_minus_phi0": int(above.sum()),
+                                      "of_non_finite_runs": int(((below | above) & ~finite_warm).sum())},
+        "l2_rel_median": {k: float(np.median(v[finite_warm])) for k, v in errs.items()},
+        "l2_rel_mean": {k: float(np.mean(v[finite_warm])) for k, v in errs.items()},
         "theta_measured": int(ok.sum()),
         "theta_err_deg_median": {"plain_K": med(dth_plain[ok]), "warm_K": med(dth_warm[ok])},
         "theta_within_0.5_at_K": {"plain": float(np.mean(dth_plain[ok] <= 0.5)),

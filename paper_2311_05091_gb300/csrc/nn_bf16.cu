@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "../../include/lbm_nn.h"
 
 namespace {
@@ -33,146 +35,229 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// neighbour of pixel p (image n, row y, column x) at tap (ky, kx), or -1 outside the image (zero padding)
-__device__ __forceinline__ long long tap_pixel(long long p, int n, int y, int x, int h, int w, int ky, int kx) {
-  const int yy = y + ky - 1, xx = x + kx - 1;
-  if (p < 0 || yy < 0 || yy >= h || xx < 0 || xx >= w) return -1;
-  return ((long long)n * h + yy) * w + xx;
-}
-
-// two consecutive channels of pixel q as one BF16 pair (zero outside)
-__device__ __forceinline__ uint32_t load_pair(const float* __restrict__ x, long long q, int cin, int c) {
-  if (q < 0) return 0u;
-  const float2 v = *reinterpret_cast<const float2*>(x + q * cin + c);
-  return pack_bf16(v.x, v.y);
-}
-
 // ---------------------------------------------------------------------------
 // forward: y[p][co] = act(b[co] + sum_{tap, ci} x[p + shift(tap)][ci] wt[tap][co][ci])
-// CTA: 4 warps x 16 pixels, 32 output channels; grid (ceil(P / 64), cout / 32)
+// CTA: one 64-pixel row segment (image, row y, columns x0 .. x0 + 63) x 32 CW
+// output channels, 4 warps in a 2 (pixels) x 2 (channels) grid, each warp 32
+// pixels x 16 CW channels.  Per chunk of 32 input channels the CTA stages, as
+// BF16 in shared memory, the input rows y - 1 .. y + 1 at columns x0 - 1 ..
+// x0 + 64 ([row][column][ci], zero outside the image) and the weights of all
+// nine taps ([tap][co][ci]); rows are padded to 40 elements (20 words) so a
+// fragment load touches 32 different banks.  The nine taps then read shifted
+// windows of the same input rows.  grid (segments, cout / (32 CW)).
 // ---------------------------------------------------------------------------
+constexpr int kFwdSeg = 64, kCiChunk = 32, kCiPad = 40;
+
+template <int CW>
 __global__ void __launch_bounds__(kThreads) conv3x3_fwd(const float* __restrict__ x,
                                                         const __nv_bfloat16* __restrict__ wt,
                                                         const float* __restrict__ bias, float* __restrict__ y,
                                                         int n, int h, int w, int cin, int cout, int relu) {
+  constexpr int CO = 32 * CW, NT = 2 * CW;                     // CTA channels, n-tiles per warp
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16(*sx)[kFwdSeg + 2][kCiPad] = reinterpret_cast<__nv_bfloat16(*)[kFwdSeg + 2][kCiPad]>(smem_raw);
+  __nv_bfloat16(*sw)[CO][kCiPad] =
+      reinterpret_cast<__nv_bfloat16(*)[CO][kCiPad]>(smem_raw + sizeof(__nv_bfloat16) * 3 * (kFwdSeg + 2) * kCiPad);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const long long P = (long long)n * h * w;
-  const long long p0 = (long long)blockIdx.x * 64 + warp * 16;
-  const int co0 = blockIdx.y * 32;
-  long long pr[2];
-  int pn[2], py[2], px[2];
+  const int wm = warp & 1, wn = warp >> 1;
+  const int spr = (w + kFwdSeg - 1) / kFwdSeg;
+  const long long sg = blockIdx.x;
+  const int img = (int)(sg / ((long long)h * spr));
+  const int yrow = (int)((sg / spr) % h);
+  const int x0 = (int)(sg % spr) * kFwdSeg;
+  const int co0 = blockIdx.y * CO;
+  float acc[2][NT][4];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const long long p = p0 + g + 8 * r;
-    pr[r] = p < P ? p : -1;
-    const long long q = p < P ? p : 0;
-    px[r] = (int)(q % w);
-    py[r] = (int)((q / w) % h);
-    pn[r] = (int)(q / ((long long)w * h));
-  }
-  float acc[4][4];
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < NT; ++j)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  const uint32_t* __restrict__ wt32 = reinterpret_cast<const uint32_t*>(wt);
-  for (int tap = 0; tap < 9; ++tap) {
-    const int ky = tap / 3, kx = tap % 3;
-    const long long q0 = tap_pixel(pr[0], pn[0], py[0], px[0], h, w, ky, kx);
-    const long long q1 = tap_pixel(pr[1], pn[1], py[1], px[1], h, w, ky, kx);
-    for (int ci0 = 0; ci0 < cin; ci0 += 16) {
-      uint32_t a[4];
-      a[0] = load_pair(x, q0, cin, ci0 + 2 * t);
-      a[1] = load_pair(x, q1, cin, ci0 + 2 * t);
-      a[2] = load_pair(x, q0, cin, ci0 + 2 * t + 8);
-      a[3] = load_pair(x, q1, cin, ci0 + 2 * t + 8);
+      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+  for (int ci0 = 0; ci0 < cin; ci0 += kCiChunk) {
+    const int cw = min(kCiChunk, cin - ci0);                   // 16 or 32 channels in this chunk
+    __syncthreads();
+    // input rows: 3 x 66 columns x 8 float4 of channels
+    for (int e = threadIdx.x; e < 3 * (kFwdSeg + 2) * 8; e += kThreads) {
+      const int r = e / ((kFwdSeg + 2) * 8), rem = e % ((kFwdSeg + 2) * 8);
+      const int jc = rem >> 3, c4 = (rem & 7) * 4;
+      const int yy = yrow + r - 1, xc = x0 + jc - 1;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (yy >= 0 && yy < h && xc >= 0 && xc < w && c4 < cw)
+        v = *reinterpret_cast<const float4*>(x + (((long long)img * h + yy) * w + xc) * cin + ci0 + c4);
+      uint2 packed;
+      packed.x = pack_bf16(v.x, v.y);
+      packed.y = pack_bf16(v.z, v.w);
+      *reinterpret_cast<uint2*>(&sx[r][jc][c4]) = packed;
+    }
+    // weights: 9 taps x CO channels x 32 inputs, 8 BF16 (16 bytes) per load
+    for (int e = threadIdx.x; e < 9 * CO * 4; e += kThreads) {
+      const int tap = e / (CO * 4), rem = e % (CO * 4);
+      const int co = rem >> 2, c8 = (rem & 3) * 8;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (c8 < cw) v = *reinterpret_cast<const uint4*>(wt + ((long long)tap * cout + co0 + co) * cin + ci0 + c8);
+      *reinterpret_cast<uint4*>(&sw[tap][co][c8]) = v;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap % 3;
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const long long wrow = ((long long)tap * cout + co0 + nt * 8 + g) * cin + ci0 + 2 * t;
-        mma_bf16(acc[nt], a, wt32[wrow >> 1], wt32[(wrow + 8) >> 1]);
+      for (int kk = 0; kk < kCiChunk; kk += 16) {
+        if (kk >= cw) break;
+        uint32_t a[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const int px = wm * 32 + mt * 16 + g + kx;           // column index jc = pixel + kx (shift kx - 1, +1 halo)
+          a[mt][0] = *reinterpret_cast<const uint32_t*>(&sx[ky][px][kk + 2 * t]);
+          a[mt][1] = *reinterpret_cast<const uint32_t*>(&sx[ky][px + 8][kk + 2 * t]);
+          a[mt][2] = *reinterpret_cast<const uint32_t*>(&sx[ky][px][kk + 2 * t + 8]);
+          a[mt][3] = *reinterpret_cast<const uint32_t*>(&sx[ky][px + 8][kk + 2 * t + 8]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int co = wn * 16 * CW + nt * 8 + g;
+          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&sw[tap][co][kk + 2 * t]);
+          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&sw[tap][co][kk + 2 * t + 8]);
+          mma_bf16(acc[0][nt], a[0], b0, b1);
+          mma_bf16(acc[1][nt], a[1], b0, b1);
+        }
       }
     }
   }
+  // acc[mt][nt]: pixels wm 32 + mt 16 + g (+8), channels co0 + wn 16 CW + nt 8 + 2 t (+1)
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    const int co = co0 + nt * 8 + 2 * t;
+  for (int nt = 0; nt < NT; ++nt) {
+    const int co = co0 + wn * 16 * CW + nt * 8 + 2 * t;
     const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (pr[r] < 0) continue;
-      float v0 = acc[nt][2 * r] + b0, v1 = acc[nt][2 * r + 1] + b1;
-      if (relu) {
-        v0 = fmaxf(v0, 0.f);
-        v1 = fmaxf(v1, 0.f);
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int xc = x0 + wm * 32 + mt * 16 + g + 8 * half;
+        if (xc >= w) continue;
+        float v0 = acc[mt][nt][2 * half] + b0, v1 = acc[mt][nt][2 * half + 1] + b1;
+        if (relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        *reinterpret_cast<float2*>(y + (((long long)img * h + yrow) * w + xc) * cout + co) = make_float2(v0, v1);
       }
-      *reinterpret_cast<float2*>(y + pr[r] * cout + co) = make_float2(v0, v1);
-    }
   }
 }
 
+template <int CW>
+constexpr int fwd_smem_bytes() {
+  return (int)sizeof(__nv_bfloat16) * (3 * (kFwdSeg + 2) * kCiPad + 9 * 32 * CW * kCiPad);
+}
+
 // ---------------------------------------------------------------------------
-// weight gradient, per pixel chunk z:
+// weight gradient, per chunk z of 64-pixel row segments:
 //   part[z][tap][co][ci] = sum_{p in chunk z} dy[p][co] x[p + shift(tap)][ci]
-// CTA: 4 warps over 16 output channels x up to 32 input channels; each warp
-// takes every fourth group of 16 pixels of the chunk; the four partial tiles
-// are summed in shared memory.  grid (9 cout / 16, ceil(cin / 32), chunks)
+// CTA: a 32 (co) x 32 (ci) tile, 9 warps, warp = tap.  Per row segment
+// (image, row y, columns x0 .. x0 + 63) the CTA stages dy^T [co][px] and, for
+// each column offset kx, x^T [kx][row y + ky - 1][ci][px + kx - 1] in shared
+// memory as BF16 (zero outside the image), so that every mma fragment is one
+// aligned 32-bit shared load; warp (ky, kx) then multiplies dy^T (32 x 64)
+// by its shifted x (64 x 32).  Rows are padded to 72 elements (36 words), so
+// the 32 lanes of a fragment load hit 32 different banks.
+// grid (ceil(cout / 32), ceil(cin / 32), chunks), 288 threads.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) conv3x3_wgrad_part(const float* __restrict__ x,
-                                                               const float* __restrict__ dy,
-                                                               float* __restrict__ part, int n, int h, int w,
-                                                               int cin, int cout, long long chunk) {
-  __shared__ float red[4][16][32];
+constexpr int kSeg = 64, kPad = 72, kWgThreads = 288;
+
+__global__ void __launch_bounds__(kWgThreads) conv3x3_wgrad_seg(const float* __restrict__ x,
+                                                                const float* __restrict__ dy,
+                                                                float* __restrict__ part, int n, int h, int w,
+                                                                int cin, int cout, long long segs_per_chunk) {
+  __shared__ __align__(16) __nv_bfloat16 sdy[32][kPad];
+  __shared__ __align__(16) __nv_bfloat16 sx[3][3][32][kPad];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const long long P = (long long)n * h * w;
-  const int ntile_co = cout / 16;
-  const int tap = blockIdx.x / ntile_co, co0 = (blockIdx.x % ntile_co) * 16;
-  const int ky = tap / 3, kx = tap % 3;
-  const int ci0 = blockIdx.y * 32;
-  const int nnt = min(4, (cin - ci0) / 8);
-  const long long pb = (long long)blockIdx.z * chunk, pe = min(P, pb + chunk);
-  float acc[4][4];
+  const int ky = warp / 3, kx = warp % 3;
+  const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
+  const int spr = (w + kSeg - 1) / kSeg;                       // segments per image row
+  const long long nseg = (long long)n * h * spr;
+  const long long s0 = (long long)blockIdx.z * segs_per_chunk;
+  const long long s1 = min(nseg, s0 + segs_per_chunk);
+  float acc[2][4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  auto dyv = [&](long long p, int co) { return p < pe ? dy[p * cout + co] : 0.f; };
-  auto xv = [&](long long p, int ci) {
-    if (p >= pe) return 0.f;
-    const int px = (int)(p % w), py = (int)((p / w) % h), pn = (int)(p / ((long long)w * h));
-    const long long q = tap_pixel(p, pn, py, px, h, w, ky, kx);
-    return q < 0 ? 0.f : x[q * cin + ci];
-  };
-  for (long long pk = pb + 16 * warp; pk < pe; pk += 64) {
-    uint32_t a[4];
-    const long long k0 = pk + 2 * t, k8 = pk + 2 * t + 8;
-    a[0] = pack_bf16(dyv(k0, co0 + g), dyv(k0 + 1, co0 + g));
-    a[1] = pack_bf16(dyv(k0, co0 + g + 8), dyv(k0 + 1, co0 + g + 8));
-    a[2] = pack_bf16(dyv(k8, co0 + g), dyv(k8 + 1, co0 + g));
-    a[3] = pack_bf16(dyv(k8, co0 + g + 8), dyv(k8 + 1, co0 + g + 8));
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      if (nt >= nnt) break;
-      const int ci = ci0 + nt * 8 + g;
-      const uint32_t b0 = pack_bf16(xv(k0, ci), xv(k0 + 1, ci));
-      const uint32_t b1 = pack_bf16(xv(k8, ci), xv(k8 + 1, ci));
-      mma_bf16(acc[nt], a, b0, b1);
+      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+  for (long long sg = s0; sg < s1; ++sg) {
+    const int img = (int)(sg / ((long long)h * spr));
+    const int y = (int)((sg / spr) % h);
+    const int x0 = (int)(sg % spr) * kSeg;
+    __syncthreads();                                           // the previous segment's fragments are consumed
+    // dy^T: 64 pixels x 32 channels as 8 float4 per pixel
+    for (int e = threadIdx.x; e < kSeg * 8; e += kWgThreads) {
+      const int j = e >> 3, c4 = (e & 7) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (x0 + j < w && co0 + c4 < cout)
+        v = *reinterpret_cast<const float4*>(dy + (((long long)img * h + y) * w + x0 + j) * cout + co0 + c4);
+      sdy[c4][j] = __float2bfloat16_rn(v.x);
+      sdy[c4 + 1][j] = __float2bfloat16_rn(v.y);
+      sdy[c4 + 2][j] = __float2bfloat16_rn(v.z);
+      sdy[c4 + 3][j] = __float2bfloat16_rn(v.w);
+    }
+    // x^T: rows y - 1 .. y + 1, columns x0 - 1 .. x0 + 64, 32 channels; column xc goes to copy kx at xc - x0 - kx + 1
+    for (int e = threadIdx.x; e < 3 * (kSeg + 2) * 8; e += kWgThreads) {
+      const int r = e / ((kSeg + 2) * 8), rem = e % ((kSeg + 2) * 8);
+      const int jc = rem >> 3, c4 = (rem & 7) * 4;             // jc = xc - x0 + 1 in 0 .. 65
+      const int yy = y + r - 1, xc = x0 + jc - 1;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (yy >= 0 && yy < h && xc >= 0 && xc < w && ci0 + c4 < cin)
+        v = *reinterpret_cast<const float4*>(x + (((long long)img * h + yy) * w + xc) * cin + ci0 + c4);
+      const __nv_bfloat16 b0 = __float2bfloat16_rn(v.x), b1 = __float2bfloat16_rn(v.y);
+      const __nv_bfloat16 b2 = __float2bfloat16_rn(v.z), b3 = __float2bfloat16_rn(v.w);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int j = jc - k;
+        if (j >= 0 && j < kSeg) {
+          sx[k][r][c4][j] = b0;
+          sx[k][r][c4 + 1][j] = b1;
+          sx[k][r][c4 + 2][j] = b2;
+          sx[k][r][c4 + 3][j] = b3;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < kSeg / 16; ++ks) {
+      const int k0 = ks * 16 + 2 * t;
+      uint32_t a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        a[mt][0] = *reinterpret_cast<const uint32_t*>(&sdy[mt * 16 + g][k0]);
+        a[mt][1] = *reinterpret_cast<const uint32_t*>(&sdy[mt * 16 + g + 8][k0]);
+        a[mt][2] = *reinterpret_cast<const uint32_t*>(&sdy[mt * 16 + g][k0 + 8]);
+        a[mt][3] = *reinterpret_cast<const uint32_t*>(&sdy[mt * 16 + g + 8][k0 + 8]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&sx[kx][ky][nt * 8 + g][k0]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&sx[kx][ky][nt * 8 + g][k0 + 8]);
+        mma_bf16(acc[0][nt], a[0], b0, b1);
+        mma_bf16(acc[1][nt], a[1], b0, b1);
+      }
     }
   }
-  // acc[nt] covers rows co0 + g (+8), columns ci0 + nt 8 + 2 t (+1)
+  // acc[mt][nt]: rows co0 + 16 mt + g (+8), columns ci0 + 8 nt + 2 t (+1)
+  const int tap = warp;
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    red[warp][g][nt * 8 + 2 * t] = acc[nt][0];
-    red[warp][g][nt * 8 + 2 * t + 1] = acc[nt][1];
-    red[warp][g + 8][nt * 8 + 2 * t] = acc[nt][2];
-    red[warp][g + 8][nt * 8 + 2 * t + 1] = acc[nt][3];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < 16 * 32; e += kThreads) {
-    const int r = e / 32, c = e % 32;
-    if (c >= nnt * 8) continue;
-    const float v = (red[0][r][c] + red[1][r][c]) + (red[2][r][c] + red[3][r][c]);
-    part[(((long long)blockIdx.z * 9 + tap) * cout + co0 + r) * cin + ci0 + c] = v;
-  }
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int co = co0 + mt * 16 + g + 8 * half;
+      if (co >= cout) continue;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int ci = ci0 + nt * 8 + 2 * t;
+        if (ci >= cin) continue;
+        *reinterpret_cast<float2*>(part + (((long long)blockIdx.z * 9 + tap) * cout + co) * cin + ci) =
+            make_float2(acc[mt][nt][2 * half], acc[mt][nt][2 * half + 1]);
+      }
+    }
 }
 
 // out[i] = sum_z part[z][i] in chunk order (deterministic)
@@ -184,15 +269,24 @@ __global__ void sum_parts(const float* __restrict__ part, float* __restrict__ ou
   out[i] = s;
 }
 
-// bias gradient partials: part[z][c] = sum_{p in chunk z} dy[p][c]
-__global__ void colsum_part(const float* __restrict__ dy, float* __restrict__ part, long long P, int c,
-                            long long chunk) {
-  const int ch = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ch >= c) return;
+// bias gradient partials: part[z][c] = sum_{p in chunk z} dy[p][c]; block = 32 channels x 8 pixel lanes,
+// lanes combined in a fixed order (deterministic).  grid (ceil(c / 32), chunks)
+__global__ void __launch_bounds__(256) colsum_part(const float* __restrict__ dy, float* __restrict__ part, long long P,
+                                                   int c, long long chunk) {
+  __shared__ float red[8][32];
+  const int ch = blockIdx.x * 32 + (threadIdx.x & 31), r = threadIdx.x >> 5;
   const long long pb = (long long)blockIdx.y * chunk, pe = min(P, pb + chunk);
   float s = 0.f;
-  for (long long p = pb; p < pe; ++p) s += dy[p * c + ch];
-  part[(long long)blockIdx.y * c + ch] = s;
+  if (ch < c)
+    for (long long p = pb + r; p < pe; p += 8) s += dy[p * c + ch];
+  red[r][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (r == 0 && ch < c) {
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v += red[k][threadIdx.x & 31];
+    part[(long long)blockIdx.y * c + ch] = v;
+  }
 }
 
 // wt'[tap][ci][co] = wt[8 - tap][co][ci]: the kernel of the data gradient
@@ -380,18 +474,55 @@ extern "C" {
 int lbm_nn_conv3x3(const float* x, const void* wt_bf16, const float* bias, float* y, int n, int h, int w, int cin,
                    int cout, int relu, void* stream) {
   if (!x || !wt_bf16 || !y || n < 1 || h < 1 || w < 1 || cin < 16 || cin % 16 || cout < 32 || cout % 32) return -1;
-  const long long P = (long long)n * h * w;
-  dim3 grid((unsigned)((P + 63) / 64), cout / 32);
-  conv3x3_fwd<<<grid, kThreads, 0, (cudaStream_t)stream>>>(x, static_cast<const __nv_bfloat16*>(wt_bf16), bias, y,
-                                                           n, h, w, cin, cout, relu);
+  static bool attr_set = false;                                // the opt-in above 48 KB, once per process
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(conv3x3_fwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd_smem_bytes<2>()) !=
+        cudaSuccess)
+      return -3;
+    attr_set = true;
+  }
+  const long long segs = (long long)n * h * ((w + kFwdSeg - 1) / kFwdSeg);
+  const auto* wb = static_cast<const __nv_bfloat16*>(wt_bf16);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cout % 64 == 0)
+    conv3x3_fwd<2><<<dim3((unsigned)segs, cout / 64), kThreads, fwd_smem_bytes<2>(), s>>>(x, wb, bias, y, n, h, w, cin,
+                                                                                            cout, relu);
+  else
+    conv3x3_fwd<1><<<dim3((unsigned)segs, cout / 32), kThreads, fwd_smem_bytes<1>(), s>>>(x, wb, bias, y, n, h, w, cin,
+                                                                                            cout, relu);
   return status(cudaGetLastError());
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr long long kBiasChunk = 4096;
+
+// row segments per CTA of the weight gradient: about four CTAs per SM over the (co, ci) tiles
+struct WgradPlan {
+  long long segs, per_chunk, chunks, bias_chunks;
+};
+
+WgradPlan wgrad_plan(int n, int h, int w, int cin, int cout) {
+  WgradPlan p;
+  p.segs = (long long)n * h * ((w + kSeg - 1) / kSeg);
+  const long long tiles = (long long)((cout + 31) / 32) * ((cin + 31) / 32);
+  const long long want = std::max(1LL, (4LL * 152 + tiles - 1) / tiles);
+  p.per_chunk = std::max(1LL, (p.segs + want - 1) / want);
+  p.chunks = (p.segs + p.per_chunk - 1) / p.per_chunk;
+  p.bias_chunks = ((long long)n * h * w + kBiasChunk - 1) / kBiasChunk;
+  return p;
+}
+
+}  // namespace
+
+extern "C" {
+
 long long lbm_nn_wgrad_workspace(int n, int h, int w, int cin, int cout) {
-  const long long P = (long long)n * h * w;
-  const long long chunk = 4096;
-  const long long chunks = (P + chunk - 1) / chunk;
-  return chunks * (9LL * cin * cout + cout);
+  if (n < 1 || h < 1 || w < 1 || cin < 1 || cout < 1) return 0;
+  const WgradPlan p = wgrad_plan(n, h, w, cin, cout);
+  return p.chunks * 9LL * cin * cout + p.bias_chunks * cout;
 }
 
 int lbm_nn_conv3x3_wgrad(const float* x, const float* dy, float* dw, float* db, float* work, long long work_len,
@@ -400,17 +531,16 @@ int lbm_nn_conv3x3_wgrad(const float* x, const float* dy, float* dw, float* db, 
     return -1;
   if (work_len < lbm_nn_wgrad_workspace(n, h, w, cin, cout)) return -1;
   cudaStream_t s = (cudaStream_t)stream;
-  const long long P = (long long)n * h * w;
-  const long long chunk = 4096;
-  const int chunks = (int)((P + chunk - 1) / chunk);
-  dim3 grid(9 * (cout / 16), (cin + 31) / 32, chunks);
-  conv3x3_wgrad_part<<<grid, kThreads, 0, s>>>(x, dy, work, n, h, w, cin, cout, chunk);
+  const WgradPlan p = wgrad_plan(n, h, w, cin, cout);
   const long long nw = 9LL * cin * cout;
-  sum_parts<<<blocks(nw), 256, 0, s>>>(work, dw, nw, chunks);
+  dim3 grid((cout + 31) / 32, (cin + 31) / 32, (unsigned)p.chunks);
+  conv3x3_wgrad_seg<<<grid, kWgThreads, 0, s>>>(x, dy, work, n, h, w, cin, cout, p.per_chunk);
+  sum_parts<<<blocks(nw), 256, 0, s>>>(work, dw, nw, (int)p.chunks);
   if (db) {
-    float* bpart = work + (long long)chunks * nw;
-    colsum_part<<<dim3((cout + 127) / 128, chunks), 128, 0, s>>>(dy, bpart, P, cout, chunk);
-    sum_parts<<<blocks(cout), 256, 0, s>>>(bpart, db, cout, chunks);
+    float* bpart = work + p.chunks * nw;
+    const long long P = (long long)n * h * w;
+    colsum_part<<<dim3((cout + 31) / 32, (unsigned)p.bias_chunks), 256, 0, s>>>(dy, bpart, P, cout, kBiasChunk);
+    sum_parts<<<blocks(cout), 256, 0, s>>>(bpart, db, cout, (int)p.bias_chunks);
   }
   return status(cudaGetLastError());
 }

@@ -274,9 +274,12 @@ def fit(net, phi0, phi1, costh, target, iters, lr=2e-3, lr_end=1e-4, warmup=50, 
 
 
 def predict_all(net, phi0, phi1, costh, out):
-    """Warm-start fields for every sample, net.n at a time; out (N, h, w) device tensor.  N % net.n == 0."""
+    """Warm-start fields for every sample, net.n at a time; out (N, h, w) device tensor, N >= net.n.
+
+    A ragged tail is covered by the last net.n samples (the overlap is computed twice, with equal results)."""
     N, B = phi0.shape[0], net.n
-    assert N % B == 0
+    assert N >= B
     for lo in range(0, N, B):
+        lo = min(lo, N - B)
         net.predict(phi0[lo:lo + B], phi1[lo:lo + B], costh[lo:lo + B], out[lo:lo + B])
     return out
