@@ -223,6 +223,23 @@ int lbm_set_solid_device(lbm_ctx* ctx, const float* phi0_dev);
 int lbm_set_phase(lbm_ctx* ctx, const float* phi1_host);
 int lbm_set_phase_device(lbm_ctx* ctx, const float* phi1_dev);
 
+/* Velocity inlet at the first x column and pressure outlet at the last one,
+ * by the non-equilibrium extrapolation the paper names for velocity and
+ * pressure boundaries (Sec. 4 intro, the scheme of Guo, Zheng and Shi).
+ * After every step the populations f and g of a boundary node become those
+ * of its neighbouring column plus the difference of the equilibria at the
+ * boundary state and at the neighbour's state.  Neighbour state: phi1 = sum
+ * f, u = sum c g / rho, p from the local part of the pressure formula
+ * (p = cs2/(1 - w0) (sum_{i != 0} g_i - w0 rho |u|^2 / (1 - cs2))).
+ * mode bit 0: inlet at x = 0 with velocity u_in ([d][nz][ny] floats, host,
+ * copied; |u| < 0.5) and phase field phi_in (phi_in < 0: taken from the
+ * neighbour); bit 1: outlet at x = nx - 1 with pressure p_out, velocity and
+ * phase field taken from the neighbour.  mode 0 turns both off (the columns
+ * are half-way bounce-back walls again).  Needs a non-periodic x axis and
+ * nx >= 4; every instance of a batch shares the settings; not for
+ * lbm_create_multi contexts (LBM_EUNSUPPORTED). */
+int lbm_set_inout(lbm_ctx* ctx, int mode, const float* u_in, double phi_in, double p_out);
+
 /* Enqueue n >= 0 coupled time steps (D2Q9: one fused kernel per step;
  * D3Q19: a moment pass, phi1 = sum f and j = sum c f, then one fused kernel;
  * replayed from a captured CUDA graph where the stream allows).  Returns once

@@ -84,10 +84,13 @@ int lbm_nn_adam(float* w, float* m, float* v, const float* grad, void* w_bf16, l
 int lbm_nn_to_bf16(const float* a, void* b, long long n, void* stream);
 
 /* Warm-start field from the network output: per pixel the prediction is
- * phi1[p] + out[p][0] (out has cpad channels); per image, q = clamp(prediction,
- * 0, 1 - phi0) and field = q + lambda 4 q (1 - q), lambda chosen so that sum
- * field equals sum phi1 (the phase mass of the initial field; lambda = 0 when
- * sum 4 q (1 - q) is 0).  work: at least 192 n doubles. */
+ * phi1[p] + out[p][0] (out has cpad channels), clamped to [0, hi], hi =
+ * max(1 - phi0, 0).  Then three correction passes per image: field +=
+ * lambda b(field) with the bump b(q) = q (hi - q) / hi (0 where hi = 0) and
+ * lambda = clamp((sum phi1 - sum field) / sum b, -1, 1), which restores the
+ * phase mass of the initial field (sum phi1) while every value stays in
+ * [0, hi] (for |lambda| <= 1 the correction is monotone with fixed points 0
+ * and hi).  work: at least 192 n doubles. */
 int lbm_nn_project(const float* out, int cpad, const float* phi0, const float* phi1, float* field, double* work,
                    long long work_len, int n, int h, int w, void* stream);
 

@@ -181,6 +181,7 @@ class State:
     step: int = 0
     macro: dict = dataclasses.field(default_factory=dict)
     macro_cache: dict = dataclasses.field(default_factory=dict)
+    inout: "InOut | None" = None
 
     @property
     def shape(self):
@@ -383,14 +384,80 @@ def collide(st: State, consts, m):
     return fstar, gstar
 
 
+@dataclasses.dataclass
+class InOut:
+    """Velocity inlet at the first x column and pressure outlet at the last
+    one, by non-equilibrium extrapolation (Sec. 4 intro: the scheme of Guo,
+    Zheng and Shi for velocity or pressure boundaries).  ``u_in``: the inlet
+    velocity, a d-tuple (uniform) or an array (d,) + the shape of a column
+    ([y] in 2D, [z, y] in 3D); None leaves x = 0 a bounce-back wall, and
+    ``p_out`` None the last column; ``phi_in`` None extrapolates phi1 at the
+    inlet (zero gradient)."""
+
+    u_in: tuple | None = None
+    phi_in: float | None = None
+    p_out: float | None = None
+
+
+def inout_boundaries(st: State):
+    """Replace the post-streaming populations of the boundary columns (readings in the design doc):
+
+    f_i(x_b) = f_i(x_f) + f_i^eq(phi_b, u_b) - f_i^eq(phi_f, u_f)
+    g_i(x_b) = g_i(x_f) + g_i^eq(p_b, rho_b, u_b) - g_i^eq(p_f, rho_f, u_f)
+
+    with x_f the neighbouring column.  At x_f: phi_f = sum f_i, rho_f from the
+    densities, u_f = sum c_i g_i / rho_f and the local part of the pressure
+    formula p_f = cs2/(1 - w_0) (sum_{i != 0} g_i - w_0 rho_f |u_f|^2 / (1 - cs2)).
+    The chemical potential and the flux S enter both equilibria alike and
+    cancel.  Inlet: u_b = u_in, phi_b = phi_in (or phi_f), p_b = p_f.
+    Outlet: u_b = u_f, phi_b = phi_f, p_b = p_out."""
+    io = st.inout
+    lat, prm = st.lat, st.params
+    d, cs2, w0 = lat.d, lat.cs2, lat.w[0]
+    rho_ref = prm.rho[0] if prm.rho_ref is None else prm.rho_ref
+    nx = st.phi0.shape[-1]
+    sides = []
+    if io.u_in is not None:
+        sides.append((0, 1, "in"))
+    if io.p_out is not None:
+        sides.append((nx - 1, nx - 2, "out"))
+    new_f, new_g = st.f.copy(), st.g.copy()
+    for xb, xf, kind in sides:
+        ff, gf = st.f[..., xf], st.g[..., xf]
+        phi0_f, phi0_b = st.phi0[..., xf], st.phi0[..., xb]
+        phi_f = ff.sum(axis=0)
+        rho = lambda p0, p1: prm.rho[0] * p0 + prm.rho[1] * p1 + prm.rho[2] * (1.0 - p0 - p1)
+        rho_f = rho(phi0_f, phi_f)
+        u_f = np.stack([sum(float(ci[a]) * gf[i] for i, ci in enumerate(lat.c)) for a in range(d)]) / rho_f
+        p_f = cs2 / (1.0 - w0) * (gf[1:].sum(axis=0) - w0 * rho_f * (u_f ** 2).sum(axis=0) / (1.0 - cs2))
+        if kind == "in":
+            phi_b = phi_f if io.phi_in is None else np.full_like(phi_f, io.phi_in)
+            u_b = np.stack([np.broadcast_to(np.asarray(io.u_in[a], dtype=np.float64), phi_f.shape)
+                            for a in range(d)])
+            p_b = p_f
+        else:
+            phi_b, u_b, p_b = phi_f, u_f, np.full_like(phi_f, io.p_out)
+        rho_b = rho(phi0_b, phi_b)
+        zero = np.zeros_like(phi_f)
+        zvec = np.zeros_like(u_f)
+        new_f[..., xb] = ff + f_equilibrium(lat, phi_b, zero, u_b, 0.0) - f_equilibrium(lat, phi_f, zero, u_f, 0.0)
+        new_g[..., xb] = gf + g_equilibrium(lat, p_b, rho_b, u_b, zvec, rho_ref) - \
+            g_equilibrium(lat, p_f, rho_f, u_f, zvec, rho_ref)
+    st.f, st.g = new_f, new_g
+
+
 def step(st: State, consts=None, nsteps=1):
     """Advance the state by ``nsteps`` time steps in place; returns the state."""
     consts = constants(st.params) if consts is None else consts
+    if st.inout is not None and st.periodic[0]:
+        raise ValueError("inlet / outlet columns need a non-periodic x axis")
     for _ in range(nsteps):
         m = macroscopic(st, consts)
         fstar, gstar = collide(st, consts, m)
         st.f = stream(fstar, st.lat, st.periodic)
         st.g = stream(gstar, st.lat, st.periodic)
+        if st.inout is not None:
+            inout_boundaries(st)
         st.hist_phi1 = m["phi1"]
         st.hist_u = m["u"]
         st.hist_S = m["S"]

@@ -195,20 +195,22 @@ def adam(w, m, v, g, lr, b1, b2, eps, t):
     return w - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
-def project(out0, phi0, phi1):
+def project(out0, phi0, phi1, passes=3):
     """Warm-start field of images (leading axis n) from the network's channel 0.
 
-    q = clamp(phi1 + out0, 0, max(1 - phi0, 0)); field = q + lambda 4 q (1 - q)
-    with lambda = (sum phi1 - sum q) / sum 4 q (1 - q) per image (0 when the
-    denominator is 0), so that the field carries the initial phase mass.
+    q = clamp(phi1 + out0, 0, hi) with hi = max(1 - phi0, 0); then ``passes``
+    times per image q += lambda b(q) with b(q) = q (hi - q) / hi (0 where
+    hi = 0) and lambda = clamp((sum phi1 - sum q) / sum b, -1, 1).  For
+    |lambda| <= 1 the update is monotone in q with fixed points 0 and hi, so
+    the field stays in [0, hi] while its mass moves to that of phi1.
     """
-    q = np.clip(phi1 + out0, 0.0, None)
-    q = np.minimum(q, np.maximum(1.0 - phi0, 0.0))
-    field = np.empty_like(q)
+    hi = np.maximum(1.0 - phi0, 0.0)
+    q = np.minimum(np.clip(phi1 + out0, 0.0, None), hi)
+    safe = np.where(hi > 0, hi, 1.0)
     for i in range(q.shape[0]):
-        a, b = phi1[i].sum(), q[i].sum()
-        bump = 4.0 * q[i] * (1.0 - q[i])
-        c = bump.sum()
-        lam = (a - b) / c if c > 0 else 0.0
-        field[i] = q[i] + lam * bump
-    return field
+        for _ in range(passes):
+            bump = np.where(hi[i] > 0, q[i] * (hi[i] - q[i]) / safe[i], 0.0)
+            c = bump.sum()
+            lam = float(np.clip((phi1[i].sum() - q[i].sum()) / c, -1.0, 1.0)) if c > 0 else 0.0
+            q[i] = q[i] + lam * bump
+    return q

@@ -29,7 +29,7 @@ EXPORTS = [
     "lbm_get_instance_shape", "lbm_tune", "lbm_destroy", "lbm_set_stream",
     "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
     "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
-    "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_kernel_time_split", "lbm_observables_noalloc",
+    "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_kernel_time_split", "lbm_observables_noalloc", "lbm_set_inout",
 ]
 
 
@@ -88,6 +88,7 @@ def library():
         "lbm_set_phase": (c_int, [P, c_float_p]),
         "lbm_set_phase_device": (c_int, [P, P]),
         "lbm_step": (c_int, [P, c_int]),
+        "lbm_set_inout": (c_int, [P, c_int, c_float_p, c_double, c_double]),
         "lbm_sync": (c_int, [P]),
         "lbm_get_fields": (c_int, [P, c_float_p, c_float_p, c_float_p]),
         "lbm_get_populations": (c_int, [P, c_float_p, c_float_p]),
@@ -232,6 +233,17 @@ def lbm_set_phase_device(ctx, dev_ptr):
     _check(library().lbm_set_phase_device(ctx, c_void_p(dev_ptr)), "lbm_set_phase_device", ctx)
 
 
+def lbm_set_inout(ctx, mode, u_in=None, phi_in=-1.0, p_out=0.0):
+    """mode bit 0: velocity inlet at x = 0 (u_in: [d][nz][ny] or [d][ny]); bit 1: pressure outlet at x = nx - 1."""
+    nx, ny, nz, nb, q = lbm_get_shape(ctx)
+    d = 2 if q == 9 else 3
+    ptr = None
+    if mode & 1:
+        a = _f32(u_in, d * ny * nz)
+        ptr = _fptr(a)
+    _check(library().lbm_set_inout(ctx, mode, ptr, float(phi_in), float(p_out)), "lbm_set_inout", ctx)
+
+
 def lbm_step(ctx, n):
     _check(library().lbm_step(ctx, n), "lbm_step", ctx)
 
@@ -357,6 +369,7 @@ class Context:
     def set_solid_device(self, ptr): lbm_set_solid_device(self.ctx, ptr)
     def set_phase_device(self, ptr): lbm_set_phase_device(self.ctx, ptr)
     def step(self, n=1): lbm_step(self.ctx, n)
+    def set_inout(self, mode, u_in=None, phi_in=-1.0, p_out=0.0): lbm_set_inout(self.ctx, mode, u_in, phi_in, p_out)
     def sync(self): lbm_sync(self.ctx)
     def get_fields(self, *a): return lbm_get_fields(self.ctx, *a)
     def get_populations(self): return lbm_get_populations(self.ctx)

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v", "-I", INCLUDE]
-UNITS = ["lbm_api.cu", "lbm_d2q9.cu", "lbm_d3q19.cu", "lbm_reduce.cu", "lbm_noalloc.cu", "nn_bf16.cu"]
+UNITS = ["lbm_api.cu", "lbm_d2q9.cu", "lbm_d3q19.cu", "lbm_reduce.cu", "lbm_noalloc.cu", "lbm_bc.cu", "nn_bf16.cu"]
 
 
 def nvcc():

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -56,6 +58,10 @@ struct lbm_ctx {
   float* phi0 = nullptr;
   float* p = nullptr;
   float* mom = nullptr;        // D3Q19 moment-pass scratch
+  // inlet / outlet columns (lbm_set_inout)
+  int inout_mode = 0;
+  float inout_phi_in = -1.f, inout_p_out = 0.f;
+  float* inout_u = nullptr;    // [d][nz][ny]
   // instances of different sizes (lbm_create_multi): per-instance shape, node
   // offset into every buffer, strip; launch arguments and work items on the device
   bool multi = false;
@@ -319,19 +325,25 @@ cudaError_t launch_step(lbm_ctx* c, int from, bool observe, cudaStream_t s, cuda
     return lbm::launch_d2q9_items(c->dargs[from], c->ditems, c->nitems, c->depth, c->g_half, 0, observe, s);
   }
   const StepArgs a = step_args(c, from);
+  cudaError_t e = cudaSuccess;
   if (c->lattice == LBM_D2Q9) {
     if (mid) cudaEventRecord(mid, s);
-    return lbm::launch_d2q9_step(a, c->nbatch, observe, s);
-  }
-  cudaError_t e = lbm::launch_d3q19_moments(a, c->nbatch, s);
-  if (e != cudaSuccess) return e;
-  if (mid) {
-    e = cudaEventRecord(mid, s);
+    e = lbm::launch_d2q9_step(a, c->nbatch, observe, s);
+  } else {
+    e = lbm::launch_d3q19_moments(a, c->nbatch, s);
     if (e != cudaSuccess) return e;
+    if (mid) {
+      e = cudaEventRecord(mid, s);
+      if (e != cudaSuccess) return e;
+    }
+    // depth 1 selects the generic kernel; otherwise the pipelined one where its tensor maps exist
+    const void* maps = (c->d3maps_ok && c->depth != 1) ? c->d3maps[from] : nullptr;
+    e = lbm::launch_d3q19_step(a, c->nbatch, observe, s, maps);
   }
-  // depth 1 selects the generic kernel; otherwise the pipelined one where its tensor maps exist
-  const void* maps = (c->d3maps_ok && c->depth != 1) ? c->d3maps[from] : nullptr;
-  return lbm::launch_d3q19_step(a, c->nbatch, observe, s, maps);
+  if (e != cudaSuccess || !c->inout_mode) return e;
+  return lbm::launch_inout(c->f[1 - from], c->g[1 - from], c->g_half, c->phi0, c->dconsts, c->inout_u,
+                           c->inout_mode, c->inout_phi_in, c->inout_p_out, c->q, c->nx, c->ny, c->nz, c->nodes,
+                           c->nbatch, s);
 }
 
 int ensure_graph(lbm_ctx* c, int from) {
@@ -389,6 +401,7 @@ void free_all(lbm_ctx* c) {
   cudaFree(c->phi0);
   cudaFree(c->p);
   cudaFree(c->mom);
+  cudaFree(c->inout_u);
   cudaFree(c->dflag);
   cudaFree(c->dpart);
   cudaFree(c->dobs);
@@ -863,6 +876,32 @@ int lbm_kernel_time(lbm_ctx* c, double* total_ms, int64_t* launches) {
   if (int s = lbm_kernel_time_split(c, part, &steps)) return s;
   if (total_ms) *total_ms = part[0] + part[1];
   if (launches) *launches = steps;
+  return LBM_OK;
+}
+
+int lbm_set_inout(lbm_ctx* c, int mode, const float* u_in, double phi_in, double p_out) {
+  if (!c) return set_err(nullptr, LBM_EINVAL, "null context");
+  if (c->failed) return LBM_ESTATE;
+  if (mode < 0 || mode > 3) return set_err(c, LBM_EINVAL, "mode must be 0..3");
+  if (c->multi) return set_err(c, LBM_EUNSUPPORTED, "inlet / outlet columns need a single-size context");
+  if (mode && c->per[0]) return set_err(c, LBM_EINVAL, "inlet / outlet columns need a non-periodic x axis");
+  if (mode && c->nx < 4) return set_err(c, LBM_EINVAL, "inlet / outlet columns need nx >= 4");
+  if ((mode & 1) && !u_in) return set_err(c, LBM_EINVAL, "a velocity inlet needs its profile");
+  if (!std::isfinite(phi_in) || phi_in > 1.0 || !std::isfinite(p_out))
+    return set_err(c, LBM_EINVAL, "phi_in must be <= 1 (negative: extrapolated) and p_out finite");
+  const size_t cols = (size_t)c->ny * c->nz;
+  if (mode & 1) {
+    for (size_t i = 0; i < cols * c->d; ++i)
+      if (!std::isfinite(u_in[i]) || std::fabs(u_in[i]) > 0.5f)
+        return set_err(c, LBM_EINVAL, "inlet velocity must be finite and below 0.5 in magnitude");
+    if (!c->inout_u) LBM_CK(c, cudaMalloc(&c->inout_u, sizeof(float) * cols * c->d));
+    LBM_CK(c, cudaMemcpyAsync(c->inout_u, u_in, sizeof(float) * cols * c->d, cudaMemcpyHostToDevice, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+  }
+  c->inout_mode = mode;
+  c->inout_phi_in = phi_in < 0 ? -1.f : (float)phi_in;
+  c->inout_p_out = (float)p_out;
+  drop_graphs(c);                  // recaptured with (or without) the boundary launch
   return LBM_OK;
 }
 

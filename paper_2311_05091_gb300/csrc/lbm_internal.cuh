@@ -72,6 +72,13 @@ cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaSt
 cudaError_t launch_d2q9_items(const StepArgs* args, const int4* items, int nitems, int depth, int g_half, int grid,
                               bool observe, cudaStream_t s);
 
+// Velocity inlet (mode bit 0, x = 0) and pressure outlet (bit 1, x = nx - 1)
+// by non-equilibrium extrapolation, applied to the streamed populations of
+// every instance; u_in: [d][nz][ny] inlet velocity, phi_in < 0 extrapolates phi1.
+cudaError_t launch_inout(float* f, void* g, int g_half, const float* phi0, const InstanceConsts* consts,
+                         const float* u_in, int mode, float phi_in, float p_out, int q, int nx, int ny, int nz,
+                         long long nodes, int nbatch, cudaStream_t s);
+
 // 3D lattices (D3Q19, D3Q15 by q) share these launchers.
 cudaError_t launch_d3q19_init(const float* phi0, const float* phi1, float* f, void* g, int g_half,
                               float* hist, const InstanceConsts* consts, int nx, int ny, int nz,

@@ -21,6 +21,7 @@
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kProjectPasses = 3;   // mass-correction passes of lbm_nn_project
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -415,20 +416,32 @@ __global__ void to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__
   if (i < n) b[i] = __float2bfloat16_rn(a[i]);
 }
 
-// warm-start projection, pass 1: per image, sums of phi1 (target mass), of the clamped prediction
-// q = clamp(phi1 + out[p][0]) and of its interface weight 4 q (1 - q)
-__global__ void project_sums(const float* __restrict__ out, int cpad, const float* __restrict__ phi0,
+// warm-start projection.  hi = max(1 - phi0, 0); the bump b(q) = q (hi - q) / hi (0 where hi = 0) vanishes at
+// both bounds, and for |lambda| <= 1 the map q -> q + lambda b(q) is monotone on [0, hi] with fixed points 0 and
+// hi, so a correction step never leaves the bounds.
+__device__ __forceinline__ float proj_bump(float q, float hi) { return hi > 0.f ? q * (hi - q) / hi : 0.f; }
+
+// field = clamp(phi1 + out[p][0], 0, hi)
+__global__ void project_init(const float* __restrict__ out, int cpad, const float* __restrict__ phi0,
+                             const float* __restrict__ phi1, float* __restrict__ field, long long n) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const float hi = fmaxf(1.f - phi0[p], 0.f);
+  field[p] = fminf(fmaxf(phi1[p] + out[p * cpad], 0.f), hi);
+}
+
+// per image and part: sums of phi1 (target mass), of the field and of its bump
+__global__ void project_sums(const float* __restrict__ field, const float* __restrict__ phi0,
                              const float* __restrict__ phi1, double* __restrict__ sums, long long hw) {
   __shared__ double s[3][kThreads];
   const int img = blockIdx.y;
   double a = 0.0, b = 0.0, c = 0.0;
   for (long long k = (long long)blockIdx.x * kThreads + threadIdx.x; k < hw; k += (long long)gridDim.x * kThreads) {
     const long long p = img * hw + k;
-    const float hi = 1.f - phi0[p];
-    const float q = fminf(fmaxf(phi1[p] + out[p * cpad], 0.f), fmaxf(hi, 0.f));
+    const float q = field[p];
     a += phi1[p];
     b += q;
-    c += 4.0 * q * (1.0 - q);
+    c += proj_bump(q, fmaxf(1.f - phi0[p], 0.f));
   }
   s[0][threadIdx.x] = a;
   s[1][threadIdx.x] = b;
@@ -443,9 +456,8 @@ __global__ void project_sums(const float* __restrict__ out, int cpad, const floa
     for (int j = 0; j < 3; ++j) sums[((long long)img * gridDim.x + blockIdx.x) * 3 + j] = s[j][0];
 }
 
-// pass 2: field = q + lambda 4 q (1 - q) with lambda fixing the image's phi1 mass
-__global__ void project_apply(const float* __restrict__ out, int cpad, const float* __restrict__ phi0,
-                              const float* __restrict__ phi1, const double* __restrict__ sums, int parts,
+// field += lambda b(field), lambda = clamp((sum phi1 - sum field) / sum b, -1, 1) per image
+__global__ void project_apply(const float* __restrict__ phi0, const double* __restrict__ sums, int parts,
                               float* __restrict__ field, long long hw) {
   const int img = blockIdx.y;
   double a = 0.0, b = 0.0, c = 0.0;
@@ -454,12 +466,11 @@ __global__ void project_apply(const float* __restrict__ out, int cpad, const flo
     b += sums[((long long)img * parts + k) * 3 + 1];
     c += sums[((long long)img * parts + k) * 3 + 2];
   }
-  const float lam = c > 0.0 ? (float)((a - b) / c) : 0.f;
+  const float lam = c > 0.0 ? (float)fmin(1.0, fmax(-1.0, (a - b) / c)) : 0.f;
   for (long long k = (long long)blockIdx.x * kThreads + threadIdx.x; k < hw; k += (long long)gridDim.x * kThreads) {
     const long long p = img * hw + k;
-    const float hi = fmaxf(1.f - phi0[p], 0.f);
-    const float q = fminf(fmaxf(phi1[p] + out[p * cpad], 0.f), hi);
-    field[p] = q + lam * 4.f * q * (1.f - q);
+    const float q = field[p];
+    field[p] = q + lam * proj_bump(q, fmaxf(1.f - phi0[p], 0.f));
   }
 }
 
@@ -622,8 +633,11 @@ int lbm_nn_project(const float* out, int cpad, const float* phi0, const float* p
   if (work_len < 3LL * parts * n) return -1;
   const long long hw = (long long)h * w;
   cudaStream_t s = (cudaStream_t)stream;
-  project_sums<<<dim3(parts, n), kThreads, 0, s>>>(out, cpad, phi0, phi1, work, hw);
-  project_apply<<<dim3(parts, n), kThreads, 0, s>>>(out, cpad, phi0, phi1, work, parts, field, hw);
+  project_init<<<blocks(n * hw), 256, 0, s>>>(out, cpad, phi0, phi1, field, n * hw);
+  for (int pass = 0; pass < kProjectPasses; ++pass) {
+    project_sums<<<dim3(parts, n), kThreads, 0, s>>>(field, phi0, phi1, work, hw);
+    project_apply<<<dim3(parts, n), kThreads, 0, s>>>(phi0, work, parts, field, hw);
+  }
   return status(cudaGetLastError());
 }
 

@@ -199,12 +199,24 @@ def test_projection_restores_mass_and_bounds():
     n, h, w = 3, 16, 12
     phi0 = np.clip(r.normal(0, 0.4, (n, h, w)), 0, 1)
     phi1 = np.clip(r.uniform(0, 1, (n, h, w)), 0, 1 - phi0)
-    out0 = r.normal(0, 0.3, (n, h, w))
-    field = onn.project(out0, phi0, phi1)
-    for i in range(n):
-        assert np.isclose(field[i].sum(), phi1[i].sum(), rtol=1e-13)
+    hi = 1 - phi0
+    for scale, bias in ((0.3, 0.0), (0.2, 0.15), (0.2, -0.15)):
+        out0 = r.normal(bias, scale, (n, h, w))
+        field = onn.project(out0, phi0, phi1)
+        assert field.min() >= 0.0 and np.all(field <= hi + 1e-15)
+        for i in range(n):
+            assert np.isclose(field[i].sum(), phi1[i].sum(), rtol=1e-6), (scale, bias)
     # an exact prediction (in range, right mass) is returned unchanged
     np.testing.assert_allclose(onn.project(np.zeros_like(phi1), phi0, phi1), phi1, atol=1e-15)
-    # a prediction clamped everywhere to 0 or 1 has no interface weight: lambda = 0
-    hard = onn.project(np.where(phi1 > 0.5, 5.0, -5.0), np.zeros_like(phi0), phi1)
-    assert set(np.unique(hard)) <= {0.0, 1.0}
+    # a prediction clamped everywhere to 0 or hi has no room to move: the correction vanishes
+    hard = onn.project(np.where(phi1 > 0.5, 5.0, -5.0), phi0, phi1)
+    assert np.all((hard == 0.0) | np.isclose(hard, hi))
+
+
+def test_projection_update_is_monotone_for_bounded_lambda():
+    hi = 0.8
+    q = np.linspace(0.0, hi, 2001)
+    for lam in (-1.0, -0.5, 0.5, 1.0):
+        v = q + lam * q * (hi - q) / hi
+        assert np.all(np.diff(v) >= -1e-15) and v[0] == 0.0 and np.isclose(v[-1], hi) and v.min() >= 0 \
+            and v.max() <= hi + 1e-15
