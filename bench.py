@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--ws-every", type=int, default=250, help="warm start: contact-angle sampling interval")
     ap.add_argument("--ws-lr", type=float, default=2e-3)
     ap.add_argument("--ws-save", default=None, help="warm start: write the trained weights (.npz) here")
+    ap.add_argument("--ws-load", default=None, help="warm start: evaluate these weights (.npz) instead of training")
+    ap.add_argument("--ws-window", type=int, default=8000,
+                    help="warm start: steps the warm-started runs go on for the time to 0.5 deg")
     return ap.parse_args()
 
 
@@ -633,37 +636,11 @@ def _ws_theta(L, ctx, s, lo, i):
         return float("nan")
 
 
-def run_warmstart(args):
-    """Learned warm start (not in the paper), measured end to end on one GPU.
-
-    Labels: the plain method run for ``ws_label_steps`` steps on training
-    samples of the batched distribution at 256^2 (synthetic.workloads.
-    warmstart_set).  Training: the U-Net of paper_2311_05091_gb300.warmstart
-    on those labels, every forward and backward operation in the library's
-    BF16 tensor-core kernels.  Evaluation on held-out seeds: each sample runs
-    the plain method from its initial field for ws_label_steps steps (the
-    reference, theta sampled every ws_every steps) and, separately, from the
-    warm-start field for ws_relax_steps steps.  Reported: relative L2 error of
-    c against the reference for the initial field, the plain run after
-    ws_relax_steps, the warm-start field and the warm start after
-    ws_relax_steps; the same for the contact angle; the steps (and time) each
-    form needs to come within 0.5 deg of the reference angle.
-    """
+def _ws_train(args, L, net, train, stream, dev, todev, T, n, e0, e1):
+    """Labels by the plain method, then training of ``net`` on them (every operation in the library's kernels)."""
     import numpy as np
     import torch
-    from paper_2311_05091_gb300 import _lbm as L
-    from paper_2311_05091_gb300.warmstart import WarmStartNet, fit, predict_all
-    from synthetic.workloads import warmstart_set
-    n = args.size or 256
-    T, K, every, B = args.ws_label_steps, args.ws_relax_steps, args.ws_every, args.ws_batch
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
-    L.library()
-    t0 = time.time()
-    train = warmstart_set(range(100000, 100000 + args.ws_train), n)
-    ev = warmstart_set(range(200000, 200000 + args.ws_eval), n)
-    log(f"warm start: samples generated in {time.time() - t0:.1f} s")
+    from paper_2311_05091_gb300.warmstart import fit
     # -- labels ---------------------------------------------------------------------------
     t0 = time.time()
     target = np.empty_like(train["phi1"])
@@ -681,13 +658,10 @@ def run_warmstart(args):
     bad = ~np.isfinite(target).all(axis=(1, 2))
     log(f"warm start: {args.ws_train} labels x {T} steps in {label_s:.1f} s ({int(bad.sum())} non-finite)")
     keep = np.flatnonzero(~bad)
-    todev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     p0, p1, tg = todev(train["phi0"][keep]), todev(train["phi1"][keep]), todev(target[keep])
     ct = todev(np.cos(np.radians(train["theta_deg"][keep])).astype(np.float32))
     # -- training ---------------------------------------------------------------------------
-    net = WarmStartNet(n=B, h=n, w=n, seed=0)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.time()
     e0.record(stream)
     curve = fit(net, p0, p1, ct, tg, args.ws_iters, lr=args.ws_lr, log_every=100)
@@ -701,6 +675,51 @@ def run_warmstart(args):
         np.savez(args.ws_save, widths=np.array(st["widths"]), **{f"W{k}": W for k, W in enumerate(st["W"])},
                  **{f"b{k}": b for k, b in enumerate(st["b"])})
     del p0, p1, tg, ct
+    return label_s, train_ms, curve, int(keep.size)
+
+
+def run_warmstart(args):
+    """Learned warm start (not in the paper), measured end to end on one GPU.
+
+    Labels: the plain method run for ``ws_label_steps`` steps on training
+    samples of the batched distribution at 256^2 (synthetic.workloads.
+    warmstart_set).  Training: the U-Net of paper_2311_05091_gb300.warmstart
+    on those labels, every forward and backward operation in the library's
+    BF16 tensor-core kernels.  Evaluation on held-out seeds: each sample runs
+    the plain method from its initial field for ws_label_steps steps (the
+    reference, theta sampled every ws_every steps) and, separately, from the
+    warm-start field for ws_window steps.  Reported: relative L2 error of c
+    against the reference for the initial field, the plain run after
+    ws_relax_steps, the warm-start field and the warm start after
+    ws_relax_steps; the same for the contact angle; the time each form needs
+    to come within 0.5 deg of the reference angle (a warm run that does not
+    get there within the window counts as never), and their ratio per
+    geometry, whose median is the line's value.
+    """
+    import numpy as np
+    import torch
+    from paper_2311_05091_gb300 import _lbm as L
+    from paper_2311_05091_gb300.warmstart import WarmStartNet, predict_all
+    from synthetic.workloads import warmstart_set
+    n = args.size or 256
+    T, K, every, B = args.ws_label_steps, args.ws_relax_steps, args.ws_every, args.ws_batch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    L.library()
+    t0 = time.time()
+    train = warmstart_set(range(100000, 100000 + args.ws_train), n)
+    ev = warmstart_set(range(200000, 200000 + args.ws_eval), n)
+    log(f"warm start: samples generated in {time.time() - t0:.1f} s")
+    net = WarmStartNet(n=B, h=n, w=n, seed=0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    todev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    if args.ws_load:
+        z = np.load(args.ws_load)
+        net.load({"W": [z[f"W{k}"] for k in range(len(net.shapes))], "b": [z[f"b{k}"] for k in range(len(net.shapes))]})
+        label_s, train_ms, curve, n_train = None, None, [], 0
+    else:
+        label_s, train_ms, curve, n_train = _ws_train(args, L, net, train, stream, dev, todev, T, n, e0, e1)
     # -- evaluation -------------------------------------------------------------------------
     NE = args.ws_eval
     e0d, e1d = todev(ev["phi0"]), todev(ev["phi1"])
@@ -714,8 +733,9 @@ def run_warmstart(args):
     infer_ms_per_sample = e0.elapsed_time(e1) / NE
     warm_h = warm.cpu().numpy()
     nsamp = T // every
+    Wn = max(args.ws_window, K)
     th_plain = np.full((NE, nsamp), np.nan)
-    th_warm = np.full((NE, K // every), np.nan)
+    th_warm = np.full((NE, Wn // every), np.nan)
     c_plain_K = np.empty_like(ev["phi1"])
     c_ref = np.empty_like(ev["phi1"])
     c_warm_K = np.empty_like(ev["phi1"])
@@ -737,11 +757,18 @@ def run_warmstart(args):
                 c_plain_K[:] = ctx.get_fields()[0].reshape(NE, n, n)
         c_ref[:] = ctx.get_fields()[0].reshape(NE, n, n)
         ctx.set_phase_device(warm.data_ptr())
-        for k in range(K // every):
+        for k in range(Wn // every):
             ctx.step(every)
             for i in range(NE):
                 th_warm[i, k] = _ws_theta(L, ctx, ev, 0, i)
-        c_warm_K[:] = ctx.get_fields()[0].reshape(NE, n, n)
+            if (k + 1) * every == K:
+                bufs = (np.empty((NE, n * n), np.float32), np.empty((NE, 2, n * n), np.float32),
+                        np.empty((NE, n * n), np.float32))
+                try:
+                    ctx.get_fields(*bufs)
+                except L.LbmError:          # a diverged instance: the copies are made before the flag is read
+                    pass
+                c_warm_K[:] = bufs[0].reshape(NE, n, n)
     finally:
         ctx.close()
     rel = lambda a: np.linalg.norm((a - c_ref).reshape(NE, -1), axis=1) / np.linalg.norm(c_ref.reshape(NE, -1), axis=1)
@@ -769,30 +796,39 @@ def run_warmstart(args):
                                           ("warm_K", c_warm_K))}
     dth_plain = np.abs(th_plain[:, kK] - th_ref)
     dth_warm = np.abs(th_warm[:, kK] - th_ref)
-    t_plain_ref = T * ms_per_inst_step
-    t_warm = infer_ms_per_sample + K * ms_per_inst_step
+    # time to come within 0.5 deg of the reference angle; a warm run that does not get there within the window
+    # counts as never (infinite time), so the medians below are over every measured geometry
+    t_plain = np.where(np.isfinite(steps_plain), steps_plain * ms_per_inst_step, np.inf)[ok]
+    t_warm = np.where(np.isfinite(steps_warm), infer_ms_per_sample + steps_warm * ms_per_inst_step, np.inf)[ok]
+    speedup = t_plain / t_warm
     line = {
-        "metric": "learned warm start: error against the plain run and time per geometry",
-        "value": t_plain_ref / t_warm, "unit": "x (time of the plain reference run / warm start time)",
-        "higher_is_better": True, "n_gpus": 1, "dtype": "bf16 network (fp32 accumulate), f32 lattice",
-        "data": "synthetic", "config": {"workload": f"warm start {n}^2, batched distribution (1-6 disks, droplet, "
-                                                    f"theta 30-150)", "train": int(keep.size), "eval": NE,
-                                        "label_steps": T, "relax_steps": K, "iters": args.ws_iters, "batch": B},
-        "label_seconds": label_s, "train_ms": train_ms, "train_ms_per_iter": train_ms / args.ws_iters,
-        "loss_curve": curve[::max(1, len(curve) // 10)] + [curve[-1]],
+        "metric": "learned warm start: time to 0.5 deg of the plain run's contact angle, plain / warm-started "
+                  "(median over held-out geometries)",
+        "value": float(np.median(speedup)), "unit": "x", "higher_is_better": True, "n_gpus": 1,
+        "dtype": "bf16 network (fp32 accumulate), f32 lattice", "data": "synthetic",
+        "config": {"workload": f"warm start {n}^2, batched distribution (1-6 disks, droplet, theta 30-150)",
+                   "train": n_train, "eval": NE, "label_steps": T, "relax_steps": K, "window": Wn,
+                   "iters": args.ws_iters, "batch": B, "weights": "loaded" if args.ws_load else "trained here"},
+        "label_seconds": label_s, "train_ms": train_ms,
+        "train_ms_per_iter": None if train_ms is None else train_ms / args.ws_iters,
+        "loss_curve": (curve[::max(1, len(curve) // 10)] + [curve[-1]]) if curve else [],
         "infer_ms_per_sample": infer_ms_per_sample, "lbm_ms_per_instance_step": ms_per_inst_step,
-        "ms_plain_reference": t_plain_ref, "ms_warm_start": t_warm,
         "warm_runs_non_finite": int((~finite_warm).sum()),
-        "warm_fields_out_of_bounds": {"below_0": int(below.sum()), "above_1_minus_phi0": int(above.sum()),
-                                      "of_non_finite_runs": int(((below | above) & ~finite_warm).sum())},
+        "warm_fields_out_of_bounds": {"below_0": int(below.sum()), "above_1_minus_phi0": int(above.sum())},
         "l2_rel_median": {k: float(np.median(v[finite_warm])) for k, v in errs.items()},
         "l2_rel_mean": {k: float(np.mean(v[finite_warm])) for k, v in errs.items()},
         "theta_measured": int(ok.sum()),
-        "theta_err_deg_median": {"plain_K": med(dth_plain[ok]), "warm_K": med(dth_warm[ok])},
+        "theta_err_deg_median_at_K": {"plain": med(dth_plain[ok]), "warm": med(dth_warm[ok])},
         "theta_within_0.5_at_K": {"plain": float(np.mean(dth_plain[ok] <= 0.5)),
                                   "warm": float(np.mean(dth_warm[ok] <= 0.5))},
-        "steps_to_0.5deg_median": {"plain": med(steps_plain[ok]), "warm": med(steps_warm[ok])},
-        "warm_within_0.5deg_by_K": float(np.mean(np.isfinite(steps_warm[ok]))),
+        "reach_0.5deg": {"plain_by_label_steps": float(np.mean(np.isfinite(t_plain))),
+                         "warm_by_window": float(np.mean(np.isfinite(t_warm)))},
+        "ms_to_0.5deg_median": {"plain": float(np.median(t_plain)), "warm": float(np.median(t_warm))},
+        "steps_to_0.5deg_quartiles": {"plain": [float(x) for x in np.percentile(steps_plain[ok], [25, 50, 75])],
+                                      "warm": [float(x) for x in np.nanpercentile(
+                                          np.where(np.isfinite(steps_warm[ok]), steps_warm[ok], np.inf),
+                                          [25, 50, 75])]},
+        "speedup_quartiles": [float(x) for x in np.percentile(speedup, [25, 50, 75])],
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -301,6 +301,21 @@ int lbm_observables(lbm_ctx* ctx, int instance, lbm_obs* out);
 int lbm_observables_noalloc(const float* phi0, const float* phi1, const float* u, int d, const float* p,
                             long long n, double* out, void* stream);
 
+/* Pore-space phase fluxes for the relative permeability (Sec. 4.4, Eq. eq-Kp):
+ * over the nodes with phi0 <= 1/2 of instance `instance`, q1 = sum phi1 u_a,
+ * q2 = sum phi2 u_a (phi2 = 1 - phi0 - phi1), q = sum u_a for the velocity
+ * component a = axis, n_pore the node count and s1, s2 the saturations
+ * sum phi_p / sum (phi1 + phi2).  The relative permeability of fluid p is
+ * K_p = q_p (two-phase run) / q (single-phase run of fluid p in the same
+ * medium under the same driving).  Synchronous, float64 sums in a fixed
+ * order; uses the fields of the last step (as lbm_get_fields). */
+typedef struct {
+  double q1, q2, q;
+  double s1, s2;
+  int64_t n_pore;
+} lbm_flux;
+int lbm_phase_flux(lbm_ctx* ctx, int instance, int axis, lbm_flux* out);
+
 /* Contact angle of instance `instance` from the droplet height on the
  * vertical grid column x = column (2D).  mode 0: flat bottom wall, H measured
  * from the phi0 = 1/2 level on that column, R0 = sqrt(2 A / pi) from the area

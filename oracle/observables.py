@@ -17,6 +17,11 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   square of the half-chord term under the last root; the standard two-circle
   lens area is used: pi r^2 - r^2 acos((k^2 + r^2 - Rs^2)/(2 k r))
   - Rs^2 acos((k^2 - r^2 + Rs^2)/(2 k Rs)) + k sqrt(Rs^2 - ((k^2 - r^2 + Rs^2)/(2k))^2).
+* Relative permeability (Sec. 4.4, Eq. eq-Kp): K_p = integral over the pore
+  space (phi0 <= 1/2) of u_{x,p} over the same integral of u'_{x,p} of a
+  single-phase run.  Reading: u_{x,p} = phi_p u_x, the part of the x velocity
+  carried by fluid p, and u'_{x,p} = u_x of the run with the pore space full
+  of fluid p under the same driving.
 """
 from __future__ import annotations
 
@@ -111,3 +116,18 @@ def disk_angle(phi0, phi1, center, Rs):
     S0 = mass(phi1)
     th = _bisect(lambda t: disk_hmax(t, Rs, S0), 1e-3, math.pi - 1e-3, Hmax)
     return math.degrees(th), Hmax, S0
+
+
+def phase_flux(phi0, phi1, u, axis=0):
+    """Pore-space sums (Eq. eq-Kp): q1 = sum phi1 u_a, q2 = sum phi2 u_a, q = sum u_a, saturations."""
+    pore = phi0 <= 0.5
+    phi2 = 1.0 - phi0 - phi1
+    ua = u[axis]
+    s1, s2 = float(phi1[pore].sum()), float(phi2[pore].sum())
+    return dict(q1=float((phi1 * ua)[pore].sum()), q2=float((phi2 * ua)[pore].sum()), q=float(ua[pore].sum()),
+                s1=s1 / (s1 + s2), s2=s2 / (s1 + s2), n_pore=int(pore.sum()))
+
+
+def relative_permeability(two_phase, single_1, single_2):
+    """(K_1, K_2) from phase_flux records of the two-phase run and of single-phase runs of each fluid."""
+    return two_phase["q1"] / single_1["q"], two_phase["q2"] / single_2["q"]

@@ -30,6 +30,7 @@ EXPORTS = [
     "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
     "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
     "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_kernel_time_split", "lbm_observables_noalloc", "lbm_set_inout",
+    "lbm_phase_flux",
 ]
 
 
@@ -44,6 +45,14 @@ class lbm_obs(ctypes.Structure):
     _fields_ = [("mass1", c_double), ("mass0", c_double), ("umax", c_double), ("p_in", c_double),
                 ("p_out", c_double), ("dp", c_double), ("n_in", ctypes.c_int64), ("n_out", ctypes.c_int64),
                 ("step", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lbm_flux(ctypes.Structure):
+    _fields_ = [("q1", c_double), ("q2", c_double), ("q", c_double), ("s1", c_double), ("s2", c_double),
+                ("n_pore", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +98,7 @@ def library():
         "lbm_set_phase_device": (c_int, [P, P]),
         "lbm_step": (c_int, [P, c_int]),
         "lbm_set_inout": (c_int, [P, c_int, c_float_p, c_double, c_double]),
+        "lbm_phase_flux": (c_int, [P, c_int, c_int, ctypes.POINTER(lbm_flux)]),
         "lbm_sync": (c_int, [P]),
         "lbm_get_fields": (c_int, [P, c_float_p, c_float_p, c_float_p]),
         "lbm_get_populations": (c_int, [P, c_float_p, c_float_p]),
@@ -248,6 +258,17 @@ def lbm_step(ctx, n):
     _check(library().lbm_step(ctx, n), "lbm_step", ctx)
 
 
+def lbm_phase_flux(ctx, instance=0, axis=0) -> dict:
+    out = lbm_flux()
+    _check(library().lbm_phase_flux(ctx, instance, axis, ctypes.byref(out)), "lbm_phase_flux", ctx)
+    return out.as_dict()
+
+
+def relative_permeability(two_phase, single_1, single_2):
+    """K_1, K_2 (Eq. eq-Kp) from lbm_phase_flux records: a two-phase run and single-phase runs of each fluid."""
+    return two_phase["q1"] / single_1["q"], two_phase["q2"] / single_2["q"]
+
+
 def lbm_sync(ctx):
     _check(library().lbm_sync(ctx), "lbm_sync", ctx)
 
@@ -376,6 +397,7 @@ class Context:
     def get_state(self): return lbm_get_state(self.ctx)
     def set_state(self, image): lbm_set_state(self.ctx, image)
     def observables(self, instance=0): return lbm_observables(self.ctx, instance)
+    def phase_flux(self, instance=0, axis=0): return lbm_phase_flux(self.ctx, instance, axis)
     def set_profiling(self, enable): lbm_set_profiling(self.ctx, enable)
     def kernel_time(self): return lbm_kernel_time(self.ctx)
     def kernel_time_split(self): return lbm_kernel_time_split(self.ctx)

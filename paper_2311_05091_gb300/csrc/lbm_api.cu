@@ -1070,6 +1070,29 @@ int lbm_observables(lbm_ctx* c, int instance, lbm_obs* out) {
   return check_flag(c);
 }
 
+int lbm_phase_flux(lbm_ctx* c, int instance, int axis, lbm_flux* out) {
+  if (int s = check_ready(c, true)) return s;
+  if (!out || instance < 0 || instance >= c->nbatch || axis < 0 || axis >= c->d)
+    return set_err(c, LBM_EINVAL, "bad instance, axis or output");
+  const int nh = 1 + 2 * c->d;
+  const long long o = c->ioff[instance], n = inst_nodes(c, instance);
+  const float* h = c->hist[c->cur] + (size_t)nh * o;
+  cudaError_t e = lbm::launch_phase_flux(c->phi0 + o, h, h + (size_t)(1 + axis) * n, n, c->dpart, c->dobs, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "phase flux kernel");
+  double r[8];
+  LBM_CK(c, cudaMemcpyAsync(r, c->dobs, sizeof r, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  out->q1 = r[0];
+  out->q2 = r[1];
+  out->q = r[3];
+  out->n_pore = (int64_t)r[4];
+  const double fl = r[5] + r[6];
+  out->s1 = fl != 0.0 ? r[5] / fl : NAN;
+  out->s2 = fl != 0.0 ? r[6] / fl : NAN;
+  if (r[7] > 0) return set_err(c, LBM_EDIVERGED, "non-finite values in the fields");
+  return check_flag(c);
+}
+
 int lbm_contact_angle(lbm_ctx* c, int instance, int mode, int column, double y_c, double disk_radius,
                       double* theta_deg, double* height) {
   if (int s = check_ready(c, true)) return s;

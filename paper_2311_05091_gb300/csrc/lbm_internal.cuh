@@ -102,6 +102,9 @@ int build_d3q19_maps(const void* g, int g_half, const float* mom, const float* h
 //   [sum phi1, sum phi0, max|u|, sum p_in, n_in, sum p_out, n_out, nonfinite].
 int obs_partials_blocks(long long n);
 long long obs_partials_len(long long n);
+// Pore-space phase fluxes of one instance along one axis (ua: that velocity component), 8 doubles to out.
+cudaError_t launch_phase_flux(const float* phi0, const float* phi1, const float* ua, long long n, double* partials,
+                              double* out, cudaStream_t s);
 cudaError_t launch_observables(const float* phi0, const float* phi1, const float* u, int d,
                                const float* p, long long n, double* partials, double* out,
                                cudaStream_t s);

@@ -102,7 +102,50 @@ __global__ void __launch_bounds__(kThreads) obs_pass2(const double* __restrict__
   }
 }
 
+// Phase fluxes for the relative permeability (Sec. 4.4, Eq. eq-Kp): over the
+// pore space phi0 <= 1/2, slot 0 = sum phi1 u_a, 1 = sum phi2 u_a, 3 = sum u_a,
+// 4 = pore nodes, 5 = sum phi1, 6 = sum phi2, 7 = non-finite values (slot 2,
+// the maximum slot of block_reduce, stays 0).
+__global__ void __launch_bounds__(kThreads) flux_pass1(const float* __restrict__ phi0,
+                                                       const float* __restrict__ phi1,
+                                                       const float* __restrict__ ua, long long n,
+                                                       double* __restrict__ partials) {
+  __shared__ double sh[kThreads / 32][kRec];
+  double v[kRec] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float a0 = phi0[i], a1 = phi1[i], u = ua[i];
+    if (!isfinite(a1) || !isfinite(u)) {
+      v[7] += 1.0;
+      continue;
+    }
+    if (a0 > 0.5f) continue;
+    const double a2 = 1.0 - (double)a0 - (double)a1;
+    v[0] += (double)a1 * u;
+    v[1] += a2 * u;
+    v[3] += u;
+    v[4] += 1.0;
+    v[5] += a1;
+    v[6] += a2;
+  }
+  block_reduce(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < kRec; ++q) partials[(long long)blockIdx.x * kRec + q] = v[q];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_phase_flux(const float* phi0, const float* phi1, const float* ua, long long n, double* partials,
+                              double* out, cudaStream_t s) {
+  const int nb = obs_partials_blocks(n);
+  flux_pass1<<<nb, kThreads, 0, s>>>(phi0, phi1, ua, n, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  obs_pass2<<<1, kThreads, 0, s>>>(partials, nb, out);
+  return cudaGetLastError();
+}
 
 int obs_partials_blocks(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
