@@ -85,7 +85,7 @@ def parse():
     ap.add_argument("--tte-every", type=int, default=2500, help="contact-angle sampling interval")
     ap.add_argument("--ws-train", type=int, default=2000, help="warm start: training samples")
     ap.add_argument("--ws-eval", type=int, default=200, help="warm start: held-out samples")
-    ap.add_argument("--ws-iters", type=int, default=3000, help="warm start: training iterations")
+    ap.add_argument("--ws-iters", type=int, default=10000, help="warm start: training iterations")
     ap.add_argument("--ws-batch", type=int, default=16, help="warm start: images per training iteration")
     ap.add_argument("--ws-label-steps", type=int, default=20000, help="warm start: plain steps of the labels")
     ap.add_argument("--ws-relax-steps", type=int, default=2000, help="warm start: relaxation steps after inference")
@@ -678,6 +678,38 @@ def _ws_train(args, L, net, train, stream, dev, todev, T, n, e0, e1):
     return label_s, train_ms, curve, int(keep.size)
 
 
+def _ws_conv_roofline(B, n, stream):
+    """Tensor roofline of the dominant warm-start kernel: the forward 3x3 convolution of the finest decoder level
+    (64 -> 32 channels on B images of n^2, the largest single layer), timed alone with CUDA events (10 launches after
+    a warm-up), against the measured dense BF16 peak."""
+    import torch
+    from paper_2311_05091_gb300 import _nn
+    cin, cout = 64, 32
+    x = torch.randn(B, n, n, cin, device="cuda")
+    w = torch.randn(9, cout, cin, device="cuda").to(torch.bfloat16)
+    y = torch.empty(B, n, n, cout, device="cuda")
+    run = lambda: _nn.conv3x3(x.data_ptr(), w.data_ptr(), 0, y.data_ptr(), B, n, n, cin, cout, 1,
+                              stream.cuda_stream)
+    run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        run()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    flops = 2.0 * 9 * cin * cout * B * n * n
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, src = float(json.load(fh)["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    except Exception:
+        peak, src = 1900.0, "fallback"
+    achieved = flops / ms / 1e9
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": src,
+            "kernel": f"conv3x3_fwd<1> {cin}->{cout} on {B} x {n}^2 (mma.sync m16n8k16 BF16, FP32 accumulate)"}
+
+
 def run_warmstart(args):
     """Learned warm start (not in the paper), measured end to end on one GPU.
 
@@ -699,7 +731,7 @@ def run_warmstart(args):
     import numpy as np
     import torch
     from paper_2311_05091_gb300 import _lbm as L
-    from paper_2311_05091_gb300.warmstart import WarmStartNet, predict_all
+    from paper_2311_05091_gb300.warmstart import WarmStartNet, forward_flops, predict_all, train_flops
     from synthetic.workloads import warmstart_set
     n = args.size or 256
     T, K, every, B = args.ws_label_steps, args.ws_relax_steps, args.ws_every, args.ws_batch
@@ -771,6 +803,7 @@ def run_warmstart(args):
                 c_warm_K[:] = bufs[0].reshape(NE, n, n)
     finally:
         ctx.close()
+    conv_roof = _ws_conv_roofline(B, n, stream)
     rel = lambda a: np.linalg.norm((a - c_ref).reshape(NE, -1), axis=1) / np.linalg.norm(c_ref.reshape(NE, -1), axis=1)
     finite_warm = np.isfinite(c_warm_K).all(axis=(1, 2))
     hi = np.maximum(1.0 - ev["phi0"], 0.0)
@@ -829,6 +862,10 @@ def run_warmstart(args):
                                           np.where(np.isfinite(steps_warm[ok]), steps_warm[ok], np.inf),
                                           [25, 50, 75])]},
         "speedup_quartiles": [float(x) for x in np.percentile(speedup, [25, 50, 75])],
+        "tensor_effective_tflops": {
+            "train": None if train_ms is None else train_flops(net.widths, n, n) * B * args.ws_iters / train_ms / 1e9,
+            "inference": forward_flops(net.widths, n, n) / infer_ms_per_sample / 1e9},
+        "roofline": conv_roof,
     }
     print(json.dumps(line), flush=True)
     return 0

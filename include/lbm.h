@@ -301,7 +301,7 @@ int lbm_observables(lbm_ctx* ctx, int instance, lbm_obs* out);
 int lbm_observables_noalloc(const float* phi0, const float* phi1, const float* u, int d, const float* p,
                             long long n, double* out, void* stream);
 
-/* Pore-space phase fluxes for the relative permeability (Sec. 4.4, Eq. eq-Kp):
+/* Pore-space phase fluxes for the relative permeability (Sec. 4.6, Eq. eq-Kp):
  * over the nodes with phi0 <= 1/2 of instance `instance`, q1 = sum phi1 u_a,
  * q2 = sum phi2 u_a (phi2 = 1 - phi0 - phi1), q = sum u_a for the velocity
  * component a = axis, n_pore the node count and s1, s2 the saturations

@@ -17,7 +17,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   square of the half-chord term under the last root; the standard two-circle
   lens area is used: pi r^2 - r^2 acos((k^2 + r^2 - Rs^2)/(2 k r))
   - Rs^2 acos((k^2 - r^2 + Rs^2)/(2 k Rs)) + k sqrt(Rs^2 - ((k^2 - r^2 + Rs^2)/(2k))^2).
-* Relative permeability (Sec. 4.4, Eq. eq-Kp): K_p = integral over the pore
+* Relative permeability (Sec. 4.6, Eq. eq-Kp): K_p = integral over the pore
   space (phi0 <= 1/2) of u_{x,p} over the same integral of u'_{x,p} of a
   single-phase run.  Reading: u_{x,p} = phi_p u_x, the part of the x velocity
   carried by fluid p, and u'_{x,p} = u_x of the run with the pore space full

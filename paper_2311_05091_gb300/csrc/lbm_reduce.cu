@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) obs_pass2(const double* __restrict__
   }
 }
 
-// Phase fluxes for the relative permeability (Sec. 4.4, Eq. eq-Kp): over the
+// Phase fluxes for the relative permeability (Sec. 4.6, Eq. eq-Kp): over the
 // pore space phi0 <= 1/2, slot 0 = sum phi1 u_a, 1 = sum phi2 u_a, 3 = sum u_a,
 // 4 = pore nodes, 5 = sum phi1, 6 = sum phi2, 7 = non-finite values (slot 2,
 // the maximum slot of block_reduce, stays 0).

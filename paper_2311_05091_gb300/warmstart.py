@@ -40,6 +40,23 @@ def _p(t):
     return t.data_ptr()
 
 
+def forward_flops(widths, h, w):
+    """Multiply-add FLOPs (2 per MAC) of the network's convolutions for one h x w image."""
+    L = len(widths)
+    fl = 0
+    for k, (ci, co) in enumerate(layer_shapes(widths)):
+        lv = k // 2 if k < 2 * L else (0 if k == 2 * L + 2 * (L - 1) else L - 2 - (k - 2 * L) // 2)
+        fl += 2 * 9 * ci * co * (h >> lv) * (w >> lv)
+    return fl
+
+
+def train_flops(widths, h, w):
+    """FLOPs of one training image: forward, data gradients (every convolution but the first) and weight gradients."""
+    first = 2 * 9 * CIN * widths[0] * h * w
+    f = forward_flops(widths, h, w)
+    return 3 * f - first
+
+
 class WarmStartNet:
     """Weights, optimiser state and activation buffers for n images of size h x w."""
 

@@ -1,4 +1,4 @@
-"""Relative-permeability diagnostic (lbm_phase_flux, Sec. 4.4 Eq. eq-Kp) on the GPU."""
+"""Relative-permeability diagnostic (lbm_phase_flux, Sec. 4.6, Eq. eq-Kp) on the GPU."""
 import numpy as np
 import pytest
 

@@ -1,4 +1,4 @@
-"""Pins of the relative-permeability diagnostic (Sec. 4.4, Eq. eq-Kp)."""
+"""Pins of the relative-permeability diagnostic (Sec. 4.6, Eq. eq-Kp)."""
 import numpy as np
 
 from oracle import lbm, model
