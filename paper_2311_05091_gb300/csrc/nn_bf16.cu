@@ -387,12 +387,18 @@ __global__ void mse_residual(const float* __restrict__ out, int cpad, const floa
   if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
-__global__ void sum_double(const double* __restrict__ part, int n, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *out = s;
+// out = sum of n partials: one CTA, strided per-thread sums, then a fixed-order tree (deterministic)
+__global__ void __launch_bounds__(256) sum_double(const double* __restrict__ part, int n, double* __restrict__ out) {
+  __shared__ double s[256];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) v += part[i];
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *out = s[0];
 }
 
 // Adam with bias correction; writes the BF16 copy of the updated weights
@@ -606,7 +612,7 @@ int lbm_nn_mse_residual(const float* out, int cpad, const float* base, const flo
   if (work_len < nb) return -1;
   cudaStream_t s = (cudaStream_t)stream;
   mse_residual<<<nb, kThreads, 0, s>>>(out, cpad, base, target, dout, work, P);
-  sum_double<<<1, 32, 0, s>>>(work, nb, loss);
+  sum_double<<<1, 256, 0, s>>>(work, nb, loss);
   return status(cudaGetLastError());
 }
 
