@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--tte-steps", type=int, default=150000,
                     help="steps of the time-to-equilibrium run (disk workload; 0 skips it)")
     ap.add_argument("--tte-every", type=int, default=2500, help="contact-angle sampling interval")
+    ap.add_argument("--tune-trial", type=int, default=40,
+                    help="steps per candidate of the strip autotuner before timing (0: the library's default strip)")
     ap.add_argument("--ws-train", type=int, default=2000, help="warm start: training samples")
     ap.add_argument("--ws-eval", type=int, default=200, help="warm start: held-out samples")
     ap.add_argument("--ws-iters", type=int, default=10000, help="warm start: training iterations")
@@ -515,6 +517,8 @@ def run_gpu(args):
     ctx.set_phase(h_phi1)
     ctx.step(args.warmup)
     ctx.sync()
+    # the library's autotuner picks the strip (rows / planes per CTA) by timing; the state is restored bitwise
+    strip_tuned = ctx.tune(args.tune_trial)[0] if args.tune_trial > 0 else None
 
     # ---- device-resident timed region: K steps replayed from CUDA graphs ----
     clocks = Clocks()
@@ -578,6 +582,7 @@ def run_gpu(args):
            "thetas": [p["theta_deg"] for p in wl["params"]], "d0": wl["params"][0]["d0"], "W": 4.0,
            "lu_per_step": lu, "bytes_per_lu": spec["bytes_per_lu"],
            "l2": f"no flush: each step moves about {2 * rw:.2f} GB through HBM (> 129 MB L2)",
+           "strip_tuned": strip_tuned,
            "parallelism": f"weak, {world} x independent copies of the workload"}
     cfg["storage"] = ("NS populations FP16 (g * 2^12), CH populations and arithmetic float32" if flags
                       else "float32 populations")

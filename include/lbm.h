@@ -174,8 +174,9 @@ int lbm_create_multi(lbm_lattice lattice, int ninst, const int* nx, const int* n
 int lbm_get_instance_shape(const lbm_ctx* ctx, int instance, int* nx, int* ny, int64_t* offset);
 
 /* Launch autotuner: chooses the row strip (of every size class of a
- * multi-size context, or the context's single strip) among 4, 8, 16, 32, 64
- * by timing `trial` steps per candidate, two coordinate-descent passes.  The
+ * multi-size context, or the context's single strip) among 4, 8, 12, 16, 18,
+ * 20, 24, 32, 48, 64 by timing `trial` steps per candidate, two
+ * coordinate-descent passes.  The
  * evolving state is saved before and restored after (bitwise), so the call can
  * come at any point after lbm_set_phase.  strips_out (nbatch ints, may be
  * NULL) receives the chosen strip of each instance. */

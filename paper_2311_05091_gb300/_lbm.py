@@ -385,6 +385,7 @@ class Context:
 
     def set_stream(self, handle): lbm_set_stream(self.ctx, handle)
     def set_launch(self, strip, depth=0): lbm_set_launch(self.ctx, strip, depth)
+    def tune(self, trial=10): return lbm_tune(self.ctx, trial, lbm_get_shape(self.ctx)[3])
     def set_solid(self, phi0): lbm_set_solid(self.ctx, phi0)
     def set_phase(self, phi1): lbm_set_phase(self.ctx, phi1)
     def set_solid_device(self, ptr): lbm_set_solid_device(self.ctx, ptr)

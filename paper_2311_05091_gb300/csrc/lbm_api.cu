@@ -743,13 +743,16 @@ int lbm_tune(lbm_ctx* c, int trial, int* strips_out) {
     if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
     return r;
   };
-  static const int cand[] = {4, 8, 16, 32, 64};
+  // powers of two plus the steps between 12 and 24 rows: on GB300 the best D2Q9 strip of a 1024^2 x 5 batch is 18
+  // (its CTA count is three full waves of 152 SMs x 5 CTAs), 1.8 % faster than 16
+  static const int cand[] = {4, 8, 12, 16, 18, 20, 24, 32, 48, 64};
+  constexpr int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
   for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
     for (int cl = 0; cl < (int)classes.size() && e == cudaSuccess; ++cl) {
       const int rows = c->multi ? c->iny[classes[cl][0]] : (c->lattice == LBM_D2Q9 ? c->ny : c->nz);
       int best = c->multi ? c->istrip[classes[cl][0]] : c->strip;
       float best_ms = 1e30f;
-      for (int sidx = 0; sidx < 5 && e == cudaSuccess; ++sidx) {
+      for (int sidx = 0; sidx < ncand && e == cudaSuccess; ++sidx) {
         const int strip = cand[sidx];
         if (strip > rows && sidx > 0 && cand[sidx - 1] >= rows) break;   // larger strips change nothing
         float ms = 0.f;
