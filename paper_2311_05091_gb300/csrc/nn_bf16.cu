@@ -160,8 +160,7 @@ constexpr int fwd_smem_bytes() {
 // memory as BF16 (zero outside the image), so that every mma fragment is one
 // aligned 32-bit shared load; warp (ky, kx) then multiplies dy^T (32 x 64)
 // by its shifted x (64 x 32).  Rows are padded to 72 elements (36 words), so
-// the 32 lanes of a fragment load hit 32 different banks; the staging stores
-// pairs of pixels as 32-bit words, 32 consecutive words of a row per warp.
+// the 32 lanes of a fragment load hit 32 different banks.
 // grid (ceil(cout / 32), ceil(cin / 32), chunks), 288 threads.
 // ---------------------------------------------------------------------------
 constexpr int kSeg = 64, kPad = 72, kWgThreads = 288;
@@ -191,38 +190,37 @@ __global__ void __launch_bounds__(kWgThreads) conv3x3_wgrad_seg(const float* __r
     const int y = (int)((sg / spr) % h);
     const int x0 = (int)(sg % spr) * kSeg;
     __syncthreads();                                           // the previous segment's fragments are consumed
-    // dy^T: a thread takes two neighbouring pixels and four channels and writes four 32-bit pairs, one per
-    // channel row; a warp covers 32 pixel pairs of one channel group, i.e. 32 consecutive words of each row
-    for (int e = threadIdx.x; e < (kSeg / 2) * 8; e += kWgThreads) {
-      const int pp = e & 31, c4 = (e >> 5) * 4;
-      const int j0 = 2 * pp;
-      float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-      if (co0 + c4 < cout) {
-        const float* src = dy + (((long long)img * h + y) * w + x0 + j0) * cout + co0 + c4;
-        if (x0 + j0 < w) v0 = *reinterpret_cast<const float4*>(src);
-        if (x0 + j0 + 1 < w) v1 = *reinterpret_cast<const float4*>(src + cout);
-      }
-      *reinterpret_cast<uint32_t*>(&sdy[c4][j0]) = pack_bf16(v0.x, v1.x);
-      *reinterpret_cast<uint32_t*>(&sdy[c4 + 1][j0]) = pack_bf16(v0.y, v1.y);
-      *reinterpret_cast<uint32_t*>(&sdy[c4 + 2][j0]) = pack_bf16(v0.z, v1.z);
-      *reinterpret_cast<uint32_t*>(&sdy[c4 + 3][j0]) = pack_bf16(v0.w, v1.w);
+    // dy^T: 64 pixels x 32 channels as 8 float4 per pixel
+    for (int e = threadIdx.x; e < kSeg * 8; e += kWgThreads) {
+      const int j = e >> 3, c4 = (e & 7) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (x0 + j < w && co0 + c4 < cout)
+        v = *reinterpret_cast<const float4*>(dy + (((long long)img * h + y) * w + x0 + j) * cout + co0 + c4);
+      sdy[c4][j] = __float2bfloat16_rn(v.x);
+      sdy[c4 + 1][j] = __float2bfloat16_rn(v.y);
+      sdy[c4 + 2][j] = __float2bfloat16_rn(v.z);
+      sdy[c4 + 3][j] = __float2bfloat16_rn(v.w);
     }
-    // x^T, copy k (column offset kx = k): sx[k][r][c][j] = x at row y + r - 1, column x0 + j + k - 1, built the
-    // same way (two pixels, four channels per thread, 32-bit stores); rows and columns outside the image are 0
-    for (int e = threadIdx.x; e < 9 * (kSeg / 2) * 8; e += kWgThreads) {
-      const int pp = e & 31, c4 = ((e >> 5) & 7) * 4, kr = e >> 8;      // kr = 3 k + r
-      const int k = kr / 3, r = kr % 3;
-      const int j0 = 2 * pp, yy = y + r - 1, xc = x0 + j0 + k - 1;
-      float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-      if (yy >= 0 && yy < h && ci0 + c4 < cin) {
-        const float* src = x + (((long long)img * h + yy) * w + xc) * cin + ci0 + c4;
-        if (xc >= 0 && xc < w) v0 = *reinterpret_cast<const float4*>(src);
-        if (xc + 1 >= 0 && xc + 1 < w) v1 = *reinterpret_cast<const float4*>(src + cin);
+    // x^T: rows y - 1 .. y + 1, columns x0 - 1 .. x0 + 64, 32 channels; column xc goes to copy kx at xc - x0 - kx + 1
+    for (int e = threadIdx.x; e < 3 * (kSeg + 2) * 8; e += kWgThreads) {
+      const int r = e / ((kSeg + 2) * 8), rem = e % ((kSeg + 2) * 8);
+      const int jc = rem >> 3, c4 = (rem & 7) * 4;             // jc = xc - x0 + 1 in 0 .. 65
+      const int yy = y + r - 1, xc = x0 + jc - 1;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (yy >= 0 && yy < h && xc >= 0 && xc < w && ci0 + c4 < cin)
+        v = *reinterpret_cast<const float4*>(x + (((long long)img * h + yy) * w + xc) * cin + ci0 + c4);
+      const __nv_bfloat16 b0 = __float2bfloat16_rn(v.x), b1 = __float2bfloat16_rn(v.y);
+      const __nv_bfloat16 b2 = __float2bfloat16_rn(v.z), b3 = __float2bfloat16_rn(v.w);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int j = jc - k;
+        if (j >= 0 && j < kSeg) {
+          sx[k][r][c4][j] = b0;
+          sx[k][r][c4 + 1][j] = b1;
+          sx[k][r][c4 + 2][j] = b2;
+          sx[k][r][c4 + 3][j] = b3;
+        }
       }
-      *reinterpret_cast<uint32_t*>(&sx[k][r][c4][j0]) = pack_bf16(v0.x, v1.x);
-      *reinterpret_cast<uint32_t*>(&sx[k][r][c4 + 1][j0]) = pack_bf16(v0.y, v1.y);
-      *reinterpret_cast<uint32_t*>(&sx[k][r][c4 + 2][j0]) = pack_bf16(v0.z, v1.z);
-      *reinterpret_cast<uint32_t*>(&sx[k][r][c4 + 3][j0]) = pack_bf16(v0.w, v1.w);
     }
     __syncthreads();
 #pragma unroll
