@@ -156,6 +156,27 @@ enum {
 int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask,
                   int nbatch, const lbm_params* params, int flags, lbm_ctx** out);
 
+/* Device-memory callbacks for lbm_create_alloc: alloc returns a device
+ * pointer to `bytes` bytes usable on `stream` (NULL on failure, which the
+ * creating call reports as LBM_ENOMEM); free takes back a pointer alloc
+ * returned, with its size and the context's stream.  `user` is passed
+ * through.  Both are called from the thread that makes the library call. */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*lbm_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* lbm_create_ex whose device buffers come from the caller's allocator (for
+ * example a framework's caching allocator, so that the simulation's memory is
+ * accounted and reused with the caller's) and whose work runs on the caller's
+ * stream (cudaStream_t; NULL: the library creates its own, as lbm_create).
+ * alloc and free: both or neither (neither: cudaMalloc / cudaFree).  Every
+ * device allocation of the context goes through alloc (populations, history,
+ * fields, scratch of the diagnostics, the autotuner's save area, the inlet
+ * profile); before handing memory back through free the library waits for
+ * the context's stream, so the caller may reuse it on any stream at once. */
+int lbm_create_alloc(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, int nbatch,
+                     const lbm_params* params, int flags, void* stream, lbm_alloc_fn alloc, lbm_free_fn free_fn,
+                     void* user, lbm_ctx** out);
+
 /* ninst independent D2Q9 instances of different sizes nx[k] x ny[k] (same
  * periodicity), advanced together by one persistent launch per step that
  * walks a work list of (instance, 128-column tile, row strip) items; no

@@ -30,8 +30,12 @@ EXPORTS = [
     "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
     "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
     "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_kernel_time_split", "lbm_observables_noalloc", "lbm_set_inout",
-    "lbm_phase_flux",
+    "lbm_phase_flux", "lbm_create_alloc",
 ]
+
+# device-memory callbacks of lbm_create_alloc
+lbm_alloc_fn = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+lbm_free_fn = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
 
 
 class lbm_params(ctypes.Structure):
@@ -99,6 +103,8 @@ def library():
         "lbm_step": (c_int, [P, c_int]),
         "lbm_set_inout": (c_int, [P, c_int, c_float_p, c_double, c_double]),
         "lbm_phase_flux": (c_int, [P, c_int, c_int, ctypes.POINTER(lbm_flux)]),
+        "lbm_create_alloc": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(lbm_params), c_int, P,
+                                     lbm_alloc_fn, lbm_free_fn, P, ctypes.POINTER(P)]),
         "lbm_sync": (c_int, [P]),
         "lbm_get_fields": (c_int, [P, c_float_p, c_float_p, c_float_p]),
         "lbm_get_populations": (c_int, [P, c_float_p, c_float_p]),
@@ -174,6 +180,36 @@ def lbm_create_ex(lattice, nx, ny, nz, periodic_mask, params_list, flags):
     _check(library().lbm_create_ex(lattice, nx, ny, nz, periodic_mask, len(params_list), arr, flags,
                                    ctypes.byref(out)), "lbm_create_ex")
     return out
+
+
+def lbm_create_alloc(lattice, nx, ny, nz, periodic_mask, params_list, flags, stream, allocator):
+    arr = (lbm_params * len(params_list))(*params_list)
+    out = c_void_p()
+    _check(library().lbm_create_alloc(lattice, nx, ny, nz, periodic_mask, len(params_list), arr, flags, stream,
+                                      allocator.alloc, allocator.free, None, ctypes.byref(out)), "lbm_create_alloc")
+    return out
+
+
+class TorchAllocator:
+    """Device memory of a context from PyTorch's caching allocator (lbm_create_alloc callbacks).
+
+    Keep the object alive as long as the context: the context holds the C callbacks it wraps."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+            except Exception:        # reported by the library as LBM_ENOMEM
+                return None
+
+        def _free(ptr, nbytes, stream, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = lbm_alloc_fn(_alloc)
+        self.free = lbm_free_fn(_free)
 
 
 def lbm_create_multi(lattice, sizes, periodic_mask, params_list, flags=0):
@@ -353,10 +389,15 @@ def lbm_strerror(status) -> str:
 class Context:
     """Owns one lbm_ctx; each method forwards to the C call of the same name."""
 
-    def __init__(self, lattice, nx, ny, nz=1, periodic=(True, True, True), params=None, batch=None, flags=0):
+    def __init__(self, lattice, nx, ny, nz=1, periodic=(True, True, True), params=None, batch=None, flags=0,
+                 allocator=None, stream=None):
         mask = sum(bit for bit, on in zip((1, 2, 4), periodic) if on)
         self.shape = (nx, ny, nz)
-        if flags:
+        self._allocator = allocator          # the callbacks must outlive the context
+        if allocator is not None:
+            plist = batch if batch is not None else [params if params is not None else lbm_default_params()]
+            self.ctx = lbm_create_alloc(lattice, nx, ny, nz, mask, plist, flags, stream, allocator)
+        elif flags:
             plist = batch if batch is not None else [params if params is not None else lbm_default_params()]
             self.ctx = lbm_create_ex(lattice, nx, ny, nz, mask, plist, flags)
         elif batch is not None:

@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include <cmath>
+#include <unordered_map>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -58,6 +59,11 @@ struct lbm_ctx {
   float* phi0 = nullptr;
   float* p = nullptr;
   float* mom = nullptr;        // D3Q19 moment-pass scratch
+  // caller's device-memory callbacks (lbm_create_alloc); NULL: cudaMalloc / cudaFree
+  lbm_alloc_fn alloc_fn = nullptr;
+  lbm_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  std::unordered_map<void*, size_t> alloc_bytes;
   // inlet / outlet columns (lbm_set_inout)
   int inout_mode = 0;
   float inout_phi_in = -1.f, inout_p_out = 0.f;
@@ -101,6 +107,38 @@ int set_err(lbm_ctx* c, int code, const char* fmt, const char* a = "", const cha
 int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
   if (c) c->failed = true;
   return set_err(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Device memory of a context: the caller's callbacks when it gave some, else the runtime.  Memory returned to a
+// caller's pool may be reused at once on other streams, so the context's stream is drained first.
+cudaError_t dev_alloc(lbm_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (!c->alloc_fn) return cudaMalloc(p, bytes);
+  *p = c->alloc_fn(bytes, c->stream, c->alloc_user);
+  if (!*p) return cudaErrorMemoryAllocation;
+  c->alloc_bytes[*p] = bytes;
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t dalloc(lbm_ctx* c, T** p, size_t bytes) {
+  void* v = nullptr;
+  const cudaError_t e = dev_alloc(c, &v, bytes);
+  *p = static_cast<T*>(v);
+  return e;
+}
+
+void dev_free(lbm_ctx* c, void* p) {
+  if (!p) return;
+  if (!c->free_fn) {
+    cudaFree(p);
+    return;
+  }
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  auto it = c->alloc_bytes.find(p);
+  const size_t bytes = it == c->alloc_bytes.end() ? 0 : it->second;
+  if (it != c->alloc_bytes.end()) c->alloc_bytes.erase(it);
+  c->free_fn(p, bytes, c->stream, c->alloc_user);
 }
 
 #define LBM_CK(c, call)                                       \
@@ -305,10 +343,10 @@ cudaError_t upload_multi(lbm_ctx* c) {
   };
   std::stable_sort(items.begin(), items.end(), [&](const int4& a, const int4& b) { return work(a) > work(b); });
   if ((int)items.size() > c->items_cap) {
-    cudaFree(c->ditems);
+    dev_free(c, c->ditems);
     c->ditems = nullptr;
     c->items_cap = 0;
-    cudaError_t e = cudaMalloc(&c->ditems, sizeof(int4) * items.size());
+    cudaError_t e = dalloc(c, &c->ditems, sizeof(int4) * items.size());
     if (e != cudaSuccess) return e;
     c->items_cap = (int)items.size();
   }
@@ -391,21 +429,21 @@ void free_all(lbm_ctx* c) {
   c->ev.clear();
   for (int i = 0; i < 2; ++i) {
     if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
-    cudaFree(c->f[i]);
-    cudaFree(c->g[i]);
-    cudaFree(c->hist[i]);
+    dev_free(c, c->f[i]);
+    dev_free(c, c->g[i]);
+    dev_free(c, c->hist[i]);
   }
-  cudaFree(c->dargs[0]);
-  cudaFree(c->dargs[1]);
-  cudaFree(c->ditems);
-  cudaFree(c->phi0);
-  cudaFree(c->p);
-  cudaFree(c->mom);
-  cudaFree(c->inout_u);
-  cudaFree(c->dflag);
-  cudaFree(c->dpart);
-  cudaFree(c->dobs);
-  cudaFree(c->dconsts);
+  dev_free(c, c->dargs[0]);
+  dev_free(c, c->dargs[1]);
+  dev_free(c, c->ditems);
+  dev_free(c, c->phi0);
+  dev_free(c, c->p);
+  dev_free(c, c->mom);
+  dev_free(c, c->inout_u);
+  dev_free(c, c->dflag);
+  dev_free(c, c->dpart);
+  dev_free(c, c->dobs);
+  dev_free(c, c->dconsts);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -501,9 +539,12 @@ int lbm_default_params(lbm_params* p) {
 }
 
 static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const int* nys, int nz, int periodic_mask,
-                       const lbm_params* params, int flags, bool multi, lbm_ctx** out) {
+                       const lbm_params* params, int flags, bool multi, lbm_ctx** out, void* stream = nullptr,
+                       lbm_alloc_fn alloc_fn = nullptr, lbm_free_fn free_fn = nullptr, void* alloc_user = nullptr) {
   if (!out) return set_err(nullptr, LBM_EINVAL, "out is NULL");
   *out = nullptr;
+  if ((alloc_fn == nullptr) != (free_fn == nullptr))
+    return set_err(nullptr, LBM_EINVAL, "give both device-memory callbacks or neither");
   if (flags & ~LBM_STORE_G_F16) return set_err(nullptr, LBM_EINVAL, "unknown flag");
   if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19 && lattice != LBM_D3Q15)
     return set_err(nullptr, LBM_EINVAL, "unknown lattice");
@@ -575,28 +616,35 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
   const size_t pop = sizeof(float) * (size_t)c->q * total;
   const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * total;
   const size_t fld = sizeof(float) * (size_t)total;
+  c->alloc_fn = alloc_fn;
+  c->free_fn = free_fn;
+  c->alloc_user = alloc_user;
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-    e = cudaMalloc(&c->f[i], pop);
-    if (e == cudaSuccess) e = cudaMalloc(&c->g[i], pop / sizeof(float) * c->g_elem);
-    if (e == cudaSuccess) e = cudaMalloc(&c->hist[i], his);
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) c->own_stream = true;
   }
-  if (e == cudaSuccess) e = cudaMalloc(&c->phi0, fld);
-  if (e == cudaSuccess) e = cudaMalloc(&c->p, fld);
-  if (e == cudaSuccess && is3d) e = cudaMalloc(&c->mom, 3 * fld);
-  if (e == cudaSuccess) e = cudaMalloc(&c->dflag, sizeof(unsigned int));
-  if (e == cudaSuccess) e = cudaMalloc(&c->dpart, sizeof(double) * lbm::obs_partials_len(max_nodes));
-  if (e == cudaSuccess) e = cudaMalloc(&c->dobs, sizeof(double) * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&c->dconsts, sizeof(InstanceConsts) * nbatch);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) c->own_stream = true;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = dalloc(c, &c->f[i], pop);
+    if (e == cudaSuccess) e = dalloc(c, &c->g[i], pop / sizeof(float) * c->g_elem);
+    if (e == cudaSuccess) e = dalloc(c, &c->hist[i], his);
+  }
+  if (e == cudaSuccess) e = dalloc(c, &c->phi0, fld);
+  if (e == cudaSuccess) e = dalloc(c, &c->p, fld);
+  if (e == cudaSuccess && is3d) e = dalloc(c, &c->mom, 3 * fld);
+  if (e == cudaSuccess) e = dalloc(c, &c->dflag, sizeof(unsigned int));
+  if (e == cudaSuccess) e = dalloc(c, &c->dpart, sizeof(double) * lbm::obs_partials_len(max_nodes));
+  if (e == cudaSuccess) e = dalloc(c, &c->dobs, sizeof(double) * 8);
+  if (e == cudaSuccess) e = dalloc(c, &c->dconsts, sizeof(InstanceConsts) * nbatch);
   if (e == cudaSuccess)
     e = cudaMemcpy(c->dconsts, c->hconsts.data(), sizeof(InstanceConsts) * nbatch, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->dflag, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(c->p, 0, fld);
   if (e == cudaSuccess && multi) {
-    e = cudaMalloc(&c->dargs[0], sizeof(StepArgs) * nbatch);
-    if (e == cudaSuccess) e = cudaMalloc(&c->dargs[1], sizeof(StepArgs) * nbatch);
+    e = dalloc(c, &c->dargs[0], sizeof(StepArgs) * nbatch);
+    if (e == cudaSuccess) e = dalloc(c, &c->dargs[1], sizeof(StepArgs) * nbatch);
     if (e == cudaSuccess) e = upload_multi(c);
   }
   if (e == cudaSuccess && is3d && lbm::d3q19_maps_bytes() <= sizeof(c->d3maps[0])) {
@@ -625,6 +673,18 @@ int lbm_create_ex(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask
   }
   std::vector<int> nxs(nbatch, nx), nys(nbatch, ny);
   return create_impl(lattice, nbatch, nxs.data(), nys.data(), nz, periodic_mask, params, flags, false, out);
+}
+
+int lbm_create_alloc(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, int nbatch,
+                     const lbm_params* params, int flags, void* stream, lbm_alloc_fn alloc_fn, lbm_free_fn free_fn,
+                     void* user, lbm_ctx** out) {
+  if (nbatch < 1 || nbatch > 65535) {
+    if (out) *out = nullptr;
+    return set_err(nullptr, LBM_EINVAL, "need 1 <= nbatch <= 65535");
+  }
+  std::vector<int> nxs(nbatch, nx), nys(nbatch, ny);
+  return create_impl(lattice, nbatch, nxs.data(), nys.data(), nz, periodic_mask, params, flags, false, out, stream,
+                     alloc_fn, free_fn, user);
 }
 
 int lbm_create_multi(lbm_lattice lattice, int ninst, const int* nx, const int* ny, int periodic_mask,
@@ -699,9 +759,9 @@ int lbm_tune(lbm_ctx* c, int trial, int* strips_out) {
   const size_t gpop = pop / sizeof(float) * c->g_elem;
   const size_t his = sizeof(float) * (size_t)(1 + 2 * c->d) * c->total;
   void *sf = nullptr, *sg = nullptr, *sh = nullptr;
-  cudaError_t e = cudaMalloc(&sf, pop);
-  if (e == cudaSuccess) e = cudaMalloc(&sg, gpop);
-  if (e == cudaSuccess) e = cudaMalloc(&sh, his);
+  cudaError_t e = dev_alloc(c, &sf, pop);
+  if (e == cudaSuccess) e = dev_alloc(c, &sg, gpop);
+  if (e == cudaSuccess) e = dev_alloc(c, &sh, his);
   const int cur0 = c->cur;
   if (e == cudaSuccess) e = cudaMemcpyAsync(sf, c->f[cur0], pop, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sg, c->g[cur0], gpop, cudaMemcpyDeviceToDevice, c->stream);
@@ -775,9 +835,9 @@ int lbm_tune(lbm_ctx* c, int trial, int* strips_out) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  cudaFree(sf);
-  cudaFree(sg);
-  cudaFree(sh);
+  dev_free(c, sf);
+  dev_free(c, sg);
+  dev_free(c, sh);
   if (e != cudaSuccess) return cuda_fail(c, e, "autotuner");
   if (strips_out)
     for (int b = 0; b < c->nbatch; ++b) strips_out[b] = c->multi ? c->istrip[b] : c->strip;
@@ -897,7 +957,7 @@ int lbm_set_inout(lbm_ctx* c, int mode, const float* u_in, double phi_in, double
     for (size_t i = 0; i < cols * c->d; ++i)
       if (!std::isfinite(u_in[i]) || std::fabs(u_in[i]) > 0.5f)
         return set_err(c, LBM_EINVAL, "inlet velocity must be finite and below 0.5 in magnitude");
-    if (!c->inout_u) LBM_CK(c, cudaMalloc(&c->inout_u, sizeof(float) * cols * c->d));
+    if (!c->inout_u) LBM_CK(c, dalloc(c, &c->inout_u, sizeof(float) * cols * c->d));
     LBM_CK(c, cudaMemcpyAsync(c->inout_u, u_in, sizeof(float) * cols * c->d, cudaMemcpyHostToDevice, c->stream));
     LBM_CK(c, cudaStreamSynchronize(c->stream));
   }

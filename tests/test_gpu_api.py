@@ -133,3 +133,40 @@ def test_caller_stream(lbm_lib):
     assert np.array_equal(a.get_populations()[0], b.get_populations()[0])
     a.close()
     b.close()
+
+
+def test_context_on_the_torch_caching_allocator(lbm_lib):
+    """lbm_create_alloc with PyTorch's caching allocator and stream: the memory is accounted by PyTorch, returned
+    at destruction, and the run is bitwise the run of a context that allocates for itself."""
+    import torch
+    L = lbm_lib
+    from synthetic import free_drop
+    geo = free_drop(48, 40, R=10.0)
+    prm = L.lbm_default_params(sigma=0.01)
+    ref = L.Context(L.LBM_D2Q9, 48, 40, 1, periodic=(True, True, False), params=prm)
+    try:
+        ref.set_solid(geo.phi0.astype(np.float32))
+        ref.set_phase(geo.phi1.astype(np.float32))
+        ref.step(120)
+        want = ref.get_fields()
+    finally:
+        ref.close()
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    stream = torch.cuda.Stream()
+    alloc = L.TorchAllocator()
+    ctx = L.Context(L.LBM_D2Q9, 48, 40, 1, periodic=(True, True, False), params=prm, allocator=alloc,
+                    stream=stream.cuda_stream)
+    try:
+        # populations (2 x 2 x 9), history (2 x 5), phi0, p: 42 floats per node at least
+        assert torch.cuda.memory_allocated() - before >= 42 * 4 * 48 * 40
+        ctx.set_solid(geo.phi0.astype(np.float32))
+        ctx.set_phase(geo.phi1.astype(np.float32))
+        ctx.step(120)
+        got = ctx.get_fields()
+        ctx.tune(2)                                   # the autotuner's save area comes from the same allocator
+    finally:
+        ctx.close()
+    for a, b in zip(got, want):
+        np.testing.assert_array_equal(a, b)
+    assert torch.cuda.memory_allocated() == before

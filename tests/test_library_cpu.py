@@ -81,3 +81,18 @@ def test_storage_options_validated_on_the_host(lbm_lib):
     with pytest.raises(L.LbmError) as e:
         L.lbm_create_ex(L.LBM_D2Q9, 16, 16, 1, 3, p, 2)
     assert e.value.status == -1          # unknown flag
+
+
+def test_create_alloc_needs_both_callbacks(lbm_lib):
+    """The callbacks are checked before any device call."""
+    import ctypes
+    lib = lbm_lib.library()
+    p = lbm_lib.lbm_default_params()
+    out = ctypes.c_void_p()
+    alloc = lbm_lib.lbm_alloc_fn(lambda n, s, u: None)
+    st = lib.lbm_create_alloc(lbm_lib.LBM_D2Q9, 16, 8, 1, 3, 1, ctypes.byref(p), 0, None, alloc, lbm_lib.lbm_free_fn(),
+                              None, ctypes.byref(out))
+    assert st == -1 and not out.value
+    st = lib.lbm_create_alloc(lbm_lib.LBM_D2Q9, 16, 8, 1, 3, 0, ctypes.byref(p), 0, None, alloc,
+                              lbm_lib.lbm_free_fn(lambda a, b, c, d: None), None, ctypes.byref(out))
+    assert st == -1                                   # nbatch 0
