@@ -137,3 +137,30 @@ def test_set_inout_validation(lbm_lib):
             ctx.set_inout(4)
     finally:
         ctx.close()
+
+
+def test_inout_batch_equals_single_runs(lbm_lib):
+    """The boundary kernel walks every instance of a batch with its own constants: bitwise the single runs."""
+    L = lbm_lib
+    nx, ny = 48, 16
+    yy, xx = np.mgrid[:ny, :nx] + 0.5
+    phi1 = (0.5 + 0.5 * np.tanh((6.0 - np.hypot(xx - 16, yy - 8)) / 2.0)).astype(np.float32)
+    phi0 = np.zeros((ny, nx), np.float32)
+    prms = [L.lbm_default_params(rho=(1.0, r, 1.0), mu=(0.05, 0.05, 0.05), d0=0.5) for r in (1.0, 3.0)]
+    u_in = np.stack([np.full(ny, 0.01), np.zeros(ny)]).astype(np.float32)
+
+    def run(batch):
+        ctx = L.Context(L.LBM_D2Q9, nx, ny, 1, periodic=(False, False, False), batch=batch)
+        try:
+            ctx.set_solid(np.broadcast_to(phi0, (len(batch), ny, nx)).copy())
+            ctx.set_phase(np.broadcast_to(phi1, (len(batch), ny, nx)).copy())
+            ctx.set_inout(3, u_in, 0.0, 0.0)
+            ctx.step(300)
+            return ctx.get_fields()
+        finally:
+            ctx.close()
+    both = run(prms)
+    for b in range(2):
+        one = run([prms[b]])
+        for a, c in zip(both, one):
+            np.testing.assert_array_equal(a[b], c[0])
