@@ -28,9 +28,17 @@ extern "C" {
 #endif
 
 /* y[p][co] = act(bias[co] + sum_{tap, ci} x[p + shift(tap)][ci] wt[tap][co][ci]),
- * act = ReLU when relu != 0.  cin a multiple of 16, cout of 32; bias may be NULL. */
+ * act = ReLU when relu != 0.  cin a multiple of 16, cout of 32; bias may be NULL.
+ * Runs on the tcgen05 tensor cores (FP32 accumulator in tensor memory); a
+ * CTA whose bounded wait for its matrix products gives up writes nothing and
+ * raises the flag that lbm_nn_check reports. */
 int lbm_nn_conv3x3(const float* x, const void* wt_bf16, const float* bias, float* y, int n, int h, int w,
                    int cin, int cout, int relu, void* stream);
+
+/* 0, or -5 when a convolution since the last call gave up waiting for the
+ * tensor cores (its output is incomplete); clears the flag.  Synchronous with
+ * respect to the device (reads a device flag), -3 on a CUDA error. */
+int lbm_nn_check(void);
 
 /* Floats of workspace lbm_nn_conv3x3_wgrad needs for this shape. */
 long long lbm_nn_wgrad_workspace(int n, int h, int w, int cin, int cout);

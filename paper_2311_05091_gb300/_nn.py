@@ -14,7 +14,7 @@ c_int, c_float, c_ll, P = ctypes.c_int, ctypes.c_float, ctypes.c_longlong, ctype
 # every symbol include/lbm_nn.h declares
 EXPORTS = ["lbm_nn_conv3x3", "lbm_nn_wgrad_workspace", "lbm_nn_conv3x3_wgrad", "lbm_nn_flip_transpose",
            "lbm_nn_relu_bwd", "lbm_nn_pool2", "lbm_nn_up2", "lbm_nn_add", "lbm_nn_pack_input",
-           "lbm_nn_mse_residual", "lbm_nn_adam", "lbm_nn_to_bf16", "lbm_nn_project"]
+           "lbm_nn_mse_residual", "lbm_nn_adam", "lbm_nn_to_bf16", "lbm_nn_project", "lbm_nn_check"]
 
 _SIG = {
     "lbm_nn_conv3x3": (c_int, [P, P, P, P, c_int, c_int, c_int, c_int, c_int, c_int, P]),
@@ -30,6 +30,7 @@ _SIG = {
     "lbm_nn_adam": (c_int, [P, P, P, P, P, c_ll, c_float, c_float, c_float, c_float, c_int, P]),
     "lbm_nn_to_bf16": (c_int, [P, P, c_ll, P]),
     "lbm_nn_project": (c_int, [P, c_int, P, P, P, P, c_ll, c_int, c_int, c_int, P]),
+    "lbm_nn_check": (c_int, []),
 }
 
 _LIB = None
@@ -107,3 +108,8 @@ def to_bf16(a, b, n, stream=0):
 
 def project(out, cpad, phi0, phi1, field, work, work_len, n, h, w, stream=0):
     _call("lbm_nn_project", out, cpad, phi0, phi1, field, work, work_len, n, h, w, stream)
+
+
+def check():
+    """Raise if a convolution gave up waiting for the tensor cores since the last check."""
+    _call("lbm_nn_check")

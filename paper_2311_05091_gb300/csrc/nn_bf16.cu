@@ -6,9 +6,10 @@
 //
 // Tensors are NHWC float32 in memory (pixel p = (n h + y) w + x, channel
 // innermost).  3x3 convolutions run on the tensor cores with BF16 operands
-// and FP32 accumulation (mma.sync m16n8k16): activations are rounded to BF16
-// as they enter a convolution, weights are kept as a BF16 copy of FP32
-// master weights.  Weight layout: wt[tap][cout][cin], tap = 3 ky + kx, so a
+// and FP32 accumulation: the forward (and data-gradient) convolution with
+// tcgen05.mma and a TMEM accumulator, the weight gradient with mma.sync
+// m16n8k16; activations are rounded to BF16 as they enter a convolution,
+// weights are kept as a BF16 copy of FP32 master weights.  Weight layout: wt[tap][cout][cin], tap = 3 ky + kx, so a
 // pair of input channels is one 32-bit word.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -38,117 +39,200 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 
 // ---------------------------------------------------------------------------
 // forward: y[p][co] = act(b[co] + sum_{tap, ci} x[p + shift(tap)][ci] wt[tap][co][ci])
-// CTA: one 64-pixel row segment (image, row y, columns x0 .. x0 + 63) x 32 CW
-// output channels, 4 warps in a 2 (pixels) x 2 (channels) grid, each warp 32
-// pixels x 16 CW channels.  Per chunk of 32 input channels the CTA stages, as
-// BF16 in shared memory, the input rows y - 1 .. y + 1 at columns x0 - 1 ..
-// x0 + 64 ([row][column][ci], zero outside the image) and the weights of all
-// nine taps ([tap][co][ci]); rows are padded to 40 elements (20 words) so a
-// fragment load touches 32 different banks.  The nine taps then read shifted
-// windows of the same input rows.  grid (segments, cout / (32 CW)).
+//
+// Implicit GEMM on the 5th-generation tensor cores: D (128 output pixels x N
+// output channels, FP32 in TMEM) += A_tap (128 x 16 input channels, BF16) *
+// B_tap^T (N x 16) for the nine taps and every chunk of 16 input channels.
+// The 128 pixels of a CTA are R image rows of W = 128 / R columns (W = 128,
+// 64, 32 or 16, the smallest that covers the image width, so narrow levels
+// keep the M = 128 tile full).  Per chunk the CTA stages in shared memory, as
+// BF16 in the canonical K-major layout without swizzle (core matrices of 8
+// rows x 16 bytes; rows 16 bytes apart, 8-row groups 128 bytes apart, the
+// two 8-channel halves of the chunk LBO bytes apart):
+//   A: for each column offset kx, rows y0 - 1 .. y0 + R of the input at
+//      columns x0 + kx - 1 .. x0 + kx - 2 + W (zero outside the image), so
+//      that tap (ky, kx) is the 128-row window starting at row ky of copy kx;
+//   B: the weights of all nine taps, [tap][half][co].
+// One thread issues the nine tcgen05.mma of the chunk and commits them to the
+// stage's mbarrier; with two stages the next chunk is staged while the tensor
+// cores work; a stage is refilled only after the bounded wait for the
+// products that read it.  The epilogue reads the accumulator with tcgen05.ld
+// (warp w owns TMEM lanes 32 w .. 32 w + 31 = pixels), adds the bias, applies
+// the ReLU and stores FP32.  grid (segments, cout / N), 128 threads.
 // ---------------------------------------------------------------------------
-constexpr int kFwdSeg = 64, kCiChunk = 32, kCiPad = 40;
+__device__ unsigned int g_nn_fault = 0;    // set when a bounded wait on the tensor cores gave up
 
-template <int CW>
-__global__ void __launch_bounds__(kThreads) conv3x3_fwd(const float* __restrict__ x,
-                                                        const __nv_bfloat16* __restrict__ wt,
-                                                        const float* __restrict__ bias, float* __restrict__ y,
-                                                        int n, int h, int w, int cin, int cout, int relu) {
-  constexpr int CO = 32 * CW, NT = 2 * CW;                     // CTA channels, n-tiles per warp
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16(*sx)[kFwdSeg + 2][kCiPad] = reinterpret_cast<__nv_bfloat16(*)[kFwdSeg + 2][kCiPad]>(smem_raw);
-  __nv_bfloat16(*sw)[CO][kCiPad] =
-      reinterpret_cast<__nv_bfloat16(*)[CO][kCiPad]>(smem_raw + sizeof(__nv_bfloat16) * 3 * (kFwdSeg + 2) * kCiPad);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int wm = warp & 1, wn = warp >> 1;
-  const int spr = (w + kFwdSeg - 1) / kFwdSeg;
-  const long long sg = blockIdx.x;
-  const int img = (int)(sg / ((long long)h * spr));
-  const int yrow = (int)((sg / spr) % h);
-  const int x0 = (int)(sg % spr) * kFwdSeg;
-  const int co0 = blockIdx.y * CO;
-  float acc[2][NT][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-  for (int ci0 = 0; ci0 < cin; ci0 += kCiChunk) {
-    const int cw = min(kCiChunk, cin - ci0);                   // 16 or 32 channels in this chunk
-    __syncthreads();
-    // input rows: 3 x 66 columns x 8 float4 of channels
-    for (int e = threadIdx.x; e < 3 * (kFwdSeg + 2) * 8; e += kThreads) {
-      const int r = e / ((kFwdSeg + 2) * 8), rem = e % ((kFwdSeg + 2) * 8);
-      const int jc = rem >> 3, c4 = (rem & 7) * 4;
-      const int yy = yrow + r - 1, xc = x0 + jc - 1;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (yy >= 0 && yy < h && xc >= 0 && xc < w && c4 < cw)
-        v = *reinterpret_cast<const float4*>(x + (((long long)img * h + yy) * w + xc) * cin + ci0 + c4);
-      uint2 packed;
-      packed.x = pack_bf16(v.x, v.y);
-      packed.y = pack_bf16(v.z, v.w);
-      *reinterpret_cast<uint2*>(&sx[r][jc][c4]) = packed;
-    }
-    // weights: 9 taps x CO channels x 32 inputs, 8 BF16 (16 bytes) per load
-    for (int e = threadIdx.x; e < 9 * CO * 4; e += kThreads) {
-      const int tap = e / (CO * 4), rem = e % (CO * 4);
-      const int co = rem >> 2, c8 = (rem & 3) * 8;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (c8 < cw) v = *reinterpret_cast<const uint4*>(wt + ((long long)tap * cout + co0 + co) * cin + ci0 + c8);
-      *reinterpret_cast<uint4*>(&sw[tap][co][c8]) = v;
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-      const int ky = tap / 3, kx = tap % 3;
-#pragma unroll
-      for (int kk = 0; kk < kCiChunk; kk += 16) {
-        if (kk >= cw) break;
-        uint32_t a[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          const int px = wm * 32 + mt * 16 + g + kx;           // column index jc = pixel + kx (shift kx - 1, +1 halo)
-          a[mt][0] = *reinterpret_cast<const uint32_t*>(&sx[ky][px][kk + 2 * t]);
-          a[mt][1] = *reinterpret_cast<const uint32_t*>(&sx[ky][px + 8][kk + 2 * t]);
-          a[mt][2] = *reinterpret_cast<const uint32_t*>(&sx[ky][px][kk + 2 * t + 8]);
-          a[mt][3] = *reinterpret_cast<const uint32_t*>(&sx[ky][px + 8][kk + 2 * t + 8]);
-        }
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          const int co = wn * 16 * CW + nt * 8 + g;
-          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&sw[tap][co][kk + 2 * t]);
-          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&sw[tap][co][kk + 2 * t + 8]);
-          mma_bf16(acc[0][nt], a[0], b0, b1);
-          mma_bf16(acc[1][nt], a[1], b0, b1);
-        }
-      }
-    }
-  }
-  // acc[mt][nt]: pixels wm 32 + mt 16 + g (+8), channels co0 + wn 16 CW + nt 8 + 2 t (+1)
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt) {
-    const int co = co0 + wn * 16 * CW + nt * 8 + 2 * t;
-    const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int xc = x0 + wm * 32 + mt * 16 + g + 8 * half;
-        if (xc >= w) continue;
-        float v0 = acc[mt][nt][2 * half] + b0, v1 = acc[mt][nt][2 * half + 1] + b1;
-        if (relu) {
-          v0 = fmaxf(v0, 0.f);
-          v1 = fmaxf(v1, 0.f);
-        }
-        *reinterpret_cast<float2*>(y + (((long long)img * h + yrow) * w + xc) * cout + co) = make_float2(v0, v1);
-      }
-  }
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major, start / LBO / SBO in bytes
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
 }
 
-template <int CW>
-constexpr int fwd_smem_bytes() {
-  return (int)sizeof(__nv_bfloat16) * (3 * (kFwdSeg + 2) * kCiPad + 9 * 32 * CW * kCiPad);
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// bounded wait for the completion of phase `parity` of an mbarrier; false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity));
+  return done != 0;
+}
+
+constexpr int kTcM = 128;
+
+// (A, B) tiles in S stages: with two, one chunk is staged while the tensor cores multiply the previous one.
+// Two stages pay only where the tiles are small enough to keep several CTAs per SM (measured on GB300: wide
+// images with N <= 64 gain 5-12 %, the 128-channel tiles lose up to 35 % when their occupancy halves).
+// A holds at most 24 KB: WIDE 2 x 3 x 130 x 16 bytes; otherwise 6 (R + 2) W 16 <= 24576 bytes (R = 2).
+template <int N, bool WIDE>
+struct FwdTcSmem {
+  static constexpr int S = (WIDE && N <= 64) ? 2 : 1;
+  static constexpr int kA = WIDE ? 13312 : 24576;
+  static constexpr int kB = 9 * 2 * N * 16;
+  static constexpr int kStage = kA + kB;
+  static constexpr int bytes() { return S * kStage + 64; }
+};
+
+// WIDE (one image row of 128 columns per CTA): a single copy of the three input rows with one halo column each
+// side, [half][row][column] x 16 bytes; the window of tap (ky, kx) starts at row ky, column kx, i.e. 16 kx bytes
+// further, and its 128 rows stay 16 bytes apart.  Otherwise (R > 1 rows per CTA) the rows of the window cross
+// image rows, so the input is staged once per column offset kx as described above.
+template <int N, bool WIDE>
+__global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc(const float* __restrict__ x,
+                                                           const __nv_bfloat16* __restrict__ wt,
+                                                           const float* __restrict__ bias, float* __restrict__ y,
+                                                           int n, int h, int w, int cin, int cout, int relu,
+                                                           int R) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  using SM = FwdTcSmem<N, WIDE>;
+  constexpr int S = SM::S;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * SM::kStage);   // one mbarrier per stage
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int W = kTcM / R;
+  const int segx = (w + W - 1) / W, segy = (h + R - 1) / R;
+  const int sx = blockIdx.x % segx, sy = (blockIdx.x / segx) % segy, img = blockIdx.x / (segx * segy);
+  const int x0 = sx * W, y0 = sy * R;
+  const int co0 = blockIdx.y * N;
+  const uint32_t bar0 = smem_addr(bar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(N < 32 ? 32 : N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int k = 0; k < S; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8 * k), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+
+  const int rows = R + 2;
+  const int pitch = WIDE ? W + 2 : W;                    // staged columns per row
+  const uint32_t lbo_a = (uint32_t)(rows * pitch * 16), lbo_b = (uint32_t)(N * 16);
+  const int nchunks = cin / 16;
+  bool ok = true;
+  for (int c = 0; c < nchunks; ++c) {
+    const int ci0 = c * 16, st = c % S;
+    unsigned char* sA = smem + st * SM::kStage;
+    unsigned char* sB = sA + SM::kA;
+    // the products of chunk c - S read this stage: wait for them (phase (c - S) / S of this stage's barrier)
+    if (c >= S) ok = ok && mbar_wait(bar0 + 8 * st, ((c - S) / S) & 1);
+    // A: WIDE, one copy of rows y0 - 1 .. y0 + 1 at columns x0 - 1 .. x0 + 128; else one copy per kx
+    for (int e = tid; e < (WIDE ? 2 : 6) * rows * pitch; e += kThreads) {
+      const int px = e % pitch, r = (e / pitch) % rows, kc = (e / (pitch * rows)) & 1;
+      const int kx = WIDE ? 0 : e / (pitch * rows * 2);
+      const int yy = y0 + r - 1, xc = x0 + px + kx - 1;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (yy >= 0 && yy < h && xc >= 0 && xc < w) {
+        const float* src = x + (((long long)img * h + yy) * w + xc) * cin + ci0 + 8 * kc;
+        const float4 a = *reinterpret_cast<const float4*>(src);
+        const float4 b = *reinterpret_cast<const float4*>(src + 4);
+        v = make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, b.w));
+      }
+      *reinterpret_cast<uint4*>(sA + (((kx * 2 + kc) * rows + r) * pitch + px) * 16) = v;
+    }
+    // B: weights of the nine taps
+    for (int e = tid; e < 18 * N; e += kThreads) {
+      const int co = e % N, kc = (e / N) & 1, tap = e / (2 * N);
+      const uint4 v =
+          *reinterpret_cast<const uint4*>(wt + ((long long)tap * cout + co0 + co) * cin + ci0 + 8 * kc);
+      *reinterpret_cast<uint4*>(sB + ((tap * 2 + kc) * N + co) * 16) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;");       // generic-proxy stores visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0 && ok) {
+      constexpr uint32_t idesc = umma_idesc(kTcM, N);
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        const uint64_t ad = WIDE ? umma_desc(smem_addr(sA + (ky * pitch + kx) * 16), lbo_a, 128)
+                                 : umma_desc(smem_addr(sA + ((kx * 2) * rows + ky) * W * 16), lbo_a, 128);
+        const uint64_t bd = umma_desc(smem_addr(sB + tap * 2 * N * 16), lbo_b, 128);
+        const uint32_t acc = (c > 0 || tap > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * st));
+    }
+  }
+  // the last commit completes after every product issued before it
+  ok = ok && mbar_wait(bar0 + 8 * ((nchunks - 1) % S), ((nchunks - 1) / S) & 1);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int m = warp * 32 + lane;
+    const int yo = y0 + m / W, xo = x0 + m % W;
+    const bool valid = yo < h && xo < w;
+    float* dst = y + (((long long)img * h + yo) * w + xo) * cout + co0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          float4 o;
+          o.x = __uint_as_float(r[j]) + (bias ? bias[co0 + c0 + j] : 0.f);
+          o.y = __uint_as_float(r[j + 1]) + (bias ? bias[co0 + c0 + j + 1] : 0.f);
+          o.z = __uint_as_float(r[j + 2]) + (bias ? bias[co0 + c0 + j + 2] : 0.f);
+          o.w = __uint_as_float(r[j + 3]) + (bias ? bias[co0 + c0 + j + 3] : 0.f);
+          if (relu) {
+            o.x = fmaxf(o.x, 0.f);
+            o.y = fmaxf(o.y, 0.f);
+            o.z = fmaxf(o.z, 0.f);
+            o.w = fmaxf(o.w, 0.f);
+          }
+          *reinterpret_cast<float4*>(dst + c0 + j) = o;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(&g_nn_fault, 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(N < 32 ? 32 : N));
 }
 
 // ---------------------------------------------------------------------------
@@ -493,21 +577,51 @@ int lbm_nn_conv3x3(const float* x, const void* wt_bf16, const float* bias, float
   if (!x || !wt_bf16 || !y || n < 1 || h < 1 || w < 1 || cin < 16 || cin % 16 || cout < 32 || cout % 32) return -1;
   static bool attr_set = false;                                // the opt-in above 48 KB, once per process
   if (!attr_set) {
-    if (cudaFuncSetAttribute(conv3x3_fwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd_smem_bytes<2>()) !=
-        cudaSuccess)
-      return -3;
+    bool good = true;
+    auto opt_in = [&](const void* fn, int bytes) {
+      good = good && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    };
+    opt_in((const void*)conv3x3_fwd_tc<128, true>, FwdTcSmem<128, true>::bytes());
+    opt_in((const void*)conv3x3_fwd_tc<64, true>, FwdTcSmem<64, true>::bytes());
+    opt_in((const void*)conv3x3_fwd_tc<32, true>, FwdTcSmem<32, true>::bytes());
+    opt_in((const void*)conv3x3_fwd_tc<128, false>, FwdTcSmem<128, false>::bytes());
+    opt_in((const void*)conv3x3_fwd_tc<64, false>, FwdTcSmem<64, false>::bytes());
+    opt_in((const void*)conv3x3_fwd_tc<32, false>, FwdTcSmem<32, false>::bytes());
+    if (!good) return -3;
     attr_set = true;
   }
-  const long long segs = (long long)n * h * ((w + kFwdSeg - 1) / kFwdSeg);
+  // R image rows of 128 / R columns per CTA: the narrowest tile that covers the width
+  const int R = w > 64 ? 1 : (w > 32 ? 2 : (w > 16 ? 4 : 8));
+  const int W = kTcM / R;
+  const long long segs = (long long)n * ((h + R - 1) / R) * ((w + W - 1) / W);
+  if (segs > 0x7fffffffLL) return -1;
   const auto* wb = static_cast<const __nv_bfloat16*>(wt_bf16);
   cudaStream_t s = (cudaStream_t)stream;
-  if (cout % 64 == 0)
-    conv3x3_fwd<2><<<dim3((unsigned)segs, cout / 64), kThreads, fwd_smem_bytes<2>(), s>>>(x, wb, bias, y, n, h, w, cin,
-                                                                                            cout, relu);
-  else
-    conv3x3_fwd<1><<<dim3((unsigned)segs, cout / 32), kThreads, fwd_smem_bytes<1>(), s>>>(x, wb, bias, y, n, h, w, cin,
-                                                                                            cout, relu);
+  const int N = cout % 128 == 0 ? 128 : (cout % 64 == 0 ? 64 : 32);
+  const dim3 grid((unsigned)segs, cout / N);
+  const bool wide = R == 1;
+#define LBM_NN_FWD(NN, WD)                                                                                        \
+  conv3x3_fwd_tc<NN, WD><<<grid, kThreads, FwdTcSmem<NN, WD>::bytes(), s>>>(x, wb, bias, y, n, h, w, cin, cout, relu, R)
+  if (N == 128) {
+    if (wide) LBM_NN_FWD(128, true); else LBM_NN_FWD(128, false);
+  } else if (N == 64) {
+    if (wide) LBM_NN_FWD(64, true); else LBM_NN_FWD(64, false);
+  } else {
+    if (wide) LBM_NN_FWD(32, true); else LBM_NN_FWD(32, false);
+  }
+#undef LBM_NN_FWD
   return status(cudaGetLastError());
+}
+
+int lbm_nn_check(void) {
+  unsigned int f = 0;
+  if (cudaMemcpyFromSymbol(&f, g_nn_fault, sizeof f) != cudaSuccess) return -3;
+  if (f) {
+    const unsigned int zero = 0;
+    cudaMemcpyToSymbol(g_nn_fault, &zero, sizeof zero);
+    return -5;
+  }
+  return 0;
 }
 
 }  // extern "C"
