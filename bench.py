@@ -712,7 +712,8 @@ def _ws_conv_roofline(B, n, stream):
     achieved = flops / ms / 1e9
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "peak_source": src,
-            "kernel": f"conv3x3_fwd<1> {cin}->{cout} on {B} x {n}^2 (mma.sync m16n8k16 BF16, FP32 accumulate)"}
+            "kernel": f"conv3x3_fwd_tc<32, wide> {cin}->{cout} on {B} x {n}^2 (tcgen05.mma kind::f16, BF16 operands, "
+                      "FP32 accumulator in TMEM)"}
 
 
 def run_warmstart(args):
