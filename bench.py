@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=60.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS) + ["warmstart256"])
+    ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS) + ["warmstart256", "kp128"])
     ap.add_argument("--size", type=int, default=None, help="lattice side (default: the workload's)")
     ap.add_argument("--g-f16", action="store_true",
                     help="store the NS populations as FP16 (D2Q9; float32 arithmetic and CH populations)")
@@ -83,6 +83,7 @@ def parse():
     ap.add_argument("--tte-steps", type=int, default=150000,
                     help="steps of the time-to-equilibrium run (disk workload; 0 skips it)")
     ap.add_argument("--tte-every", type=int, default=2500, help="contact-angle sampling interval")
+    ap.add_argument("--kp-steps", type=int, default=40000, help="relative permeability: steps of every run")
     ap.add_argument("--tune-trial", type=int, default=40,
                     help="steps per candidate of the strip autotuner before timing (0: the library's default strip)")
     ap.add_argument("--ws-train", type=int, default=2000, help="warm start: training samples")
@@ -716,6 +717,58 @@ def _ws_conv_roofline(B, n, stream):
                       "FP32 accumulator in TMEM)"}
 
 
+def run_kp(args):
+    """Relative permeabilities K_1, K_2 (Sec. 4.6, Eq. eq-Kp) against the wetting saturation S_1 on a sphere pack.
+
+    All runs of synthetic.workloads.kp_porous (one two-phase run per initial radius R0 of the wetting cylinder and
+    the two single-phase runs) advance together as one batch; every 5000 steps lbm_phase_flux gives each run's
+    pore-space fluxes, and K_p = q_p (two-phase) / q (single phase of fluid p).  The line reports K_1, K_2 and S_1
+    at the end and the relative change of the fluxes over the last 5000 steps (steadiness)."""
+    import numpy as np
+    import torch
+    from paper_2311_05091_gb300 import _lbm as L
+    from synthetic.workloads import kp_porous
+    n = args.size or 128
+    wl = kp_porous(n=n, R0s=(20.0, 32.0, 44.0, 56.0, 68.0))
+    nb = wl["phi1"].shape[0]
+    stream = torch.cuda.Stream()
+    ctx = L.Context(L.LBM_D3Q19, n, n, n, periodic=(True, True, True),
+                    batch=[L.lbm_default_params(**wl["params"]) for _ in range(nb)])
+    try:
+        ctx.set_stream(stream.cuda_stream)
+        ctx.set_solid(np.broadcast_to(wl["phi0"], (nb, n, n, n)).copy())
+        ctx.set_phase(wl["phi1"])
+        hist, done, block = [], 0, 5000
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        while done < args.kp_steps:
+            k = min(block, args.kp_steps - done)
+            ctx.step(k)
+            done += k
+            hist.append([ctx.phase_flux(i, 0) for i in range(nb)])
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        ctx.close()
+    last, prev = hist[-1], hist[-2] if len(hist) > 1 else hist[-1]
+    s1, s2 = last[nb - 2], last[nb - 1]
+    rows = []
+    for i in range(nb - 2):
+        K1, K2 = L.relative_permeability(last[i], s1, s2)
+        change = max(abs(last[i][q] - prev[i][q]) / max(abs(last[i][q]), 1e-30) for q in ("q1", "q2"))
+        rows.append({"run": wl["labels"][i], "S1": last[i]["s1"], "K1": K1, "K2": K2,
+                     "flux_change_last_5000_steps": change})
+    line = {"metric": "relative permeabilities K_1, K_2 against wetting saturation S_1 (Eq. eq-Kp)",
+            "value": None, "unit": "-", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "porosity": wl["porosity"], "steps": args.kp_steps, "runs": nb},
+            "results": rows,
+            "single_phase_change_last_5000_steps": abs(s1["q"] - prev[nb - 2]["q"]) / abs(s1["q"]),
+            "seconds": ms / 1e3, "mlups": nb * n ** 3 * args.kp_steps / (ms * 1e3)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_warmstart(args):
     """Learned warm start (not in the paper), measured end to end on one GPU.
 
@@ -883,6 +936,8 @@ def main():
         return run_reference(args)
     if args.workload == "warmstart256":
         return run_warmstart(args)
+    if args.workload == "kp128":
+        return run_kp(args)
     return run_gpu(args)
 
 
