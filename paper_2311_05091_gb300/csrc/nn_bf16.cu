@@ -575,8 +575,11 @@ extern "C" {
 int lbm_nn_conv3x3(const float* x, const void* wt_bf16, const float* bias, float* y, int n, int h, int w, int cin,
                    int cout, int relu, void* stream) {
   if (!x || !wt_bf16 || !y || n < 1 || h < 1 || w < 1 || cin < 16 || cin % 16 || cout < 32 || cout % 32) return -1;
-  static bool attr_set = false;                                // the opt-in above 48 KB, once per process
-  if (!attr_set) {
+  // the opt-in above 48 KB of shared memory is a per-device attribute: set it once for each device used
+  static unsigned long long attr_set = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -3;
+  if (!(attr_set & (1ull << dev))) {
     bool good = true;
     auto opt_in = [&](const void* fn, int bytes) {
       good = good && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
@@ -588,7 +591,7 @@ int lbm_nn_conv3x3(const float* x, const void* wt_bf16, const float* bias, float
     opt_in((const void*)conv3x3_fwd_tc<64, false>, FwdTcSmem<64, false>::bytes());
     opt_in((const void*)conv3x3_fwd_tc<32, false>, FwdTcSmem<32, false>::bytes());
     if (!good) return -3;
-    attr_set = true;
+    attr_set |= 1ull << dev;
   }
   // R image rows of 128 / R columns per CTA: the narrowest tile that covers the width
   const int R = w > 64 ? 1 : (w > 32 ? 2 : (w > 16 ? 4 : 8));
