@@ -11,6 +11,8 @@
 
 #include <cmath>
 #include <unordered_map>
+
+#include <nvtx3/nvToolsExt.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -96,6 +98,14 @@ struct lbm_ctx {
 };
 
 namespace {
+
+// NVTX range for the duration of a scope (host side; a no-op unless a profiler is attached)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 int set_err(lbm_ctx* c, int code, const char* fmt, const char* a = "", const char* b = "") {
   char* dst = c ? c->err : g_last_error;
@@ -366,8 +376,10 @@ cudaError_t launch_step(lbm_ctx* c, int from, bool observe, cudaStream_t s, cuda
   cudaError_t e = cudaSuccess;
   if (c->lattice == LBM_D2Q9) {
     if (mid) cudaEventRecord(mid, s);
+    Range r("d2q9_step (fused stencils, collisions, streaming)");
     e = lbm::launch_d2q9_step(a, c->nbatch, observe, s);
   } else {
+    Range r("3D step: moment pass + fused kernel");
     e = lbm::launch_d3q19_moments(a, c->nbatch, s);
     if (e != cudaSuccess) return e;
     if (mid) {
@@ -752,6 +764,7 @@ int lbm_set_launch(lbm_ctx* c, int strip, int depth) {
 // of `trial` steps (after one untimed step), two passes over the classes.
 // The evolving state is saved before and restored after, bitwise.
 int lbm_tune(lbm_ctx* c, int trial, int* strips_out) {
+  Range range("lbm_tune");
   if (int s = check_ready(c, true)) return s;
   if (trial < 1) return set_err(c, LBM_EINVAL, "trial must be >= 1");
   LBM_CK(c, cudaStreamSynchronize(c->stream));
@@ -969,6 +982,7 @@ int lbm_set_inout(lbm_ctx* c, int mode, const float* u_in, double phi_in, double
 }
 
 int lbm_step(lbm_ctx* c, int n) {
+  Range range("lbm_step");
   if (int s = check_ready(c, true)) return s;
   if (n < 0) return set_err(c, LBM_EINVAL, "n must be >= 0");
   const bool graphs = c->stream != nullptr && !c->profiling;
@@ -996,6 +1010,7 @@ int lbm_sync(lbm_ctx* c) {
 }
 
 int lbm_get_fields(lbm_ctx* c, float* phi1, float* u, float* p) {
+  Range range("lbm_get_fields");
   if (int s = check_ready(c, true)) return s;
   const int nh = 1 + 2 * c->d;
   const float* h = c->hist[c->cur];
@@ -1109,6 +1124,7 @@ int lbm_set_state(lbm_ctx* c, const void* buf, size_t bytes) {
 }
 
 int lbm_observables(lbm_ctx* c, int instance, lbm_obs* out) {
+  Range range("lbm_observables");
   if (int s = check_ready(c, true)) return s;
   if (!out || instance < 0 || instance >= c->nbatch) return set_err(c, LBM_EINVAL, "bad instance or output");
   const int nh = 1 + 2 * c->d;
@@ -1134,6 +1150,7 @@ int lbm_observables(lbm_ctx* c, int instance, lbm_obs* out) {
 }
 
 int lbm_phase_flux(lbm_ctx* c, int instance, int axis, lbm_flux* out) {
+  Range range("lbm_phase_flux");
   if (int s = check_ready(c, true)) return s;
   if (!out || instance < 0 || instance >= c->nbatch || axis < 0 || axis >= c->d)
     return set_err(c, LBM_EINVAL, "bad instance, axis or output");
