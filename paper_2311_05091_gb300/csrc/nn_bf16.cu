@@ -150,6 +150,8 @@ __global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc(const float* __restri
     // the products of chunk c - S read this stage: wait for them (phase (c - S) / S of this stage's barrier)
     if (c >= S) ok = ok && mbar_wait(bar0 + 8 * st, ((c - S) / S) & 1);
     // A: WIDE, one copy of rows y0 - 1 .. y0 + 1 at columns x0 - 1 .. x0 + 128; else one copy per kx
+    // (unrolled so that several iterations' global loads are in flight before their conversions)
+#pragma unroll 4
     for (int e = tid; e < (WIDE ? 2 : 6) * rows * pitch; e += kThreads) {
       const int px = e % pitch, r = (e / pitch) % rows, kc = (e / (pitch * rows)) & 1;
       const int kx = WIDE ? 0 : e / (pitch * rows * 2);
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc(const float* __restri
       *reinterpret_cast<uint4*>(sA + (((kx * 2 + kc) * rows + r) * pitch + px) * 16) = v;
     }
     // B: weights of the nine taps
+#pragma unroll 4
     for (int e = tid; e < 18 * N; e += kThreads) {
       const int co = e % N, kc = (e / N) & 1, tap = e / (2 * N);
       const uint4 v =
@@ -275,6 +278,7 @@ __global__ void __launch_bounds__(kWgThreads) conv3x3_wgrad_seg(const float* __r
     const int x0 = (int)(sg % spr) * kSeg;
     __syncthreads();                                           // the previous segment's fragments are consumed
     // dy^T: 64 pixels x 32 channels as 8 float4 per pixel
+#pragma unroll 2
     for (int e = threadIdx.x; e < kSeg * 8; e += kWgThreads) {
       const int j = e >> 3, c4 = (e & 7) * 4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -286,6 +290,7 @@ __global__ void __launch_bounds__(kWgThreads) conv3x3_wgrad_seg(const float* __r
       sdy[c4 + 3][j] = __float2bfloat16_rn(v.w);
     }
     // x^T: rows y - 1 .. y + 1, columns x0 - 1 .. x0 + 64, 32 channels; column xc goes to copy kx at xc - x0 - kx + 1
+#pragma unroll 3
     for (int e = threadIdx.x; e < 3 * (kSeg + 2) * 8; e += kWgThreads) {
       const int r = e / ((kSeg + 2) * 8), rem = e % ((kSeg + 2) * 8);
       const int jc = rem >> 3, c4 = (rem & 7) * 4;             // jc = xc - x0 + 1 in 0 .. 65
