@@ -367,8 +367,10 @@ __global__ void __launch_bounds__(256) colsum_part(const float* __restrict__ dy,
   const int ch = blockIdx.x * 32 + (threadIdx.x & 31), r = threadIdx.x >> 5;
   const long long pb = (long long)blockIdx.y * chunk, pe = min(P, pb + chunk);
   float s = 0.f;
-  if (ch < c)
+  if (ch < c) {
+#pragma unroll 8
     for (long long p = pb + r; p < pe; p += 8) s += dy[p * c + ch];
+  }
   red[r][threadIdx.x & 31] = s;
   __syncthreads();
   if (r == 0 && ch < c) {
@@ -433,6 +435,45 @@ __global__ void up2_bwd(const float* __restrict__ dy, float* __restrict__ dx, in
   const long long b = (((long long)nn * 2 * h + 2 * yy) * 2 * w + 2 * xx) * c + ch;
   const long long row = 2LL * w * c;
   dx[i] = (dy[b] + dy[b + c]) + (dy[b + row] + dy[b + row + c]);
+}
+
+// The same four maps on float4 groups of channels with 32-bit index arithmetic (c4 = c / 4 groups; the callers
+// use them when c % 4 == 0 and the element count fits 32 bits)
+__global__ void pool2_fwd4(const float4* __restrict__ x, float4* __restrict__ y, int n, int h, int w, int c4) {
+  const unsigned h2 = h / 2, w2 = w / 2;
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)n * h2 * w2 * c4) return;
+  const unsigned ch = i % c4, q = i / c4;
+  const unsigned xx = q % w2, r = q / w2, yy = r % h2, nn = r / h2;
+  const unsigned b = ((nn * h + 2 * yy) * w + 2 * xx) * c4 + ch, row = (unsigned)w * c4;
+  const float4 a = x[b], bb = x[b + c4], cc = x[b + row], d = x[b + row + c4];
+  y[i] = make_float4(0.25f * ((a.x + bb.x) + (cc.x + d.x)), 0.25f * ((a.y + bb.y) + (cc.y + d.y)),
+                     0.25f * ((a.z + bb.z) + (cc.z + d.z)), 0.25f * ((a.w + bb.w) + (cc.w + d.w)));
+}
+__global__ void pool2_bwd4(const float4* __restrict__ dy, float4* __restrict__ dx, int n, int h, int w, int c4) {
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)n * h * w * c4) return;
+  const unsigned ch = i % c4, q = i / c4;
+  const unsigned xx = q % w, r = q / w, yy = r % h, nn = r / h;
+  const float4 v = dy[((nn * (h / 2) + yy / 2) * (w / 2) + xx / 2) * c4 + ch];
+  dx[i] = make_float4(0.25f * v.x, 0.25f * v.y, 0.25f * v.z, 0.25f * v.w);
+}
+__global__ void up2_fwd4(const float4* __restrict__ x, float4* __restrict__ y, int n, int h, int w, int c4) {
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)n * 4 * h * w * c4) return;
+  const unsigned ch = i % c4, q = i / c4;
+  const unsigned xx = q % (2 * w), r = q / (2 * w), yy = r % (2 * h), nn = r / (2 * h);
+  y[i] = x[((nn * h + yy / 2) * w + xx / 2) * c4 + ch];
+}
+__global__ void up2_bwd4(const float4* __restrict__ dy, float4* __restrict__ dx, int n, int h, int w, int c4) {
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)n * h * w * c4) return;
+  const unsigned ch = i % c4, q = i / c4;
+  const unsigned xx = q % w, r = q / w, yy = r % h, nn = r / h;
+  const unsigned b = ((nn * 2 * h + 2 * yy) * 2 * w + 2 * xx) * c4 + ch, row = 2u * w * c4;
+  const float4 a = dy[b], bb = dy[b + c4], cc = dy[b + row], d = dy[b + row + c4];
+  dx[i] = make_float4((a.x + bb.x) + (cc.x + d.x), (a.y + bb.y) + (cc.y + d.y), (a.z + bb.z) + (cc.z + d.z),
+                      (a.w + bb.w) + (cc.w + d.w));
 }
 
 // z = x + a y (z may be x or y)
@@ -700,16 +741,40 @@ int lbm_nn_relu_bwd(const float* dy, const float* y, float* dx, long long n, voi
 int lbm_nn_pool2(const float* x, float* y, int n, int h, int w, int c, int backward, void* stream) {
   if (!x || !y || n < 1 || h < 2 || w < 2 || h % 2 || w % 2 || c < 1) return -1;
   cudaStream_t s = (cudaStream_t)stream;
-  if (!backward) pool2_fwd<<<blocks((long long)n * h * w * c / 4), 256, 0, s>>>(x, y, n, h, w, c);
-  else pool2_bwd<<<blocks((long long)n * h * w * c), 256, 0, s>>>(x, y, n, h, w, c);
+  const long long total = (long long)n * h * w * c;
+  if (c % 4 == 0 && total < (1LL << 31) && ((uintptr_t)x | (uintptr_t)y) % 16 == 0) {
+    const int c4 = c / 4;
+    if (!backward)
+      pool2_fwd4<<<blocks(total / 16), 256, 0, s>>>(reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(y),
+                                                     n, h, w, c4);
+    else
+      pool2_bwd4<<<blocks(total / 4), 256, 0, s>>>(reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(y),
+                                                    n, h, w, c4);
+  } else if (!backward) {
+    pool2_fwd<<<blocks(total / 4), 256, 0, s>>>(x, y, n, h, w, c);
+  } else {
+    pool2_bwd<<<blocks(total), 256, 0, s>>>(x, y, n, h, w, c);
+  }
   return status(cudaGetLastError());
 }
 
 int lbm_nn_up2(const float* x, float* y, int n, int h, int w, int c, int backward, void* stream) {
   if (!x || !y || n < 1 || h < 1 || w < 1 || c < 1) return -1;
   cudaStream_t s = (cudaStream_t)stream;
-  if (!backward) up2_fwd<<<blocks(4LL * n * h * w * c), 256, 0, s>>>(x, y, n, h, w, c);
-  else up2_bwd<<<blocks((long long)n * h * w * c), 256, 0, s>>>(x, y, n, h, w, c);
+  const long long fine = 4LL * n * h * w * c;
+  if (c % 4 == 0 && fine < (1LL << 31) && ((uintptr_t)x | (uintptr_t)y) % 16 == 0) {
+    const int c4 = c / 4;
+    if (!backward)
+      up2_fwd4<<<blocks(fine / 4), 256, 0, s>>>(reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(y), n,
+                                                 h, w, c4);
+    else
+      up2_bwd4<<<blocks(fine / 16), 256, 0, s>>>(reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(y), n,
+                                                  h, w, c4);
+  } else if (!backward) {
+    up2_fwd<<<blocks(fine), 256, 0, s>>>(x, y, n, h, w, c);
+  } else {
+    up2_bwd<<<blocks(fine / 4), 256, 0, s>>>(x, y, n, h, w, c);
+  }
   return status(cudaGetLastError());
 }
 

@@ -121,9 +121,10 @@ def test_wgrad_is_deterministic(nn):
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
 
 
-def test_pooling_upsampling_relu_add_pack(nn):
+@pytest.mark.parametrize("c", [32, 6])          # float4 path (c % 4 == 0) and the scalar path
+def test_pooling_upsampling_relu_add_pack(nn, c):
     r = _rng(4)
-    n, h, w, c = 2, 10, 14, 32
+    n, h, w = 2, 10, 14
     x = r.normal(0, 1, (n, h, w, c)).astype(np.float32)
     xd = _dev(x)                       # every device input is held by a name while kernels use it
     y = torch.empty((n, h // 2, w // 2, c), device="cuda")
