@@ -476,6 +476,20 @@ __global__ void up2_bwd4(const float4* __restrict__ dy, float4* __restrict__ dx,
                       (a.w + bb.w) + (cc.w + d.w));
 }
 
+// float4 forms of relu_bwd and add (n % 4 == 0, 16-byte aligned pointers)
+__global__ void relu_bwd4(const float4* dy, const float4* __restrict__ y, float4* dx, long long n4) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  const float4 g = dy[i], v = y[i];
+  dx[i] = make_float4(v.x > 0.f ? g.x : 0.f, v.y > 0.f ? g.y : 0.f, v.z > 0.f ? g.z : 0.f, v.w > 0.f ? g.w : 0.f);
+}
+__global__ void add4(float4* z, const float4* x, const float4* y, float a, long long n4) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  const float4 u = x[i], v = y[i];
+  z[i] = make_float4(u.x + a * v.x, u.y + a * v.y, u.z + a * v.z, u.w + a * v.w);
+}
+
 // z = x + a y (z may be x or y)
 __global__ void add(float* z, const float* x, const float* y, float a, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -734,7 +748,14 @@ int lbm_nn_flip_transpose(const void* wt_bf16, void* wf_bf16, int cin, int cout,
 
 int lbm_nn_relu_bwd(const float* dy, const float* y, float* dx, long long n, void* stream) {
   if (!dy || !y || !dx || n < 0) return -1;
-  if (n) relu_bwd<<<blocks(n), 256, 0, (cudaStream_t)stream>>>(dy, y, dx, n);
+  if (n % 4 == 0 && ((uintptr_t)dy | (uintptr_t)y | (uintptr_t)dx) % 16 == 0) {
+    if (n)
+      relu_bwd4<<<blocks(n / 4), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float4*>(dy),
+                                                                  reinterpret_cast<const float4*>(y),
+                                                                  reinterpret_cast<float4*>(dx), n / 4);
+  } else if (n) {
+    relu_bwd<<<blocks(n), 256, 0, (cudaStream_t)stream>>>(dy, y, dx, n);
+  }
   return status(cudaGetLastError());
 }
 
@@ -780,7 +801,14 @@ int lbm_nn_up2(const float* x, float* y, int n, int h, int w, int c, int backwar
 
 int lbm_nn_add(float* z, const float* x, const float* y, float a, long long n, void* stream) {
   if (!z || !x || !y || n < 0) return -1;
-  if (n) add<<<blocks(n), 256, 0, (cudaStream_t)stream>>>(z, x, y, a, n);
+  if (n % 4 == 0 && ((uintptr_t)z | (uintptr_t)x | (uintptr_t)y) % 16 == 0) {
+    if (n)
+      add4<<<blocks(n / 4), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<float4*>(z),
+                                                             reinterpret_cast<const float4*>(x),
+                                                             reinterpret_cast<const float4*>(y), a, n / 4);
+  } else if (n) {
+    add<<<blocks(n), 256, 0, (cudaStream_t)stream>>>(z, x, y, a, n);
+  }
   return status(cudaGetLastError());
 }
 

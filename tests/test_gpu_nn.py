@@ -141,16 +141,17 @@ def test_pooling_upsampling_relu_add_pack(nn, c):
     ua = torch.empty((n, h // 2, w // 2, c), device="cuda")
     nn.up2(xd.data_ptr(), ua.data_ptr(), n, h // 2, w // 2, c, backward=True)
     np.testing.assert_allclose(ua.cpu().numpy(), onn.up2_adj(x.astype(np.float64)), rtol=1e-6, atol=1e-6)
-    # ReLU adjoint, out of place and in place
-    yv = r.normal(0, 1, 1000).astype(np.float32)
-    dy = r.normal(0, 1, 1000).astype(np.float32)
-    dyd, yvd, out = _dev(dy), _dev(yv), torch.empty(1000, device="cuda")
-    nn.relu_bwd(dyd.data_ptr(), yvd.data_ptr(), out.data_ptr(), 1000)
+    # ReLU adjoint, out of place and in place; add (m = 1000: float4 path, 999: scalar path)
+    m = 1000 if c % 4 == 0 else 999
+    yv = r.normal(0, 1, m).astype(np.float32)
+    dy = r.normal(0, 1, m).astype(np.float32)
+    dyd, yvd, out = _dev(dy), _dev(yv), torch.empty(m, device="cuda")
+    nn.relu_bwd(dyd.data_ptr(), yvd.data_ptr(), out.data_ptr(), m)
     np.testing.assert_array_equal(out.cpu().numpy(), np.where(yv > 0, dy, 0.0))
-    nn.relu_bwd(dyd.data_ptr(), yvd.data_ptr(), dyd.data_ptr(), 1000)
+    nn.relu_bwd(dyd.data_ptr(), yvd.data_ptr(), dyd.data_ptr(), m)
     np.testing.assert_array_equal(dyd.cpu().numpy(), np.where(yv > 0, dy, 0.0))
     a, b = _dev(dy), _dev(yv)
-    nn.add(a.data_ptr(), a.data_ptr(), b.data_ptr(), -0.5, 1000)
+    nn.add(a.data_ptr(), a.data_ptr(), b.data_ptr(), -0.5, m)
     np.testing.assert_array_equal(a.cpu().numpy(), (dy + np.float32(-0.5) * yv).astype(np.float32))
     # network input
     phi0 = r.uniform(0, 1, (n, h, w)).astype(np.float32)
