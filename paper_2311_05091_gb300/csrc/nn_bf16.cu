@@ -355,6 +355,7 @@ __global__ void sum_parts(const float* __restrict__ part, float* __restrict__ ou
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float s = 0.f;
+#pragma unroll 8
   for (int z = 0; z < chunks; ++z) s += part[(long long)z * n + i];
   out[i] = s;
 }
