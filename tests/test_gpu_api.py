@@ -170,3 +170,25 @@ def test_context_on_the_torch_caching_allocator(lbm_lib):
     for a, b in zip(got, want):
         np.testing.assert_array_equal(a, b)
     assert torch.cuda.memory_allocated() == before
+
+
+def test_d3q19_context_on_the_torch_caching_allocator(lbm_lib):
+    """The 3D pipelined kernel's tensor maps are built on the caller's memory: bitwise the default context's run."""
+    import torch
+    L = lbm_lib
+    n = 24
+    zc, yc, xc = np.mgrid[:n, :n, :n] + 0.5
+    phi1 = (0.5 + 0.5 * np.tanh((6.0 - np.sqrt((xc - 12) ** 2 + (yc - 12) ** 2 + (zc - 12) ** 2)) / 2.0))
+    prm = L.lbm_default_params(d0=1.0 / 3.0, sigma=0.01)
+    out = []
+    for alloc in (None, L.TorchAllocator()):
+        ctx = L.Context(L.LBM_D3Q19, n, n, n, periodic=(True, True, True), params=prm, allocator=alloc)
+        try:
+            ctx.set_solid(np.zeros((n, n, n), np.float32))
+            ctx.set_phase(phi1.astype(np.float32))
+            ctx.step(60)
+            out.append(ctx.get_fields())
+        finally:
+            ctx.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)

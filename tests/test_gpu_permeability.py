@@ -86,3 +86,32 @@ def test_phase_flux_validation(lbm_lib):
             ctx.phase_flux(1, 0)               # one instance
     finally:
         ctx.close()
+
+
+def test_phase_flux_of_uneven_instances(lbm_lib):
+    """lbm_phase_flux on a multi-size context reads each instance's own block."""
+    L = lbm_lib
+    sizes = [(32, 24), (48, 40)]
+    def disk(nx, ny):
+        y, x = np.mgrid[:ny, :nx] + 0.5
+        return (0.5 + 0.5 * np.tanh((6.0 - np.hypot(x - nx / 3, y - ny / 2)) / 2.0)).astype(np.float32)
+    phi0s = [disk(nx, ny) for nx, ny in sizes]
+    phi1s = [((1 - p) * (0.5 + 0.5 * np.tanh((np.mgrid[:p.shape[0], :p.shape[1]][0] + 0.5 - p.shape[0] / 2) / 2.0)))
+             .astype(np.float32) for p in phi0s]
+    m = L.MultiContext(sizes, periodic=(True, True),
+                       batch=[L.lbm_default_params(body_force=(1e-5, 0.0, 0.0)) for _ in sizes])
+    try:
+        m.set_solid(phi0s)
+        m.set_phase(phi1s)
+        m.step(50)
+        fields = m.get_fields()
+        for i, (nx, ny) in enumerate(sizes):
+            fl = L.lbm_phase_flux(m.ctx, i, 0)
+            ph, u = fields[i][0], fields[i][1]
+            ref = ob.phase_flux(phi0s[i].astype(np.float64), ph.reshape(ny, nx).astype(np.float64),
+                                u.reshape(2, ny, nx).astype(np.float64), axis=0)
+            for k in ("q1", "q2", "q"):
+                assert np.isclose(fl[k], ref[k], rtol=1e-9, atol=1e-15), (i, k)
+            assert fl["n_pore"] == ref["n_pore"]
+    finally:
+        m.close()
