@@ -27,7 +27,7 @@ Per step, in the paper's order (Sec. 2 and 3):
 10. NS collision  g* = g - L(g - g^eq) + (I - L/2) F_i.
 11. Streaming with half-way bounce-back; history <- (phi1, u, S).
 
-Readings where the paper is silent (all listed in the design doc):
+Readings where the paper is silent:
 * S with frozen phi0 is (rho1 - rho2) M grad(mubar_1) / gamma_1.
 * F_c and the Euler derivatives use the stored step n-1 fields; the history
   starts as (phi1^0, u = 0, S = 0).
@@ -400,7 +400,7 @@ class InOut:
 
 
 def inout_boundaries(st: State):
-    """Replace the post-streaming populations of the boundary columns (readings in the design doc):
+    """Replace the post-streaming populations of the boundary columns:
 
     f_i(x_b) = f_i(x_f) + f_i^eq(phi_b, u_b) - f_i^eq(phi_f, u_f)
     g_i(x_b) = g_i(x_f) + g_i^eq(p_b, rho_b, u_b) - g_i^eq(p_f, rho_f, u_f)

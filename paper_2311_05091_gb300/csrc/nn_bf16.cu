@@ -2,7 +2,7 @@
 // that maps (solid indicator, initial phase field, cos theta) to a phase field
 // close to equilibrium, followed by plain lattice Boltzmann relaxation.  The
 // network is not part of the paper; it is a throughput device for the
-// method (the paper's steps stay the judge of the final state).
+// method (the paper's steps still decide the final state).
 //
 // Tensors are NHWC float32 in memory (pixel p = (n h + y) w + x, channel
 // innermost).  3x3 convolutions run on the tensor cores with BF16 operands

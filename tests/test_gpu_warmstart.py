@@ -4,7 +4,7 @@ A three-level network is trained on the GPU by the library's own kernels on
 solver-generated labels (64^2 lattices of the batched distribution, labels
 after T plain steps), then evaluated on held-out seeds: K plain steps from the
 warm-start field against K plain steps from the initial field, both measured
-against the T-step plain run (the method itself is the judge).  The warm
+against the T-step plain run (the method itself decides).  The warm
 start must cut the error of the short run clearly, and the lattice Boltzmann
 steps after it must keep the phase mass of the initial field."""
 import numpy as np
