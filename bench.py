@@ -391,7 +391,7 @@ def run_gpu_batch(args):
     m.set_phase([i["phi1"] for i in inst])
     m.step(args.warmup)
     m.sync()
-    strips = m.tune(10)
+    strips = m.tune(args.tune_trial if args.tune_trial > 0 else 10)
     clocks = Clocks()
     barrier(world)
     torch.cuda.synchronize()
