@@ -87,6 +87,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 constexpr int kTcM = 128;
+constexpr int kTcThreads = 256;   // 8 warps stage the tiles; warps w and w + 4 share TMEM lane quarter w % 4
 
 // (A, B) tiles in S stages: with two, one chunk is staged while the tensor cores multiply the previous one.
 // Two stages pay only where the tiles are small enough to keep several CTAs per SM (measured on GB300: wide
@@ -106,7 +107,7 @@ struct FwdTcSmem {
 // further, and its 128 rows stay 16 bytes apart.  Otherwise (R > 1 rows per CTA) the rows of the window cross
 // image rows, so the input is staged once per column offset kx as described above.
 template <int N, bool WIDE>
-__global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc(const float* __restrict__ x,
+__global__ void __launch_bounds__(kTcThreads) conv3x3_fwd_tc(const float* __restrict__ x,
                                                            const __nv_bfloat16* __restrict__ wt,
                                                            const float* __restrict__ bias, float* __restrict__ y,
                                                            int n, int h, int w, int cin, int cout, int relu,
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc(const float* __restri
     // A: WIDE, one copy of rows y0 - 1 .. y0 + 1 at columns x0 - 1 .. x0 + 128; else one copy per kx
     // (unrolled so that several iterations' global loads are in flight before their conversions)
 #pragma unroll 4
-    for (int e = tid; e < (WIDE ? 2 : 6) * rows * pitch; e += kThreads) {
+    for (int e = tid; e < (WIDE ? 2 : 6) * rows * pitch; e += kTcThreads) {
       const int px = e % pitch, r = (e / pitch) % rows, kc = (e / (pitch * rows)) & 1;
       const int kx = WIDE ? 0 : e / (pitch * rows * 2);
       const int yy = y0 + r - 1, xc = x0 + px + kx - 1;
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc(const float* __restri
     }
     // B: weights of the nine taps
 #pragma unroll 4
-    for (int e = tid; e < 18 * N; e += kThreads) {
+    for (int e = tid; e < 18 * N; e += kTcThreads) {
       const int co = e % N, kc = (e / N) & 1, tap = e / (2 * N);
       const uint4 v =
           *reinterpret_cast<const uint4*>(wt + ((long long)tap * cout + co0 + co) * cin + ci0 + 8 * kc);
@@ -198,19 +199,21 @@ __global__ void __launch_bounds__(kThreads) conv3x3_fwd_tc(const float* __restri
   ok = ok && mbar_wait(bar0 + 8 * ((nchunks - 1) % S), ((nchunks - 1) / S) & 1);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    const int m = warp * 32 + lane;
+    const int q = warp & 3;                                // TMEM lane quarter of this warp
+    const int m = q * 32 + lane;
     const int yo = y0 + m / W, xo = x0 + m % W;
     const bool valid = yo < h && xo < w;
     float* dst = y + (((long long)img * h + yo) * w + xo) * cout + co0;
+    constexpr int HALF = N / 2;                            // warps 0-3 take columns 0 .. N/2, warps 4-7 the rest
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += 16) {
+    for (int c0 = (warp >> 2) * HALF; c0 < (warp >> 2) * HALF + HALF; c0 += 16) {
       uint32_t r[16];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
           "%14, %15}, [%16];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
             "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+          : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (valid) {
 #pragma unroll
@@ -665,7 +668,8 @@ int lbm_nn_conv3x3(const float* x, const void* wt_bf16, const float* bias, float
   const dim3 grid((unsigned)segs, cout / N);
   const bool wide = R == 1;
 #define LBM_NN_FWD(NN, WD)                                                                                        \
-  conv3x3_fwd_tc<NN, WD><<<grid, kThreads, FwdTcSmem<NN, WD>::bytes(), s>>>(x, wb, bias, y, n, h, w, cin, cout, relu, R)
+  conv3x3_fwd_tc<NN, WD><<<grid, kTcThreads, FwdTcSmem<NN, WD>::bytes(), s>>>(x, wb, bias, y, n, h, w, cin, cout, relu, \
+                                                                              R)
   if (N == 128) {
     if (wide) LBM_NN_FWD(128, true); else LBM_NN_FWD(128, false);
   } else if (N == 64) {
