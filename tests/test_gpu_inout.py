@@ -137,6 +137,12 @@ def test_set_inout_validation(lbm_lib):
             ctx.set_inout(4)
     finally:
         ctx.close()
+    ctx = L.Context(L.LBM_D2Q9, 3, 8, 1, periodic=(False, False, False))
+    try:
+        with pytest.raises(L.LbmError):            # inlet and outlet columns need nx >= 4
+            ctx.set_inout(2, None, -1.0, 0.0)
+    finally:
+        ctx.close()
 
 
 def test_inout_batch_equals_single_runs(lbm_lib):

@@ -115,3 +115,18 @@ def test_phase_flux_of_uneven_instances(lbm_lib):
             assert fl["n_pore"] == ref["n_pore"]
     finally:
         m.close()
+
+
+def test_phase_flux_without_pore_space(lbm_lib):
+    """A fully solid instance: no pore nodes, zero fluxes, undefined saturations (NaN), no error."""
+    L = lbm_lib
+    ctx = L.Context(L.LBM_D2Q9, 16, 8, 1, periodic=(True, True, False))
+    try:
+        ctx.set_solid(np.full((8, 16), 0.99, np.float32))
+        ctx.set_phase(np.zeros((8, 16), np.float32))
+        ctx.step(5)
+        fl = ctx.phase_flux(0, 0)
+    finally:
+        ctx.close()
+    assert fl["n_pore"] == 0 and fl["q"] == 0.0 and fl["q1"] == 0.0 and fl["q2"] == 0.0
+    assert np.isnan(fl["s1"]) and np.isnan(fl["s2"])
