@@ -353,14 +353,22 @@ __global__ void __launch_bounds__(kWgThreads) conv3x3_wgrad_seg(const float* __r
     }
 }
 
-// out[i] = sum_z part[z][i] in chunk order (deterministic)
-__global__ void sum_parts(const float* __restrict__ part, float* __restrict__ out, long long n, int chunks) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// out[i] = sum_z part[z][i]: 8 lanes per output take the chunks z = lane, lane + 8, ... in order, then the 8 lane
+// sums are added in a fixed tree (deterministic).  Block = 32 outputs x 8 lanes.
+__global__ void __launch_bounds__(256) sum_parts(const float* __restrict__ part, float* __restrict__ out, long long n,
+                                                 int chunks) {
+  __shared__ float red[8][32];
+  const int o = threadIdx.x & 31, lane = threadIdx.x >> 5;
+  const long long i = (long long)blockIdx.x * 32 + o;
   float s = 0.f;
-#pragma unroll 8
-  for (int z = 0; z < chunks; ++z) s += part[(long long)z * n + i];
-  out[i] = s;
+  if (i < n) {
+#pragma unroll 4
+    for (int z = lane; z < chunks; z += 8) s += part[(long long)z * n + i];
+  }
+  red[lane][o] = s;
+  __syncthreads();
+  if (lane == 0 && i < n)
+    out[i] = ((red[0][o] + red[1][o]) + (red[2][o] + red[3][o])) + ((red[4][o] + red[5][o]) + (red[6][o] + red[7][o]));
 }
 
 // bias gradient partials: part[z][c] = sum_{p in chunk z} dy[p][c]; block = 32 channels x 8 pixel lanes,
@@ -734,12 +742,12 @@ int lbm_nn_conv3x3_wgrad(const float* x, const float* dy, float* dw, float* db, 
   const long long nw = 9LL * cin * cout;
   dim3 grid((cout + 31) / 32, (cin + 31) / 32, (unsigned)p.chunks);
   conv3x3_wgrad_seg<<<grid, kWgThreads, 0, s>>>(x, dy, work, n, h, w, cin, cout, p.per_chunk);
-  sum_parts<<<blocks(nw), 256, 0, s>>>(work, dw, nw, (int)p.chunks);
+  sum_parts<<<(unsigned)((nw + 31) / 32), 256, 0, s>>>(work, dw, nw, (int)p.chunks);
   if (db) {
     float* bpart = work + p.chunks * nw;
     const long long P = (long long)n * h * w;
     colsum_part<<<dim3((cout + 31) / 32, (unsigned)p.bias_chunks), 256, 0, s>>>(dy, bpart, P, cout, kBiasChunk);
-    sum_parts<<<blocks(cout), 256, 0, s>>>(bpart, db, cout, (int)p.bias_chunks);
+    sum_parts<<<(unsigned)((cout + 31) / 32), 256, 0, s>>>(bpart, db, cout, (int)p.bias_chunks);
   }
   return status(cudaGetLastError());
 }
