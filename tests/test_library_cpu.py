@@ -96,3 +96,18 @@ def test_create_alloc_needs_both_callbacks(lbm_lib):
     st = lib.lbm_create_alloc(lbm_lib.LBM_D2Q9, 16, 8, 1, 3, 0, ctypes.byref(p), 0, None, alloc,
                               lbm_lib.lbm_free_fn(lambda a, b, c, d: None), None, ctypes.byref(out))
     assert st == -1                                   # nbatch 0
+
+
+def test_public_headers_are_plain_c(tmp_path):
+    """include/lbm.h and include/lbm_nn.h compile as strict C11 (a C caller needs no C++ compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_headers.c"
+    src.write_text('#include "lbm.h"\n#include "lbm_nn.h"\n'
+                   "int main(void) { lbm_params p; lbm_flux f; (void)f; return lbm_default_params(&p); }\n")
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
