@@ -170,3 +170,25 @@ def test_inout_batch_equals_single_runs(lbm_lib):
         one = run([prms[b]])
         for a, c in zip(both, one):
             np.testing.assert_array_equal(a[b], c[0])
+
+
+def test_inout_d3q19_fp16_matches_float32(lbm_lib):
+    """FP16 NS populations on a 3D lattice go through the same boundary arithmetic (scaled loads and stores)."""
+    L = lbm_lib
+    nx, ny, nz = 32, 10, 8
+    prm = L.lbm_default_params(rho=(1.0, 1.0, 1.0), mu=(0.1, 0.1, 0.1), d0=1.0 / 3.0)
+    zz, yy = np.mgrid[:nz, :ny] + 0.5
+    prof = 0.03 * (1 - ((yy - ny / 2) / (ny / 2)) ** 2) * (1 - ((zz - nz / 2) / (nz / 2)) ** 2)
+    u_in = np.stack([prof, 0 * prof, 0 * prof]).astype(np.float32)
+    out = []
+    for flags in (0, L.LBM_STORE_G_F16):
+        ctx = L.Context(L.LBM_D3Q19, nx, ny, nz, periodic=(False, False, False), params=prm, flags=flags)
+        try:
+            ctx.set_solid(np.zeros((nz, ny, nx), np.float32))
+            ctx.set_phase(np.ones((nz, ny, nx), np.float32))
+            ctx.set_inout(3, u_in, 1.0, 0.0)
+            ctx.step(400)
+            out.append(ctx.get_fields()[1][0].copy())
+        finally:
+            ctx.close()
+    assert rel_l2(out[1], out[0]) < 2e-3
