@@ -221,6 +221,18 @@ int lbm_set_stream(lbm_ctx* ctx, void* stream);
  * falls back to the generic kernel. */
 int lbm_set_launch(lbm_ctx* ctx, int strip, int depth);
 
+/* Poll limit of the bounded device waits (the paper has no counterpart; a
+ * failure-detection service).  The pipelined 3D kernel waits on an mbarrier
+ * for the TMA tile load of each z plane; after `polls` unsuccessful polls
+ * it stops the step, drains the load still in flight (at the default
+ * limit), and sets a flag that the next synchronising call reports as
+ * LBM_ETIMEOUT; the context stays usable and its state must be set again
+ * (lbm_set_phase or lbm_set_state) before it is trusted.  polls < 0
+ * restores the default (2^22); polls = 0 makes every such wait give up at
+ * once, which is how tests inject the failure without faulting the GPU.
+ * Synchronises the context's stream; applies to later steps. */
+int lbm_set_wait_limit(lbm_ctx* ctx, int polls);
+
 /* Kernel timing.  While enabled, every time step is bracketed by CUDA
  * events recorded on the context's stream, with one more between the D3Q19
  * moment pass and the fused kernel (CUDA-graph replay is off meanwhile).

@@ -30,7 +30,7 @@ EXPORTS = [
     "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
     "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
     "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_kernel_time_split", "lbm_observables_noalloc", "lbm_set_inout",
-    "lbm_phase_flux", "lbm_create_alloc",
+    "lbm_phase_flux", "lbm_create_alloc", "lbm_set_wait_limit",
 ]
 
 # device-memory callbacks of lbm_create_alloc
@@ -96,6 +96,7 @@ def library():
         "lbm_destroy": (None, [P]),
         "lbm_set_stream": (c_int, [P, P]),
         "lbm_set_launch": (c_int, [P, c_int, c_int]),
+        "lbm_set_wait_limit": (c_int, [P, c_int]),
         "lbm_set_solid": (c_int, [P, c_float_p]),
         "lbm_set_solid_device": (c_int, [P, P]),
         "lbm_set_phase": (c_int, [P, c_float_p]),
@@ -246,6 +247,10 @@ def lbm_set_stream(ctx, stream_handle):
 
 def lbm_set_launch(ctx, strip, depth=0):
     _check(library().lbm_set_launch(ctx, strip, depth), "lbm_set_launch", ctx)
+
+
+def lbm_set_wait_limit(ctx, polls):
+    _check(library().lbm_set_wait_limit(ctx, int(polls)), "lbm_set_wait_limit", ctx)
 
 
 def lbm_get_shape(ctx):
@@ -426,6 +431,7 @@ class Context:
 
     def set_stream(self, handle): lbm_set_stream(self.ctx, handle)
     def set_launch(self, strip, depth=0): lbm_set_launch(self.ctx, strip, depth)
+    def set_wait_limit(self, polls): lbm_set_wait_limit(self.ctx, polls)
     def tune(self, trial=10): return lbm_tune(self.ctx, trial, lbm_get_shape(self.ctx)[3])
     def set_solid(self, phi0): lbm_set_solid(self.ctx, phi0)
     def set_phase(self, phi1): lbm_set_phase(self.ctx, phi1)

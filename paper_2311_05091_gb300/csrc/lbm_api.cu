@@ -51,6 +51,7 @@ struct lbm_ctx {
   long long nodes = 0;        // per instance
   int strip = 32;
   int depth = 1;
+  int wait_polls = lbm::kWaitPollsDefault;   // lbm_set_wait_limit
   std::vector<InstanceConsts> hconsts;
   InstanceConsts* dconsts = nullptr;
   float* f[2] = {nullptr, nullptr};
@@ -299,6 +300,7 @@ StepArgs step_args(lbm_ctx* c, int from) {
   a.per_z = c->per[2];
   a.strip = c->strip;
   a.depth = c->depth;
+  a.wait_polls = c->wait_polls;
   a.nodes = c->nodes;
   a.g_half = c->g_half;
   a.q = c->q;
@@ -757,6 +759,15 @@ int lbm_set_launch(lbm_ctx* c, int strip, int depth) {
     for (int b = 0; b < c->nbatch; ++b) c->istrip[b] = std::min(strip, c->iny[b]);
     LBM_CK(c, upload_multi(c));
   }
+  return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_ctx* c, int polls) {
+  if (int s = check_ready(c, false)) return s;
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->wait_polls = polls < 0 ? lbm::kWaitPollsDefault : polls;
+  drop_graphs(c);
+  if (c->multi) LBM_CK(c, upload_multi(c));
   return LBM_OK;
 }
 

@@ -861,7 +861,6 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
 constexpr int PW = 40;                       // halo tile row: columns x0-4 .. x0+35 (16-byte aligned chunks)
 constexpr int PR2 = TY + 4, PR1 = TY + 2;    // rows of the two-halo and one-halo tiles
 constexpr int RP5 = 5;                       // phi ring: z-1 .. z+2 in use, z+3 in flight
-constexpr int kSpinLimit = 1 << 22;          // try_wait polls before a TMA wait gives up
 
 struct TmaMaps {
   CUtensorMap g, j, h;   // g: (nx, ny, nz, QL nb), j: (.., 3 nb), h: (.., 7 nb); boxes 32 x 8 x 1 x {QL, 3, 7}
@@ -898,9 +897,9 @@ __device__ __forceinline__ void bar_expect(unsigned long long* bar, unsigned byt
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-// bounded wait for phase `parity`; returns false when the poll limit is reached
-__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
-  for (int it = 0; it < kSpinLimit; ++it) {
+// bounded wait for phase `parity`; returns false after `polls` unsuccessful polls
+__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity, int polls) {
+  for (int it = 0; it < polls; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -1087,7 +1086,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   for (int z = zs; z < ze; ++z) {
     cp_wait_all();                                      // phi z+2, history z+1
     const unsigned parity = (unsigned)(z - zs) & 1u;
-    if (!bar_wait(&S.bar, parity)) {                    // owned planes of z
+    if (!bar_wait(&S.bar, parity, a.wait_polls)) {      // owned planes of z
       ok = false;
       pending = parity;
     }
@@ -1138,7 +1137,8 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   }
   // leave no copy in flight: asynchronous copies, and a TMA load issued for a plane not processed
   cp_wait_all();
-  if (!ok) (void)bar_wait(&S.bar, pending);   // one more bounded wait for the TMA load that was late
+  // one more bounded wait, at the default limit, for the TMA load that was late
+  if (!ok) (void)bar_wait(&S.bar, pending, kWaitPollsDefault);
 }
 
 }  // namespace

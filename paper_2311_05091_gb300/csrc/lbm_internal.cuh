@@ -59,7 +59,11 @@ struct StepArgs {
   long long nodes;        // nodes per instance
   int g_half;             // NS populations stored as FP16
   int q;                  // lattice directions (9, 15 or 19)
+  int wait_polls;         // polls of a bounded tile-load wait before it gives up (3D pipelined kernel)
 };
+
+// Default poll limit of a bounded device wait (mbarrier try_wait polls).
+constexpr int kWaitPollsDefault = 1 << 22;
 
 // Kernel launchers (return cudaGetLastError of the launch).
 cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, void* g, int g_half,

@@ -56,6 +56,7 @@ def test_null_arguments(lbm_lib):
     assert lib.lbm_default_params(None) == -1
     assert lib.lbm_step(None, 1) == -1
     assert lib.lbm_sync(None) == -1
+    assert lib.lbm_set_wait_limit(None, 0) == -1
     lib.lbm_destroy(None)
 
 
