@@ -311,7 +311,7 @@ def run_reference(args):
     return 0
 
 
-def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5, flags=0):
+def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5, flags=0, tune_trial=40):
     """Contact-angle relaxation of the disk + droplet sweep on a size^2 lattice.
 
     The five instances start from the droplet of the workload recipe (scaled
@@ -321,7 +321,8 @@ def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5, flags=0):
     area relation).  The equilibrium angle of an instance is its last sample;
     its time to equilibrium is the first sample from which every later sample
     stays within tol_deg of it (at least five samples, else None).  Wall time
-    = steps x the device time per step of the same lattice.
+    = steps x the device time per step of the same lattice, at the strip the
+    library's autotuner picks for it (strips change no result bit).
     """
     import torch
     wl = make_workload("disk1024x5", size)
@@ -336,6 +337,7 @@ def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5, flags=0):
         ctx.set_solid(wl["phi0"])
         ctx.set_phase(wl["phi1"])
         ctx.step(64)
+        strip = ctx.tune(tune_trial)[0] if tune_trial > 0 else None
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ctx.step(4096)
@@ -355,7 +357,7 @@ def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5, flags=0):
         ctx.close()
     out = {"workload": wl["name"], "criterion": f"first sample after which theta stays within {tol_deg} deg of "
                                                 f"its value after {total} steps (sampled every {every} steps)",
-           "steps_run": total, "sample_every": every, "ms_per_step": step_ms, "instances": []}
+           "steps_run": total, "sample_every": every, "ms_per_step": step_ms, "strip_tuned": strip, "instances": []}
     for i in range(nb):
         eq = th[i][-1]
         k = len(th[i]) - 1
@@ -565,7 +567,8 @@ def run_gpu(args):
     ctx.close()
     tte = None
     if d == 2 and args.tte_steps > 0 and rank == 0:
-        tte = time_to_equilibrium(L, stream, args.tte_size, args.tte_steps, args.tte_every, flags=flags)
+        tte = time_to_equilibrium(L, stream, args.tte_size, args.tte_steps, args.tte_every, flags=flags,
+                                   tune_trial=args.tune_trial)
 
     if rank != 0:
         return 0
