@@ -212,7 +212,9 @@ void lbm_destroy(lbm_ctx* ctx);
 int lbm_set_stream(lbm_ctx* ctx, void* stream);
 
 /* Launch tuning; results do not depend on it (bitwise).  strip >= 1: rows
- * (D2Q9) or z planes (D3Q19) swept by one CTA of the step kernel.  depth in
+ * (D2Q9) or z planes (D3Q19) swept by one CTA of the step kernel; by default
+ * 16 rows or 32 planes, or, when that gives fewer CTAs than two waves on the
+ * device, the shorter strip a wave model picks.  depth in
  * 1..3 (0 keeps the current value): D2Q9, rows of asynchronous
  * global-to-shared copies each CTA keeps in flight (default 1); D3Q19, 1
  * selects the generic fused kernel (synchronous halo loads), 2 or 3 the

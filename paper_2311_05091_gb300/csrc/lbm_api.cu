@@ -52,6 +52,7 @@ struct lbm_ctx {
   int strip = 32;
   int depth = 1;
   int wait_polls = lbm::kWaitPollsDefault;   // lbm_set_wait_limit
+  int device = 0;             // CUDA device the context was created on
   std::vector<InstanceConsts> hconsts;
   InstanceConsts* dconsts = nullptr;
   float* f[2] = {nullptr, nullptr};
@@ -273,8 +274,29 @@ int default_strip(const lbm_ctx* c) {
   // 16..64 rows on the 1024^2 x 5 workload: shorter strips balance the
   // 152 SMs better than the two-row prologue of each strip costs)
   // 32 planes per CTA for the D3Q19 sweep: 2048 CTAs on 256^3
-  const long long rows = c->lattice == LBM_D2Q9 ? c->ny : c->nz;
-  long long strip = c->lattice == LBM_D2Q9 ? 16 : 32;
+  const bool is2d = c->lattice == LBM_D2Q9;
+  const long long rows = is2d ? c->ny : c->nz;
+  long long strip = is2d ? 16 : 32;
+  // A lattice that gives fewer CTAs than two waves at that strip leaves SMs
+  // idle: take the shorter strip with the least modelled time, waves x (rows
+  // per CTA + the sweep's prologue rows), with 5 (2D) or 2 (3D) resident
+  // CTAs per SM.  The autotuner (lbm_tune) measures instead of modelling.
+  int sms = 0;
+  if (!c->multi && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0) {
+    const long long tiles = is2d ? (c->nx + 127) / 128 : (long long)((c->nx + 31) / 32) * ((c->ny + 7) / 8);
+    const long long slots = (long long)sms * (is2d ? 5 : 2);
+    const long long prologue = is2d ? 4 : 3;
+    auto ctas = [&](long long s) { return tiles * ((rows + s - 1) / s) * c->nbatch; };
+    if (ctas(strip) < 2 * slots) {
+      long long best = strip, best_cost = -1;
+      for (long long s : {4LL, 8LL, 12LL, 16LL, 20LL, 24LL, 32LL}) {
+        if (s > strip) break;
+        const long long cost = ((ctas(s) + slots - 1) / slots) * (std::min(s, rows) + prologue);
+        if (best_cost < 0 || cost < best_cost) best = s, best_cost = cost;
+      }
+      strip = best;
+    }
+  }
   if (strip > rows) strip = rows;
   return (int)std::max(1LL, strip);
 }
@@ -437,6 +459,23 @@ int check_flag(lbm_ctx* c) {
   }
   return LBM_OK;
 }
+
+// Makes the context's device current for one entry point and gives the
+// calling thread its own device back on return, so contexts on different
+// devices can be driven from one thread.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(const lbm_ctx* c) {
+    int cur = -1;
+    if (c && cudaGetDevice(&cur) == cudaSuccess && cur != c->device && cudaSetDevice(c->device) == cudaSuccess)
+      prev = cur;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+};
 
 void free_all(lbm_ctx* c) {
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -621,6 +660,10 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
       return LBM_EINVAL;
     }
   }
+  if (cudaError_t e = cudaGetDevice(&c->device)) {   // the first device call: parameters are valid
+    delete c;
+    return cuda_fail(nullptr, e, "cudaGetDevice");
+  }
   c->strip = default_strip(c);
   c->depth = is3d ? 2 : 1;
   c->g_half = g_half;
@@ -729,6 +772,7 @@ int lbm_create(lbm_lattice lattice, int nx, int ny, int nz, int periodic_mask, c
 }
 
 void lbm_destroy(lbm_ctx* c) {
+  DeviceScope ds(c);
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_all(c);
@@ -736,6 +780,7 @@ void lbm_destroy(lbm_ctx* c) {
 }
 
 int lbm_set_stream(lbm_ctx* c, void* stream) {
+  DeviceScope ds(c);
   if (!c) return set_err(nullptr, LBM_EINVAL, "null context");
   if (c->failed) return check_ready(c, false);
   LBM_CK(c, cudaStreamSynchronize(c->stream));
@@ -748,6 +793,7 @@ int lbm_set_stream(lbm_ctx* c, void* stream) {
 }
 
 int lbm_set_launch(lbm_ctx* c, int strip, int depth) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, false)) return s;
   if (strip < 1) return set_err(c, LBM_EINVAL, "strip must be >= 1");
   if (depth < 0 || depth > 3) return set_err(c, LBM_EINVAL, "depth must lie in 0..3 (0 keeps the current)");
@@ -763,6 +809,7 @@ int lbm_set_launch(lbm_ctx* c, int strip, int depth) {
 }
 
 int lbm_set_wait_limit(lbm_ctx* c, int polls) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, false)) return s;
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   c->wait_polls = polls < 0 ? lbm::kWaitPollsDefault : polls;
@@ -775,6 +822,7 @@ int lbm_set_wait_limit(lbm_ctx* c, int polls) {
 // of `trial` steps (after one untimed step), two passes over the classes.
 // The evolving state is saved before and restored after, bitwise.
 int lbm_tune(lbm_ctx* c, int trial, int* strips_out) {
+  DeviceScope ds(c);
   Range range("lbm_tune");
   if (int s = check_ready(c, true)) return s;
   if (trial < 1) return set_err(c, LBM_EINVAL, "trial must be >= 1");
@@ -869,6 +917,7 @@ int lbm_tune(lbm_ctx* c, int trial, int* strips_out) {
 }
 
 static int set_solid_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, false)) return s;
   if (!src) return set_err(c, LBM_EINVAL, "phi0 is NULL");
   LBM_CK(c, cudaMemcpyAsync(c->phi0, src, sizeof(float) * c->total, kind, c->stream));
@@ -879,10 +928,12 @@ static int set_solid_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
 
 int lbm_set_solid(lbm_ctx* c, const float* phi0_host) { return set_solid_impl(c, phi0_host, cudaMemcpyHostToDevice); }
 int lbm_set_solid_device(lbm_ctx* c, const float* phi0_dev) {
+  DeviceScope ds(c);
   return set_solid_impl(c, phi0_dev, cudaMemcpyDeviceToDevice);
 }
 
 static int set_phase_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, false)) return s;
   if (!src) return set_err(c, LBM_EINVAL, "phi1 is NULL");
   if (!c->solid_set) return set_err(c, LBM_ESTATE, "call lbm_set_solid before lbm_set_phase");
@@ -927,10 +978,12 @@ static int set_phase_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {
 
 int lbm_set_phase(lbm_ctx* c, const float* phi1_host) { return set_phase_impl(c, phi1_host, cudaMemcpyHostToDevice); }
 int lbm_set_phase_device(lbm_ctx* c, const float* phi1_dev) {
+  DeviceScope ds(c);
   return set_phase_impl(c, phi1_dev, cudaMemcpyDeviceToDevice);
 }
 
 int lbm_set_profiling(lbm_ctx* c, int enable) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, false)) return s;
   c->profiling = enable != 0;
   c->ev_used = 0;
@@ -938,6 +991,7 @@ int lbm_set_profiling(lbm_ctx* c, int enable) {
 }
 
 int lbm_kernel_time_split(lbm_ctx* c, double* part_ms, int64_t* steps) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, false)) return s;
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   double t0 = 0.0, t1 = 0.0;
@@ -958,6 +1012,7 @@ int lbm_kernel_time_split(lbm_ctx* c, double* part_ms, int64_t* steps) {
 }
 
 int lbm_kernel_time(lbm_ctx* c, double* total_ms, int64_t* launches) {
+  DeviceScope ds(c);
   double part[2] = {0.0, 0.0};
   int64_t steps = 0;
   if (int s = lbm_kernel_time_split(c, part, &steps)) return s;
@@ -967,6 +1022,7 @@ int lbm_kernel_time(lbm_ctx* c, double* total_ms, int64_t* launches) {
 }
 
 int lbm_set_inout(lbm_ctx* c, int mode, const float* u_in, double phi_in, double p_out) {
+  DeviceScope ds(c);
   if (!c) return set_err(nullptr, LBM_EINVAL, "null context");
   if (c->failed) return LBM_ESTATE;
   if (mode < 0 || mode > 3) return set_err(c, LBM_EINVAL, "mode must be 0..3");
@@ -993,6 +1049,7 @@ int lbm_set_inout(lbm_ctx* c, int mode, const float* u_in, double phi_in, double
 }
 
 int lbm_step(lbm_ctx* c, int n) {
+  DeviceScope ds(c);
   Range range("lbm_step");
   if (int s = check_ready(c, true)) return s;
   if (n < 0) return set_err(c, LBM_EINVAL, "n must be >= 0");
@@ -1015,12 +1072,14 @@ int lbm_step(lbm_ctx* c, int n) {
 }
 
 int lbm_sync(lbm_ctx* c) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, false)) return s;
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   return check_flag(c);
 }
 
 int lbm_get_fields(lbm_ctx* c, float* phi1, float* u, float* p) {
+  DeviceScope ds(c);
   Range range("lbm_get_fields");
   if (int s = check_ready(c, true)) return s;
   const int nh = 1 + 2 * c->d;
@@ -1049,6 +1108,7 @@ int lbm_get_fields(lbm_ctx* c, float* phi1, float* u, float* p) {
 }
 
 int lbm_get_populations(lbm_ctx* c, float* f, float* g) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, true)) return s;
   const size_t n = (size_t)c->q * c->total;
   if (f) LBM_CK(c, cudaMemcpyAsync(f, c->f[c->cur], sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
@@ -1075,6 +1135,7 @@ static size_t state_bytes(const lbm_ctx* c) {
 }
 
 int lbm_get_state(lbm_ctx* c, void* buf, size_t* bytes) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, true)) return s;
   if (!bytes) return set_err(c, LBM_EINVAL, "bytes is NULL");
   const size_t need = state_bytes(c);
@@ -1111,6 +1172,7 @@ int lbm_get_state(lbm_ctx* c, void* buf, size_t* bytes) {
 }
 
 int lbm_set_state(lbm_ctx* c, const void* buf, size_t bytes) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, false)) return s;
   if (!buf || bytes < sizeof(StateHeader)) return set_err(c, LBM_EINVAL, "state image too small");
   StateHeader hd;
@@ -1135,6 +1197,7 @@ int lbm_set_state(lbm_ctx* c, const void* buf, size_t bytes) {
 }
 
 int lbm_observables(lbm_ctx* c, int instance, lbm_obs* out) {
+  DeviceScope ds(c);
   Range range("lbm_observables");
   if (int s = check_ready(c, true)) return s;
   if (!out || instance < 0 || instance >= c->nbatch) return set_err(c, LBM_EINVAL, "bad instance or output");
@@ -1161,6 +1224,7 @@ int lbm_observables(lbm_ctx* c, int instance, lbm_obs* out) {
 }
 
 int lbm_phase_flux(lbm_ctx* c, int instance, int axis, lbm_flux* out) {
+  DeviceScope ds(c);
   Range range("lbm_phase_flux");
   if (int s = check_ready(c, true)) return s;
   if (!out || instance < 0 || instance >= c->nbatch || axis < 0 || axis >= c->d)
@@ -1186,6 +1250,7 @@ int lbm_phase_flux(lbm_ctx* c, int instance, int axis, lbm_flux* out) {
 
 int lbm_contact_angle(lbm_ctx* c, int instance, int mode, int column, double y_c, double disk_radius,
                       double* theta_deg, double* height) {
+  DeviceScope ds(c);
   if (int s = check_ready(c, true)) return s;
   if (c->lattice != LBM_D2Q9) return set_err(c, LBM_EUNSUPPORTED, "contact angle is measured on 2D lattices");
   if (instance < 0 || instance >= c->nbatch || column < 0 || column >= c->inx[instance] || (mode != 0 && mode != 1))

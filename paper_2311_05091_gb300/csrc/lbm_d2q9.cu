@@ -708,15 +708,9 @@ cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, voi
 template <int D, typename GT>
 cudaError_t launch_depth(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
   const size_t smem = step_smem_bytes<D, GT>();
-  static bool configured = false;   // attribute set once per process (both variants)
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(d2q9_step<true, D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(d2q9_step<false, D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};   // devices where both variants were raised
+  if (cudaError_t e = smem_opt_in(configured, smem, d2q9_step<true, D, GT>, d2q9_step<false, D, GT>))
+    return e;
   dim3 block(BX), grid((a.nx + BX - 1) / BX, (a.ny + a.strip - 1) / a.strip, nbatch);
   if (observe) d2q9_step<true, D, GT><<<grid, block, smem, s>>>(a);
   else d2q9_step<false, D, GT><<<grid, block, smem, s>>>(a);
@@ -740,16 +734,9 @@ template <int D, typename GT>
 cudaError_t items_depth(const StepArgs* args, const int4* items, int nitems, int grid, bool observe,
                         cudaStream_t s) {
   const size_t smem = step_smem_bytes<D, GT>();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(d2q9_step_items<true, D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(d2q9_step_items<false, D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};
+  if (cudaError_t e = smem_opt_in(configured, smem, d2q9_step_items<true, D, GT>, d2q9_step_items<false, D, GT>))
+    return e;
   if (grid <= 0) {
     // persistent grid: every SM filled to its occupancy, no more CTAs than items
     int dev = 0, sms = 0, per_sm = 0;

@@ -1214,28 +1214,17 @@ cudaError_t launch_step_q(const StepArgs& a, int nbatch, bool observe, cudaStrea
     TmaMaps m;
     memcpy(&m, maps, sizeof m);
     const size_t smem = sizeof(PipeSmem3<QL, GT>);
-    static bool configured = false;
-    if (!configured) {
-      e = cudaFuncSetAttribute(d3q19_step_pipe<QL, true, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(d3q19_step_pipe<QL, false, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-      if (e != cudaSuccess) return e;
-      configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    e = smem_opt_in(configured, smem, d3q19_step_pipe<QL, true, GT>, d3q19_step_pipe<QL, false, GT>);
+    if (e != cudaSuccess) return e;
     if (observe) d3q19_step_pipe<QL, true, GT><<<grid, NT, smem, s>>>(a, m);
     else d3q19_step_pipe<QL, false, GT><<<grid, NT, smem, s>>>(a, m);
     return cudaGetLastError();
   }
   const size_t smem = sizeof(StepSmem3);
-  static bool configured = false;   // attribute set once per process (both variants)
-  if (!configured) {
-    e = cudaFuncSetAttribute(d3q19_step<QL, true, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(d3q19_step<QL, false, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};   // devices where both variants were raised
+  e = smem_opt_in(configured, smem, d3q19_step<QL, true, GT>, d3q19_step<QL, false, GT>);
+  if (e != cudaSuccess) return e;
   if (observe) d3q19_step<QL, true, GT><<<grid, NT, smem, s>>>(a);
   else d3q19_step<QL, false, GT><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();

@@ -9,7 +9,29 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <initializer_list>
+
 namespace lbm {
+
+// Kernels with more than 48 KB of dynamic shared memory need an opt-in on
+// every device they run on.  `mask` records the device ordinals (bit d) on
+// which `kernels` were already raised to `bytes`; ordinals from 64 up are
+// configured on every call.
+template <typename... K>
+cudaError_t smem_opt_in(std::atomic<unsigned long long>& mask, size_t bytes, K... kernels) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (mask.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  for (const void* k : {reinterpret_cast<const void*>(kernels)...}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
+  mask.fetch_or(bit, std::memory_order_acq_rel);
+  return cudaSuccess;
+}
 
 struct InstanceConsts {
   // lattice (cs2 = d0, weights of the scale-factor lattice)

@@ -32,12 +32,12 @@ def test_flat_wall_1000_steps_ragged(lbm_lib):
     # 150 columns = one full 128-column strip plus a ragged tail; 48 rows in strips of 16
     geo = wall_droplet(150, 48, 8, 16.0, 4.0, xc=75.0)
     prm = dict(theta_deg=60.0, sigma=0.01, d0=0.5)
-    st, obs, errs = _compare(lbm_lib, "D2Q9", geo, prm, (True, False), 1000)
+    st, obs, errs = _compare(lbm_lib, "D2Q9", geo, prm, (True, False), 1000, strip=16)
     # mass and contact angle against the oracle
     assert abs(obs["mass1"] - oobs.mass(st.macro["phi1"])) <= 1e-5 * obs["mass1"]
     th_o = oobs.flat_wall_angle(geo.phi0.astype(np.float32).astype(np.float64), st.macro["phi1"], 75)[0]
     phi0, phi1 = as_inputs(geo)
-    ctx = gpu_run(lbm_lib, "D2Q9", phi0, phi1, prm, (True, False), 1000)
+    ctx = gpu_run(lbm_lib, "D2Q9", phi0, phi1, prm, (True, False), 1000, strip=16)
     try:
         th_g, _ = ctx.contact_angle(0, 0, 75)
     finally:
