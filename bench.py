@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--kp-steps", type=int, default=40000, help="relative permeability: steps of every run")
     ap.add_argument("--tune-trial", type=int, default=40,
                     help="steps per candidate of the strip autotuner before timing (0: the library's default strip)")
+    ap.add_argument("--strip", type=int, default=0,
+                    help="run at this strip (rows / planes per CTA) instead of tuning; results are bitwise the same")
     ap.add_argument("--ws-train", type=int, default=2000, help="warm start: training samples")
     ap.add_argument("--ws-eval", type=int, default=200, help="warm start: held-out samples")
     ap.add_argument("--ws-iters", type=int, default=10000, help="warm start: training iterations")
@@ -393,7 +395,11 @@ def run_gpu_batch(args):
     m.set_phase([i["phi1"] for i in inst])
     m.step(args.warmup)
     m.sync()
-    strips = m.tune(args.tune_trial if args.tune_trial > 0 else 10)
+    if args.strip > 0:
+        m.set_launch(args.strip)
+        strips = [min(args.strip, i["ny"]) for i in inst]
+    else:
+        strips = m.tune(args.tune_trial if args.tune_trial > 0 else 10)
     clocks = Clocks()
     barrier(world)
     torch.cuda.synchronize()
@@ -447,7 +453,8 @@ def run_gpu_batch(args):
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["name"], "lattice": "D2Q9", "instances": len(inst), "lu_per_step": total,
-                   "bytes_per_lu": spec["bytes_per_lu"], "strips_tuned": strips,
+                   "bytes_per_lu": spec["bytes_per_lu"], "strips_tuned": strips if args.strip <= 0 else None,
+                   "strip_fixed": args.strip or None,
                    "l2": f"no flush: each step moves about {spec['bytes_per_lu'] * total / 1e9:.2f} GB through HBM",
                    "parallelism": f"weak, {world} x independent copies of the batch"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -521,7 +528,11 @@ def run_gpu(args):
     ctx.step(args.warmup)
     ctx.sync()
     # the library's autotuner picks the strip (rows / planes per CTA) by timing; the state is restored bitwise
-    strip_tuned = ctx.tune(args.tune_trial)[0] if args.tune_trial > 0 else None
+    if args.strip > 0:
+        ctx.set_launch(args.strip)
+        strip_tuned = None
+    else:
+        strip_tuned = ctx.tune(args.tune_trial)[0] if args.tune_trial > 0 else None
 
     # ---- device-resident timed region: K steps replayed from CUDA graphs ----
     clocks = Clocks()
@@ -586,7 +597,7 @@ def run_gpu(args):
            "thetas": [p["theta_deg"] for p in wl["params"]], "d0": wl["params"][0]["d0"], "W": 4.0,
            "lu_per_step": lu, "bytes_per_lu": spec["bytes_per_lu"],
            "l2": f"no flush: each step moves about {2 * rw:.2f} GB through HBM (> 129 MB L2)",
-           "strip_tuned": strip_tuned,
+           "strip_tuned": strip_tuned, "strip_fixed": args.strip or None,
            "parallelism": f"weak, {world} x independent copies of the workload"}
     cfg["storage"] = ("NS populations FP16 (g * 2^12), CH populations and arithmetic float32" if flags
                       else "float32 populations")
