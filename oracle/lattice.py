@@ -19,8 +19,11 @@ d0 (Sec. 3, below Eq. of f_i^eq).
   valid for 0 < d0 < 1/2.  Because the plain Hermite polynomials are not
   w-orthogonal on D3Q19, N is built by w-weighted Gram-Schmidt of the monomial
   rows in the order listed, which is the "row transformation" the paper asks
-  for on D3Q15 (end of Appendix A).  Parity for D3Q19 is pinned only by those
-  moment conditions, orthogonality and the physics tests.
+  for on D3Q15 (end of Appendix A).  Pinned by those moment conditions,
+  orthogonality, and the 3D shear-wave decay at nu k^2 along an axis and a
+  face diagonal (its second-order rows and their rate groups).  Parity
+  unpinned: the third- and fourth-order rows, whose rates are free (1 by
+  default) and enter no law the paper states.
 
 The relaxation-rate group of every moment row is returned as ``groups``
 (labels "s0", "s1", "s2a", "s2b", "s3", "s4"), matching the printed K.

@@ -257,7 +257,12 @@ def ns_forcing(lat, u, gradrho, Ft, M2F):
 
 
 def pressure_constants(lat, d0, s0, s2a):
-    """K and H of the pressure formula (Sec. 3, after the fluid-structure force)."""
+    """K and H of the pressure formula (Sec. 3, after the fluid-structure force).
+
+    The 2D constants are the printed D2Q9 ones; the 3D ones are taken as printed
+    for D3Q15 and used for D3Q19 too.  H multiplies u . grad rho, which vanishes at
+    rest, so the pressure pins (equilibrium pressure, Laplace law) do not reach it:
+    parity unpinned for H beyond the oracle-vs-GPU comparison."""
     if lat.d == 2:
         K = 1.0 - d0
         H = K * ((1.0 - d0) / s0 - (2.0 - 4.0 * d0) / s2a + (1.0 - 3.0 * d0) / 2.0)
