@@ -394,7 +394,8 @@ cudaError_t upload_multi(lbm_ctx* c) {
 cudaError_t launch_step(lbm_ctx* c, int from, bool observe, cudaStream_t s, cudaEvent_t mid = nullptr) {
   if (c->multi) {
     if (mid) cudaEventRecord(mid, s);
-    return lbm::launch_d2q9_items(c->dargs[from], c->ditems, c->nitems, c->depth, c->g_half, 0, observe, s);
+    return lbm::launch_d2q9_items(c->dargs[from], c->ditems, c->nitems, c->depth, c->g_half, 0, observe,
+                                  c->per[0] && c->per[1], s);
   }
   const StepArgs a = step_args(c, from);
   cudaError_t e = cudaSuccess;

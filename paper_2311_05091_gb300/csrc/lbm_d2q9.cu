@@ -262,7 +262,8 @@ template <int D, typename GT>
 constexpr size_t step_smem_bytes() { return sizeof(StepSmem<D, GT>); }
 
 // One CTA's work: columns x0 .. x0+127 and rows ys .. ys+strip-1 of instance b.
-template <bool OBS, int D, typename GT>
+// PER: both axes periodic (known at compile time), so no push can meet a wall
+template <bool OBS, int D, typename GT, bool PER>
 __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S, const int x0, const int ys,
                                           const int b) {
   constexpr bool kHalf = std::is_same<GT, __half>::value;
@@ -538,8 +539,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
 
       // destinations of the nine pushes without branches: per axis and sign the
       // neighbour's offset (periodic wrap folded in) and whether a wall reflects
-      const bool wxp = x + 1 >= nx && !per_x, wxm = x == 0 && !per_x;
-      const bool wyp = y + 1 >= ny && !per_y, wym = y == 0 && !per_y;
+      const bool wxp = !PER && x + 1 >= nx && !per_x, wxm = !PER && x == 0 && !per_x;
+      const bool wyp = !PER && y + 1 >= ny && !per_y, wym = !PER && y == 0 && !per_y;
       const int oxp = x + 1 < nx ? 1 : 1 - nx, oxm = x > 0 ? -1 : nx - 1;
       const int oyp = y + 1 < ny ? nx : nx - pl, oym = y > 0 ? -nx : pl - nx;
       auto store = [&](auto* __restrict__ out, int i, int io, int cx, int cy, float v) {
@@ -667,17 +668,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
 }
 
 // one tile per CTA: grid (column tiles, row strips, instances)
-template <bool OBS, int D, typename GT>
+template <bool OBS, int D, typename GT, bool PER>
 __global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<D, GT>& S = *reinterpret_cast<StepSmem<D, GT>*>(smem_raw);
-  step_tile<OBS, D, GT>(a, S, blockIdx.x * BX, blockIdx.y * a.strip, blockIdx.z);
+  step_tile<OBS, D, GT, PER>(a, S, blockIdx.x * BX, blockIdx.y * a.strip, blockIdx.z);
 }
 
 // Persistent form for instances of different sizes: CTA k takes work items
 // k, k + gridDim.x, ...; item = (instance, x0, ys), with per-instance launch
 // arguments (base pointers of that instance, its sizes and strip).
-template <bool OBS, int D, typename GT>
+template <bool OBS, int D, typename GT, bool PER>
 __global__ void __launch_bounds__(BX, 5) d2q9_step_items(const StepArgs* __restrict__ args,
                                                       const int4* __restrict__ items, int nitems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -685,7 +686,7 @@ __global__ void __launch_bounds__(BX, 5) d2q9_step_items(const StepArgs* __restr
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 w = items[it];
     const StepArgs a = args[w.x];
-    step_tile<OBS, D, GT>(a, S, w.y, w.z, 0);
+    step_tile<OBS, D, GT, PER>(a, S, w.y, w.z, 0);
     __syncthreads();   // shared memory is reused by the next item
   }
 }
@@ -705,16 +706,22 @@ cudaError_t launch_d2q9_init(const float* phi0, const float* phi1, float* f, voi
   return cudaGetLastError();
 }
 
-template <int D, typename GT>
-cudaError_t launch_depth(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+template <int D, typename GT, bool PER>
+cudaError_t launch_per(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
   const size_t smem = step_smem_bytes<D, GT>();
   static std::atomic<unsigned long long> configured{0};   // devices where both variants were raised
-  if (cudaError_t e = smem_opt_in(configured, smem, d2q9_step<true, D, GT>, d2q9_step<false, D, GT>))
+  if (cudaError_t e = smem_opt_in(configured, smem, d2q9_step<true, D, GT, PER>, d2q9_step<false, D, GT, PER>))
     return e;
   dim3 block(BX), grid((a.nx + BX - 1) / BX, (a.ny + a.strip - 1) / a.strip, nbatch);
-  if (observe) d2q9_step<true, D, GT><<<grid, block, smem, s>>>(a);
-  else d2q9_step<false, D, GT><<<grid, block, smem, s>>>(a);
+  if (observe) d2q9_step<true, D, GT, PER><<<grid, block, smem, s>>>(a);
+  else d2q9_step<false, D, GT, PER><<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int D, typename GT>
+cudaError_t launch_depth(const StepArgs& a, int nbatch, bool observe, cudaStream_t s) {
+  return (a.per_x && a.per_y) ? launch_per<D, GT, true>(a, nbatch, observe, s)
+                              : launch_per<D, GT, false>(a, nbatch, observe, s);
 }
 
 template <typename GT>
@@ -730,42 +737,50 @@ cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaSt
   return a.g_half ? launch_typed<__half>(a, nbatch, observe, s) : launch_typed<float>(a, nbatch, observe, s);
 }
 
-template <int D, typename GT>
-cudaError_t items_depth(const StepArgs* args, const int4* items, int nitems, int grid, bool observe,
-                        cudaStream_t s) {
+template <int D, typename GT, bool PER>
+cudaError_t items_per(const StepArgs* args, const int4* items, int nitems, int grid, bool observe,
+                      cudaStream_t s) {
   const size_t smem = step_smem_bytes<D, GT>();
   static std::atomic<unsigned long long> configured{0};
-  if (cudaError_t e = smem_opt_in(configured, smem, d2q9_step_items<true, D, GT>, d2q9_step_items<false, D, GT>))
+  if (cudaError_t e =
+          smem_opt_in(configured, smem, d2q9_step_items<true, D, GT, PER>, d2q9_step_items<false, D, GT, PER>))
     return e;
   if (grid <= 0) {
     // persistent grid: every SM filled to its occupancy, no more CTAs than items
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, d2q9_step_items<false, D, GT>, BX, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, d2q9_step_items<false, D, GT, PER>, BX, smem);
     grid = sms * (per_sm > 0 ? per_sm : 1);
   }
   if (grid > nitems) grid = nitems;
   if (grid < 1) return cudaSuccess;
-  if (observe) d2q9_step_items<true, D, GT><<<grid, BX, smem, s>>>(args, items, nitems);
-  else d2q9_step_items<false, D, GT><<<grid, BX, smem, s>>>(args, items, nitems);
+  if (observe) d2q9_step_items<true, D, GT, PER><<<grid, BX, smem, s>>>(args, items, nitems);
+  else d2q9_step_items<false, D, GT, PER><<<grid, BX, smem, s>>>(args, items, nitems);
   return cudaGetLastError();
+}
+
+template <int D, typename GT>
+cudaError_t items_depth(const StepArgs* args, const int4* items, int nitems, int grid, bool observe, bool periodic,
+                        cudaStream_t s) {
+  return periodic ? items_per<D, GT, true>(args, items, nitems, grid, observe, s)
+                  : items_per<D, GT, false>(args, items, nitems, grid, observe, s);
 }
 
 template <typename GT>
 cudaError_t items_typed(const StepArgs* args, const int4* items, int nitems, int depth, int grid, bool observe,
-                        cudaStream_t s) {
+                        bool periodic, cudaStream_t s) {
   switch (depth) {
-    case 1: return items_depth<1, GT>(args, items, nitems, grid, observe, s);
-    case 3: return items_depth<3, GT>(args, items, nitems, grid, observe, s);
-    default: return items_depth<2, GT>(args, items, nitems, grid, observe, s);
+    case 1: return items_depth<1, GT>(args, items, nitems, grid, observe, periodic, s);
+    case 3: return items_depth<3, GT>(args, items, nitems, grid, observe, periodic, s);
+    default: return items_depth<2, GT>(args, items, nitems, grid, observe, periodic, s);
   }
 }
 
 cudaError_t launch_d2q9_items(const StepArgs* args, const int4* items, int nitems, int depth, int g_half, int grid,
-                              bool observe, cudaStream_t s) {
-  return g_half ? items_typed<__half>(args, items, nitems, depth, grid, observe, s)
-                : items_typed<float>(args, items, nitems, depth, grid, observe, s);
+                              bool observe, bool periodic, cudaStream_t s) {
+  return g_half ? items_typed<__half>(args, items, nitems, depth, grid, observe, periodic, s)
+                : items_typed<float>(args, items, nitems, depth, grid, observe, periodic, s);
 }
 
 }  // namespace lbm
