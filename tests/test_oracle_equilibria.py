@@ -5,7 +5,8 @@ import pytest
 from oracle import lattice as L
 from oracle import lbm as olbm
 
-LATS = [("D2Q9", 0.5), ("D2Q9", 1.0 / 3.0), ("D2Q9", 0.4), ("D3Q19", 1.0 / 3.0), ("D3Q19", 0.3)]
+LATS = [("D2Q9", 0.5), ("D2Q9", 1.0 / 3.0), ("D2Q9", 0.4), ("D3Q19", 1.0 / 3.0), ("D3Q19", 0.3),
+        ("D3Q15", 1.0 / 3.0), ("D3Q15", 0.3)]
 
 
 def _mom(lat, h):
