@@ -127,6 +127,31 @@ typedef struct {
  * no body force.  Returns LBM_EINVAL if p is NULL. */
 int lbm_default_params(lbm_params* p);
 
+/* What the library derives from one parameter set, in float64 before the
+ * kernels round it to float32 (the paper has no counterpart: a diagnostic of
+ * the host derivation of Sec. 2.2, Sec. 3 and Appendix A). */
+typedef struct {
+  double k;          /* wetting closure k(theta, kappa) of Eq. kk                 */
+  double gamma[3];   /* spreading coefficients gamma_0 (solid), gamma_1, gamma_2  */
+  double gamma_T;    /* 3 / (1/gamma_0 + 1/gamma_1 + 1/gamma_2)                    */
+  double eta;        /* eta_1 = eta_hat / gamma_1                                  */
+  double s1_ch;      /* CH first-moment rate 1 / (1/2 + M / (gamma_1 eta_1 cs2))  */
+  double cs2;        /* squared sound speed: d0 rounded to float32, as the kernels */
+  double w[3];       /* weights: rest, axis, and diagonal (D2Q9), edge (D3Q19) or
+                        corner (D3Q15), all from cs2                               */
+  double visc[2];    /* kinematic viscosity nu = (1/s - 1/2) visc[i], s = s2a (i = 0)
+                        or s2b (i = 1) of the NS collision                        */
+  double p_f, p_w;   /* pressure formula prefactor cs2 / (1 - w0) and w0 / (1 - cs2) */
+  double p_K;        /* K of the pressure formula                                 */
+  double p_h[3];     /* H = K (p_h[0] / s0 - p_h[1] / s2a + p_h[2])               */
+} lbm_derived;
+
+/* Fill *out with the constants a context created with `params` on `lattice`
+ * would use.  Host only (no context, no device call).  LBM_EINVAL, with the
+ * reason in lbm_last_error(NULL), for a NULL pointer, an unknown lattice or
+ * parameters lbm_create would reject. */
+int lbm_derive(lbm_lattice lattice, const lbm_params* params, lbm_derived* out);
+
 /* Create a context for one lattice of nx * ny * nz nodes (nz = 1 for D2Q9).
  * Derives k, gamma_p, gamma_T, eta_1 and the CH rate s1 from *p (Sec. 2.2,
  * Sec. 3) on the host in float64 and allocates the device state.  Axes

@@ -30,7 +30,7 @@ EXPORTS = [
     "lbm_set_launch", "lbm_set_solid", "lbm_set_solid_device", "lbm_set_phase", "lbm_set_phase_device",
     "lbm_step", "lbm_sync", "lbm_get_fields", "lbm_get_populations", "lbm_get_state", "lbm_set_state",
     "lbm_observables", "lbm_contact_angle", "lbm_get_shape", "lbm_strerror", "lbm_last_error", "lbm_set_profiling", "lbm_kernel_time", "lbm_kernel_time_split", "lbm_observables_noalloc", "lbm_set_inout",
-    "lbm_phase_flux", "lbm_create_alloc", "lbm_set_wait_limit",
+    "lbm_phase_flux", "lbm_create_alloc", "lbm_set_wait_limit", "lbm_derive",
 ]
 
 # device-memory callbacks of lbm_create_alloc
@@ -43,6 +43,19 @@ class lbm_params(ctypes.Structure):
                 ("kappa", c_double), ("sigma", c_double), ("rho", c_double * 3), ("mu", c_double * 3),
                 ("d0", c_double), ("eta_hat", c_double), ("s_free_ch", c_double), ("s_free_ns", c_double),
                 ("body_force", c_double * 3)]
+
+
+class lbm_derived(ctypes.Structure):
+    _fields_ = [("k", c_double), ("gamma", c_double * 3), ("gamma_T", c_double), ("eta", c_double),
+                ("s1_ch", c_double), ("cs2", c_double), ("w", c_double * 3), ("visc", c_double * 2),
+                ("p_f", c_double), ("p_w", c_double), ("p_K", c_double), ("p_h", c_double * 3)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
 
 class lbm_obs(ctypes.Structure):
@@ -97,6 +110,7 @@ def library():
         "lbm_set_stream": (c_int, [P, P]),
         "lbm_set_launch": (c_int, [P, c_int, c_int]),
         "lbm_set_wait_limit": (c_int, [P, c_int]),
+        "lbm_derive": (c_int, [c_int, ctypes.POINTER(lbm_params), ctypes.POINTER(lbm_derived)]),
         "lbm_set_solid": (c_int, [P, c_float_p]),
         "lbm_set_solid_device": (c_int, [P, P]),
         "lbm_set_phase": (c_int, [P, c_float_p]),
@@ -247,6 +261,13 @@ def lbm_set_stream(ctx, stream_handle):
 
 def lbm_set_launch(ctx, strip, depth=0):
     _check(library().lbm_set_launch(ctx, strip, depth), "lbm_set_launch", ctx)
+
+
+def lbm_derive(lattice, params: lbm_params) -> dict:
+    """The float64 constants a context with these parameters would use (host only)."""
+    out = lbm_derived()
+    _check(library().lbm_derive(lattice, ctypes.byref(params), ctypes.byref(out)), "lbm_derive")
+    return out.as_dict()
 
 
 def lbm_set_wait_limit(ctx, polls):

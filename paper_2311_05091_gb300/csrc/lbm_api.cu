@@ -163,7 +163,7 @@ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
 // Model constants of one instance (Sec. 2.2 Eq. kk and gamma_p; Sec. 3
 // relations for s1, the viscosity relation and the pressure constants).
-int derive(const lbm_params& p, int lattice, InstanceConsts& k, char* why) {
+int derive(const lbm_params& p, int lattice, InstanceConsts& k, char* why, lbm_derived* dv = nullptr) {
   const bool is3d = lattice != LBM_D2Q9;
   const double d0 = p.d0;
   if (!finite_pos(p.W)) return snprintf(why, 128, "W must be > 0"), LBM_EINVAL;
@@ -265,6 +265,28 @@ int derive(const lbm_params& p, int lattice, InstanceConsts& k, char* why) {
     k.h0 = (float)(1.0 - df);
     k.h2 = (float)(2.0 - 4.0 * df);
     k.h3 = (float)((1.0 - 3.0 * df) / 2.0);
+  }
+  if (dv) {   // the same values before rounding, for lbm_derive
+    memset(dv, 0, sizeof(*dv));
+    dv->k = kk;
+    dv->gamma[0] = g0;
+    dv->gamma[1] = g1;
+    dv->gamma[2] = g2;
+    dv->gamma_T = gT;
+    dv->eta = eta;
+    dv->s1_ch = s1c;
+    dv->cs2 = cs2;
+    dv->w[0] = w0;
+    dv->w[1] = wa;
+    dv->w[2] = we;
+    dv->visc[0] = (1.0 - df) / 2.0;
+    dv->visc[1] = df;
+    dv->p_f = cs2 / (1.0 - w0);
+    dv->p_w = w0 / (1.0 - cs2);
+    dv->p_K = is3d ? 1.0 - 2.0 * df : 1.0 - df;
+    dv->p_h[0] = 1.0 - df;
+    dv->p_h[1] = is3d ? 3.0 - 7.0 * df : 2.0 - 4.0 * df;
+    dv->p_h[2] = is3d ? 1.0 - 3.0 * df : (1.0 - 3.0 * df) / 2.0;
   }
   return LBM_OK;
 }
@@ -571,6 +593,16 @@ int timed_step(lbm_ctx* c, bool observe) {
 }  // namespace
 
 extern "C" {
+
+int lbm_derive(lbm_lattice lattice, const lbm_params* p, lbm_derived* out) {
+  if (!p || !out) return set_err(nullptr, LBM_EINVAL, "params and out must not be NULL");
+  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19 && lattice != LBM_D3Q15)
+    return set_err(nullptr, LBM_EINVAL, "unknown lattice");
+  char why[128] = "";
+  InstanceConsts k;
+  if (derive(*p, lattice, k, why, out) != LBM_OK) return set_err(nullptr, LBM_EINVAL, "%s", why);
+  return LBM_OK;
+}
 
 int lbm_default_params(lbm_params* p) {
   if (!p) return LBM_EINVAL;
