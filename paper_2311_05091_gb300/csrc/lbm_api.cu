@@ -741,7 +741,7 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
     int r = 0;
     for (int i = 0; i < 2 && r == 0; ++i)
       r = lbm::build_d3q19_maps(c->g[i], g_half, c->mom, c->hist[i], nx, ny, nz, nbatch, q, c->d3maps[i]);
-    if (r < 0) e = cudaErrorInvalidValue;   // the driver refused a tensor map
+    if (r < 0) e = cudaErrorInvalidValue;   // the CUDA driver refused a tensor map
     c->d3maps_ok = r == 0;
   }
   if (e != cudaSuccess) {
