@@ -102,3 +102,35 @@ def test_k_closure_is_eq_kk_at_90_degrees(lbm_lib):
         d = L.lbm_derive(L.LBM_D2Q9, L.lbm_default_params(theta_deg=90.0, kappa=kappa, sigma=0.01))
         assert math.isclose(d["k"], 9.0 / (1.0 + kappa), rel_tol=1e-14)
         assert math.isclose(d["gamma"][1], 0.01, rel_tol=1e-13) and math.isclose(d["gamma"][2], 0.01, rel_tol=1e-13)
+
+
+def test_random_parameter_sets_agree_with_the_oracle(lbm_lib):
+    # 300 seeded parameter sets over the whole admissible box: the library accepts exactly the sets whose
+    # spreading coefficients the oracle finds positive, and derives the same k, gamma, eta and s_1 for them
+    L = lbm_lib
+    rng = np.random.default_rng(20231109)
+    accepted = rejected = 0
+    for _ in range(300):
+        name = ("D2Q9", "D3Q19", "D3Q15")[rng.integers(3)]
+        # kappa up to 40: gamma_1 = sigma (1 - cos theta) and gamma_2 = sigma (1 + cos theta) are always positive,
+        # gamma_0 = sigma (2 k + cos theta - 1) turns negative once k(theta, kappa) is small enough
+        kappa = float(rng.uniform(-0.9, 3.0) if rng.random() < 0.6 else rng.uniform(3.0, 40.0))
+        kw = dict(theta_deg=float(rng.uniform(1.0, 179.0)), kappa=kappa,
+                  sigma=float(10 ** rng.uniform(-3, -1)), M_deg=float(10 ** rng.uniform(-3, 0)),
+                  eta_hat=float(10 ** rng.uniform(-2, 0)),
+                  d0=float(rng.uniform(0.05, 0.95 if name == "D2Q9" else 0.45)))
+        lattice = {"D2Q9": L.LBM_D2Q9, "D3Q19": L.LBM_D3Q19, "D3Q15": L.LBM_D3Q15}[name]
+        k, gam = omodel.spreading(math.radians(kw["theta_deg"]), kw["kappa"], kw["sigma"])
+        if min(gam) <= 0.0:
+            with pytest.raises(L.LbmError):
+                L.lbm_derive(lattice, _lib_params(L, kw))
+            rejected += 1
+            continue
+        d = L.lbm_derive(lattice, _lib_params(L, kw))
+        c = omodel.constants(_oracle_params(L, kw))
+        assert _rel(d["k"], c.k) < 1e-12, kw
+        assert max(_rel(a, b) for a, b in zip(d["gamma"], c.gamma)) < 1e-9, kw
+        assert _rel(d["eta"], c.eta) < 1e-9, kw
+        assert _rel(d["s1_ch"], c.s_ch["s1"]) < F32, kw
+        accepted += 1
+    assert accepted > 100 and rejected > 10, (accepted, rejected)
