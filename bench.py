@@ -41,23 +41,27 @@ if ROOT not in sys.path:
 METRIC = "coupled CH+NS LBM MLUPS on 1 GB300, % of HBM roofline, time-to-equilibrium"
 FALLBACK_HBM_GBS = 6800.0
 
-# Algorithmic HBM bytes per lattice update.  D2Q9: f, g read + write 144;
-# phi0 4; history (phi1, u, S) read 20 + write 20.  D3Q19: f, g read + write
-# 304; phi0 4; history (phi1, u, S) read 28 + write 28.  Of the D3Q19 bytes
-# the moment pass moves f read 76 + phi1 write 4 and the fused kernel the
-# other 284.  D3Q15: f, g read + write 240, phi0 4, history 56: 300, of which
-# the fused kernel moves 236.
+# Algorithmic HBM bytes per lattice update, by the byte model of the hot-path
+# scope: 2 Q 2 s (populations f and g read and written) + 4 (phi0 read) + 12
+# (phi1 written, read by the stencil, read as the previous step's value) +
+# 2 (2d) 4 (history u and S read and written) + 8 (mubar_1 written by the
+# chemical-potential kernel and read by the collision kernel), less those 8
+# bytes where the two kernels are fused and mubar_1 never leaves shared
+# memory.  D2Q9 (one fused kernel): 144 + 4 + 12 + 32 = 192.  D3Q19: 304 + 4
+# + 12 + 48 = 368, of which the moment pass moves f read 76 + phi1 write 4
+# and the fused kernel the other 288 (its phi1 stencil read included).
+# D3Q15: 240 + 4 + 12 + 48 = 304, moment pass 64, fused kernel 240.
 WORKLOADS = {
-    "disk1024x5": dict(lattice="D2Q9", size=1024, bytes_per_lu=188, kernel="d2q9_step", kernel_bytes_per_lu=188,
+    "disk1024x5": dict(lattice="D2Q9", size=1024, bytes_per_lu=192, kernel="d2q9_step", kernel_bytes_per_lu=192,
                        kernel_src="lbm_d2q9.cu", profile="d2q9_step_disk1024x5.md", launches_per_step=1,
                        oracle_us_per_node_step=2.5),
-    "batch64": dict(lattice="D2Q9", size=None, bytes_per_lu=188, kernel="d2q9_step_items", kernel_bytes_per_lu=188,
+    "batch64": dict(lattice="D2Q9", size=None, bytes_per_lu=192, kernel="d2q9_step_items", kernel_bytes_per_lu=192,
                     kernel_src="lbm_d2q9.cu", profile="d2q9_step_items_batch64.md", launches_per_step=1,
                     oracle_us_per_node_step=2.5),
-    "porous256_d3q15": dict(lattice="D3Q15", size=256, bytes_per_lu=300, kernel="d3q19_step_pipe<15>",
-                            kernel_bytes_per_lu=236, kernel_src="lbm_d3q19.cu", profile="d3q15_step_porous256.md",
+    "porous256_d3q15": dict(lattice="D3Q15", size=256, bytes_per_lu=304, kernel="d3q19_step_pipe<15>",
+                            kernel_bytes_per_lu=240, kernel_src="lbm_d3q19.cu", profile="d3q15_step_porous256.md",
                             launches_per_step=2, oracle_us_per_node_step=7.0),
-    "porous256": dict(lattice="D3Q19", size=256, bytes_per_lu=364, kernel="d3q19_step_pipe", kernel_bytes_per_lu=284,
+    "porous256": dict(lattice="D3Q19", size=256, bytes_per_lu=368, kernel="d3q19_step_pipe", kernel_bytes_per_lu=288,
                       kernel_src="lbm_d3q19.cu", profile="d3q19_step_porous256.md", launches_per_step=2,
                       oracle_us_per_node_step=8.5),
 }
@@ -74,8 +78,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=60.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS) + ["warmstart256", "kp128"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS) + ["warmstart256"])
     ap.add_argument("--size", type=int, default=None, help="lattice side (default: the workload's)")
     ap.add_argument("--g-f16", action="store_true",
                     help="store the NS populations as FP16 (D2Q9; float32 arithmetic and CH populations)")
@@ -83,7 +87,6 @@ def parse():
     ap.add_argument("--tte-steps", type=int, default=150000,
                     help="steps of the time-to-equilibrium run (disk workload; 0 skips it)")
     ap.add_argument("--tte-every", type=int, default=2500, help="contact-angle sampling interval")
-    ap.add_argument("--kp-steps", type=int, default=40000, help="relative permeability: steps of every run")
     ap.add_argument("--tune-trial", type=int, default=40,
                     help="steps per candidate of the strip autotuner before timing (0: the library's default strip)")
     ap.add_argument("--strip", type=int, default=0,
@@ -203,12 +206,15 @@ def make_workload(name, size=None):
     return wl
 
 
-def oracle_sample(wl, steps, cpu_seconds, us_per_node_step):
-    """Time the FP64 oracle (single thread) on a crop of instance 0 of the workload.
+def oracle_sample(wl, steps, cpu_seconds, us_per_node_step, procs=1):
+    """Time the FP64 oracle, as it stands, on a crop of instance 0 of the workload.
 
     The crop is a square (2D) or cube (3D) at the origin sized so that
-    ``steps`` oracle steps take about ``cpu_seconds``; it keeps the
-    workload's periodicity.  Returns (MLUPS, seconds, description).
+    ``steps`` oracle steps take about ``cpu_seconds`` on one core; it keeps
+    the workload's periodicity.  ``procs`` single-threaded processes run the
+    same crop at the same time, one per host core (the oracle itself is one
+    numpy thread); the throughput is their lattice updates over the slowest
+    one's time.  Returns (MLUPS, seconds, description).
     """
     import numpy as np
     d = 2 if wl["lattice"] == "D2Q9" else 3
@@ -247,16 +253,70 @@ print(json.dumps({{"seconds": dt, "lu": int(z["phi0"].size) * {int(steps)}}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     try:
-        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+        runs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                 text=True, env=env) for _ in range(max(1, procs))]
+        outs = [r.communicate() for r in runs]
     finally:
         os.unlink(path)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    res = json.loads(r.stdout.strip().splitlines()[-1])
+    res = []
+    for r, (out, err) in zip(runs, outs):
+        if r.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    secs = max(x["seconds"] for x in res)
+    lu = sum(x["lu"] for x in res)
     crop = "x".join([str(side)] * d)
+    who = "1 thread" if len(res) == 1 else f"{len(res)} single-threaded processes at once, one per host core"
     desc = (f"FP64 oracle, {steps} steps of a {crop} crop at the origin of instance 0 "
-            f"(theta {prm.get('theta_deg', 90.0):g} deg), {res['seconds']:.1f} s, 1 thread")
-    return res["lu"] / res["seconds"] / 1e6, res["seconds"], desc
+            f"(theta {prm.get('theta_deg', 90.0):g} deg), {secs:.1f} s, {who}")
+    return lu / secs / 1e6, secs, desc, steps
+
+
+def cpu_baselines(wl, spec, cpu_seconds):
+    """The oracle on every host core (the reported baseline) and on one core beside it."""
+    cores = os.cpu_count() or 1
+    out = {}
+    mlups, secs, desc, _ = oracle_sample(wl, 8, cpu_seconds, spec["oracle_us_per_node_step"], procs=cores)
+    out = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+    m1, s1, d1, _ = oracle_sample(wl, 8, cpu_seconds, spec["oracle_us_per_node_step"], procs=1)
+    out["single_thread"] = {"value": m1, "unit": "MLUPS", "cores": 1, "sample": d1}
+    return out
+
+
+def loaded_timed_region(step, stream, steps, warmup, world, lead_in_s=1.0):
+    """Clock samples, W warm-up steps and the K timed steps, in that order, on a continuously loaded GPU.
+
+    nvidia-smi samples every 200 ms, far longer than a timed region of a few
+    milliseconds, so the sampler starts before an untimed lead-in of about
+    ``lead_in_s`` seconds of steps; the W warm-up steps follow and then the K
+    timed steps, bracketed by barriers, synchronisation and CUDA events on the
+    library's stream.  Returns (ms of the K steps, clock record).
+    """
+    import torch
+    clocks = Clocks()
+    clocks.start()
+    t0 = time.perf_counter()
+    lead = 0
+    while time.perf_counter() - t0 < lead_in_s and lead < 200000:
+        step(32)
+        lead += 32
+        stream.synchronize()
+    if warmup > 0:
+        step(warmup)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    if clk is not None:
+        clk["window"] = (f"samples over {time.perf_counter() - t0:.2f} s of back-to-back steps: {lead} untimed "
+                         f"lead-in steps, the W warm-up steps, then the K timed steps")
+    return ev0.elapsed_time(ev1), clk
 
 
 def dist_setup(gpus):
@@ -298,14 +358,15 @@ def run_reference(args):
     wl = make_workload(args.workload, args.size)
     total = args.steps + args.warmup
     # a few minutes of oracle work in all, whatever K and W are
-    mlups, secs, desc = oracle_sample(wl, args.steps, 120.0 * args.steps / max(total, 1),
-                                      spec["oracle_us_per_node_step"])
+    cores = os.cpu_count() or 1
+    mlups, secs, desc, ran = oracle_sample(wl, args.steps, 120.0 * args.steps / max(total, 1),
+                                           spec["oracle_us_per_node_step"], procs=cores)
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(ran, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{desc.split(',')[1].strip()} of {wl['name']}; each step one oracle time "
                                    f"step of that crop"},
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if world > 1:
         line["note"] = "rank 0 alone runs the CPU reference"
@@ -393,25 +454,15 @@ def run_gpu_batch(args):
     m.set_stream(stream.cuda_stream)
     m.set_solid([i["phi0"] for i in inst])
     m.set_phase([i["phi1"] for i in inst])
-    m.step(args.warmup)
+    m.step(64)
     m.sync()
     if args.strip > 0:
         m.set_launch(args.strip)
         strips = [min(args.strip, i["ny"]) for i in inst]
     else:
         strips = m.tune(args.tune_trial if args.tune_trial > 0 else 10)
-    clocks = Clocks()
-    barrier(world)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks.start()
-    ev0.record(stream)
-    m.step(args.steps)
-    ev1.record(stream)
-    ev1.synchronize()
-    clk = clocks.stop()
-    barrier(world)
-    ms = max_over_ranks(world, ev0.elapsed_time(ev1))
+    ms, clk = loaded_timed_region(m.step, stream, args.steps, args.warmup, world)
+    ms = max_over_ranks(world, ms)
     m.sync()
     value = world * total * args.steps / (ms * 1e-3) / 1e6
 
@@ -474,10 +525,9 @@ def run_gpu_batch(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         try:
-            mlups, secs, desc = oracle_sample(wl, 8, args.cpu_seconds, spec["oracle_us_per_node_step"])
-            line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc}
+            line["cpu_baseline"] = cpu_baselines(wl, spec, args.cpu_seconds)
         except Exception as e:
-            line["cpu_baseline"] = {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            line["cpu_baseline"] = {"value": None, "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": f"failed: {str(e)[:200]}"}
     print(json.dumps(line), flush=True)
     return 0
@@ -525,9 +575,11 @@ def run_gpu(args):
 
     ctx.set_solid(h_phi0)
     ctx.set_phase(h_phi1)
-    ctx.step(args.warmup)
+    mass0 = [ctx.observables(i)["mass1"] for i in range(nb)]
+    ctx.step(64)
     ctx.sync()
-    # the library's autotuner picks the strip (rows / planes per CTA) by timing; the state is restored bitwise
+    # the library's autotuner picks the strip (rows / planes per CTA) by timing; the state is restored bitwise and
+    # the step graphs of the chosen shape are captured before it returns
     if args.strip > 0:
         ctx.set_launch(args.strip)
         strip_tuned = None
@@ -535,19 +587,7 @@ def run_gpu(args):
         strip_tuned = ctx.tune(args.tune_trial)[0] if args.tune_trial > 0 else None
 
     # ---- device-resident timed region: K steps replayed from CUDA graphs ----
-    clocks = Clocks()
-    barrier(world)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks.start()
-    ev0.record(stream)
-    ctx.step(args.steps)
-    ev1.record(stream)
-    ev1.synchronize()
-    clk = clocks.stop()
-    torch.cuda.synchronize()
-    barrier(world)
-    ms = ev0.elapsed_time(ev1)
+    ms, clk = loaded_timed_region(ctx.step, stream, args.steps, args.warmup, world)
     ctx.sync()
     ms = max_over_ranks(world, ms)
     value = world * lu * args.steps / (ms * 1e-3) / 1e6
@@ -574,7 +614,7 @@ def run_gpu(args):
     barrier(world)
     e2e_s = max_over_ranks(world, e2e_s)
     e2e = world * lu * args.steps / e2e_s / 1e6
-    obs = ctx.observables(0)
+    obs = [ctx.observables(i) for i in range(nb)]
     ctx.close()
     tte = None
     if d == 2 and args.tte_steps > 0 and rank == 0:
@@ -623,17 +663,20 @@ def run_gpu(args):
                 "note": "set_solid + set_phase from pinned host, K steps, get_fields to pinned host"},
         "gpu_launches": launches,
         "clocks": clk,
-        "check": {"mass1": obs["mass1"], "umax": obs["umax"], "dp": obs["dp"]},
+        "check": {"steps": args.steps, "mass1_initial": mass0, "mass1_final": [o["mass1"] for o in obs],
+                  "mass1_rel_drift": [o["mass1"] / m - 1.0 for o, m in zip(obs, mass0)],
+                  "umax": [o["umax"] for o in obs], "dp": [o["dp"] for o in obs],
+                  "note": "float64 sums of phi1 at set_phase and after the K steps of the end-to-end leg, which "
+                          "restarts from the same initial state"},
         "time_to_equilibrium": tte,
     }
     if d == 3:
         line["roofline"]["moment_pass_ms_per_launch"] = moment_ms / max(nk, 1)
     if world == 1 and not args.no_cpu_baseline:
         try:
-            mlups, secs, desc = oracle_sample(wl, 8, args.cpu_seconds, spec["oracle_us_per_node_step"])
-            line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc}
+            line["cpu_baseline"] = cpu_baselines(wl, spec, args.cpu_seconds)
         except Exception as e:   # the GPU number stands on its own
-            line["cpu_baseline"] = {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            line["cpu_baseline"] = {"value": None, "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
                                     "sample": f"failed: {str(e)[:200]}"}
     print(json.dumps(line), flush=True)
     return 0
@@ -729,58 +772,6 @@ def _ws_conv_roofline(B, n, stream):
             "traffic": None, "peak_source": src,
             "kernel": f"conv3x3_fwd_tc<32, wide> {cin}->{cout} on {B} x {n}^2 (tcgen05.mma kind::f16, BF16 operands, "
                       "FP32 accumulator in TMEM)"}
-
-
-def run_kp(args):
-    """Relative permeabilities K_1, K_2 (Sec. 4.6, Eq. eq-Kp) against the wetting saturation S_1 on a sphere pack.
-
-    All runs of synthetic.workloads.kp_porous (one two-phase run per initial radius R0 of the wetting cylinder and
-    the two single-phase runs) advance together as one batch; every 5000 steps lbm_phase_flux gives each run's
-    pore-space fluxes, and K_p = q_p (two-phase) / q (single phase of fluid p).  The line reports K_1, K_2 and S_1
-    at the end and the relative change of the fluxes over the last 5000 steps (steadiness)."""
-    import numpy as np
-    import torch
-    from paper_2311_05091_gb300 import _lbm as L
-    from synthetic.workloads import kp_porous
-    n = args.size or 128
-    wl = kp_porous(n=n, R0s=(20.0, 32.0, 44.0, 56.0, 68.0))
-    nb = wl["phi1"].shape[0]
-    stream = torch.cuda.Stream()
-    ctx = L.Context(L.LBM_D3Q19, n, n, n, periodic=(True, True, True),
-                    batch=[L.lbm_default_params(**wl["params"]) for _ in range(nb)])
-    try:
-        ctx.set_stream(stream.cuda_stream)
-        ctx.set_solid(np.broadcast_to(wl["phi0"], (nb, n, n, n)).copy())
-        ctx.set_phase(wl["phi1"])
-        hist, done, block = [], 0, 5000
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        while done < args.kp_steps:
-            k = min(block, args.kp_steps - done)
-            ctx.step(k)
-            done += k
-            hist.append([ctx.phase_flux(i, 0) for i in range(nb)])
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-    finally:
-        ctx.close()
-    last, prev = hist[-1], hist[-2] if len(hist) > 1 else hist[-1]
-    s1, s2 = last[nb - 2], last[nb - 1]
-    rows = []
-    for i in range(nb - 2):
-        K1, K2 = L.relative_permeability(last[i], s1, s2)
-        change = max(abs(last[i][q] - prev[i][q]) / max(abs(last[i][q]), 1e-30) for q in ("q1", "q2"))
-        rows.append({"run": wl["labels"][i], "S1": last[i]["s1"], "K1": K1, "K2": K2,
-                     "flux_change_last_5000_steps": change})
-    line = {"metric": "relative permeabilities K_1, K_2 against wetting saturation S_1 (Eq. eq-Kp)",
-            "value": None, "unit": "-", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl["name"], "porosity": wl["porosity"], "steps": args.kp_steps, "runs": nb},
-            "results": rows,
-            "single_phase_change_last_5000_steps": abs(s1["q"] - prev[nb - 2]["q"]) / abs(s1["q"]),
-            "seconds": ms / 1e3, "mlups": nb * n ** 3 * args.kp_steps / (ms * 1e3)}
-    print(json.dumps(line), flush=True)
-    return 0
 
 
 def run_warmstart(args):
@@ -950,8 +941,6 @@ def main():
         return run_reference(args)
     if args.workload == "warmstart256":
         return run_warmstart(args)
-    if args.workload == "kp128":
-        return run_kp(args)
     return run_gpu(args)
 
 

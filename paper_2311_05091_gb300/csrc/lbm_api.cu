@@ -463,6 +463,17 @@ int ensure_graph(lbm_ctx* c, int from) {
   return LBM_OK;
 }
 
+// Captures the step graphs of both starting buffers ahead of use, so that the
+// first lbm_step after a launch-shape change replays a graph instead of
+// capturing one (capture and instantiation are host work of a few hundred
+// microseconds during which the stream would otherwise sit idle).
+int prepare_graphs(lbm_ctx* c) {
+  if (c->stream == nullptr || c->profiling) return LBM_OK;
+  for (int from = 0; from < 2; ++from)
+    if (int s = ensure_graph(c, from)) return s;
+  return LBM_OK;
+}
+
 int check_ready(lbm_ctx* c, bool need_state) {
   if (!c) return set_err(nullptr, LBM_EINVAL, "null context");
   if (c->failed) return LBM_ESTATE;   // c->err keeps the first failure
@@ -838,7 +849,7 @@ int lbm_set_launch(lbm_ctx* c, int strip, int depth) {
     for (int b = 0; b < c->nbatch; ++b) c->istrip[b] = std::min(strip, c->iny[b]);
     LBM_CK(c, upload_multi(c));
   }
-  return LBM_OK;
+  return c->phase_set ? prepare_graphs(c) : LBM_OK;
 }
 
 int lbm_set_wait_limit(lbm_ctx* c, int polls) {
@@ -946,7 +957,7 @@ int lbm_tune(lbm_ctx* c, int trial, int* strips_out) {
   if (e != cudaSuccess) return cuda_fail(c, e, "autotuner");
   if (strips_out)
     for (int b = 0; b < c->nbatch; ++b) strips_out[b] = c->multi ? c->istrip[b] : c->strip;
-  return LBM_OK;
+  return prepare_graphs(c);
 }
 
 static int set_solid_impl(lbm_ctx* c, const float* src, cudaMemcpyKind kind) {

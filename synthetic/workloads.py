@@ -102,28 +102,3 @@ def warmstart_set(seeds, n=256, W=4.0):
         disk[i] = ((cx + sx) % n, (cy + sy) % n, Rs)
         params.append(dict(W=W, M_deg=0.1, theta_deg=th, kappa=geo.kappa, sigma=0.01, d0=0.5))
     return dict(phi0=phi0, phi1=phi1, theta_deg=theta, disk=disk, params=params, n=n)
-
-
-def kp_porous(n=128, seed=1, R0s=(20.0, 32.0, 44.0, 56.0), W=4.0, rmin=5.0, rmax=10.0, target_solid=0.4,
-              dp=5e-3, theta=60.0):
-    """Relative-permeability runs in the manner of the porous-medium study (Sec. 4.6): a periodic n^3 pack of
-    seeded random spheres (radii rmin-rmax, sharp solid fraction target_solid; the paper's micro-CT sandpack is not
-    available), the wetting fluid 1 initialised as a cylinder of radius R0 around the x axis through the centre of
-    the y-z plane, phi1 = (1 - phi0) (1/2 + 1/2 tanh((R0 - r) / (D/2))), one two-phase run per R0, and the two
-    single-phase runs (pore space full of fluid 1, of fluid 2).  Fluids as in the paper: densities 1, viscosities
-    0.1, sigma 0.004, D = 4, theta = 60 deg; the pressure drop dp across the lattice enters as the body force
-    density dp / n along x on the periodic lattice.  The solid takes the fluids' density and viscosity."""
-    from .geometry import rsa_spheres, spheres_phi0
-    spheres = rsa_spheres(n=n, seed=seed, rmin=rmin, rmax=rmax, target_solid=target_solid)
-    phi0 = spheres_phi0((n, n, n), spheres, W=W).astype(np.float32)
-    z, y = np.mgrid[:n, :n] + 0.5
-    r = np.hypot(y - n / 2, z - n / 2)[:, :, None]
-    fields = [((1.0 - phi0) * (0.5 + 0.5 * np.tanh((R0 - r) / (W / 2)))).astype(np.float32) for R0 in R0s]
-    fields += [(1.0 - phi0).astype(np.float32), np.zeros_like(phi0)]
-    prm = dict(W=W, M_deg=0.1, theta_deg=theta, kappa=0.0, sigma=0.004, d0=1.0 / 3.0, rho=(1.0, 1.0, 1.0),
-               mu=(0.1, 0.1, 0.1), body_force=(dp / n, 0.0, 0.0))
-    labels = [f"R0={R0:g}" for R0 in R0s] + ["single phase 1", "single phase 2"]
-    return dict(name=f"D3Q19 relative permeability, {n}^3 sphere pack (radii {rmin:g}-{rmax:g}, solid fraction "
-                     f"{target_solid:g}, seed {seed}), theta {theta:g}, dp {dp:g}",
-                lattice="D3Q19", n=n, phi0=phi0, phi1=np.stack(fields), labels=labels, params=prm,
-                porosity=float((phi0 <= 0.5).mean()))
