@@ -26,6 +26,7 @@ __all__ = [
     "cylinder_droplet",
     "free_drop",
     "flat_layer",
+    "capillary_slug",
     "random_disks_droplet",
     "rsa_spheres",
     "porous_inlet_slab",
@@ -148,6 +149,24 @@ def flat_layer(nx=4, ny=128, W=4.0, y_lo=None, y_hi=None):
 
 
 # --- seeded random geometry ---------------------------------------------------
+
+def capillary_slug(nx=64, ny=40, wall_rows=6, W=4.0):
+    """A slug of fluid 1 filling a channel between two flat solid walls, with flat menisci.
+
+    The bottom and top ``wall_rows`` rows are solid; the wall surfaces lie at
+    ``y = wall_rows - 1/2`` and ``y = ny - wall_rows - 1/2``, so the channel is
+    ``ny - 2 wall_rows`` lattice units wide.  Fluid 1 fills ``nx/4 <= x <
+    3 nx/4`` of the channel with two straight interfaces normal to the walls
+    (a 90 deg start); x is periodic, y has no-flux walls.
+    """
+    x, y = _grid2(nx, ny)
+    ylo, yhi = wall_rows - 0.5, ny - wall_rows - 0.5
+    phi0 = diffuse(ylo - y, W) + diffuse(y - yhi, W)
+    x0, x1 = nx / 4.0, 3.0 * nx / 4.0
+    phi1 = (1.0 - phi0) * diffuse(np.minimum(x - x0, x1 - x), W)
+    return Geometry(phi0, phi1, (True, False), probe_origin=(nx / 2.0, 0.0), probe_axis=1, wall_level=ylo,
+                    note=f"capillary slug, {nx}x{ny}, walls {wall_rows} rows, channel {yhi - ylo:g}, W={W}")
+
 
 def splitmix64(seed):
     """A tiny seeded uniform generator (SplitMix64), returned as a closure on [0, 1)."""

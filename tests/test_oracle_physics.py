@@ -2,8 +2,8 @@
 
 * exact conservation of sum phi1 (zeroth moments of f^eq and R, Sec. 3);
 * the flat-interface profile 1/2 + 1/2 tanh(2x/D) (equilibrium of the free energy of Sec. 2.1);
-* the Laplace law dp = sigma / R of a free 2D drop;
-* Young's law on a flat wall (Sec. 4.2) with the k closure of Eq. kk;
+* the Laplace law dp = sigma / R of free 2D drops of radius 20 and 32 (Young's law is pinned in
+  test_oracle_wetting.py);
 * the viscosity relation of Sec. 3 (shear-wave decay along an axis and a diagonal);
 * independence from the constant rho_0 inside lambda_0;
 * linear stability at rest of the NS rate reading (s0 = s4 = s2a).
@@ -15,7 +15,7 @@ import pytest
 
 from oracle import lbm, model
 from oracle import observables as ob
-from synthetic import free_drop, wall_cap, wall_droplet
+from synthetic import wall_droplet
 from synthetic.geometry import Geometry
 
 
@@ -49,23 +49,33 @@ def test_flat_interface_tanh_profile():
     assert np.abs(st.macro["phi1"][lower, 0] - wrong[lower]).max() > 3e-2
 
 
+def _laplace_ratio(R, n):
+    """dp R / sigma of a free drop, dp averaged over steps 1000-2000 (the periodic box rings acoustically)."""
+    from oracle import lbm, model
+    from oracle import observables as ob
+    from synthetic import free_drop
+    geo = free_drop(n, n, R, 4.0)
+    prm = model.Params(sigma=0.01, mu=(1.0, 1.0, 1.0))
+    c = model.constants(prm)
+    st = lbm.init_state("D2Q9", geo.phi0, geo.phi1, prm, geo.periodic, consts=c)
+    lbm.step(st, c, 1000)
+    acc = []
+    for _ in range(1000):
+        lbm.step(st, c, 1)
+        acc.append(ob.laplace_dp(geo.phi0, st.macro["phi1"], st.macro["p"]))
+    R_eq = math.sqrt(st.macro["phi1"].sum() / math.pi)   # radius of the conserved area
+    return float(np.mean(acc)) * R_eq / prm.sigma
+
+
 def test_laplace_law_free_drop():
-    geo = free_drop(64, 64, 16.0, 4.0)
-    prm = model.Params(sigma=0.01, mu=(0.3, 0.3, 0.3))
-    st = _run(geo, prm, 3000)
-    R = math.sqrt(st.macro["phi1"].sum() / math.pi)
-    dp = ob.laplace_dp(geo.phi0, st.macro["phi1"], st.macro["p"])
-    assert abs(dp * R / prm.sigma - 1.0) < 0.02, dp * R / prm.sigma
-
-
-@pytest.mark.parametrize("theta", [60.0, 120.0])
-def test_young_law_flat_wall(theta):
-    # a cap placed at the prescribed angle keeps it (R0 = 25 lu, D = 4 lu)
-    geo = wall_cap(96, 48, 8, 25.0, theta, 4.0)
-    prm = model.Params(theta_deg=theta, sigma=0.02, mu=(0.1, 0.1, 0.1))
-    st = _run(geo, prm, 2000)
-    th = ob.flat_wall_angle(geo.phi0, st.macro["phi1"], 48)[0]
-    assert abs(th - theta) < 1.0, th
+    # Laplace's law in 2D, dp = sigma / R, for free drops of radius 20 and 32 at D = 4 (no solid: with phi0 = 0
+    # the model is the two-phase model of tension sigma_12, Sec. 2.2): within 1 %
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(2) as pool:
+        ratios = pool.starmap(_laplace_ratio, [(20.0, 80), (32.0, 128)])
+    print("dp R / sigma", ratios)
+    for r in ratios:
+        assert abs(r - 1.0) < 0.01, ratios
 
 
 def _shear_rate(d0, diagonal, nu=0.02, t1=100, t2=500):
