@@ -250,8 +250,8 @@ int derive(const lbm_params& p, int lattice, InstanceConsts& k, char* why, lbm_d
   k.bx = (float)p.body_force[0];
   k.by = (float)p.body_force[1];
   k.bz = (float)p.body_force[2];
-  k.a2a = (float)((1.0 - df) / 2.0);
-  k.a2b = (float)df;
+  k.ia2a = (float)(2.0 / (1.0 - df));
+  k.ia2b = (float)(1.0 / df);
   // pressure: pf = cs2 / (1 - w0), wq = w0 / (c^2 - cs2)
   k.pf = (float)(cs2 / (1.0 - w0));
   k.wq = (float)(w0 / (1.0 - cs2));

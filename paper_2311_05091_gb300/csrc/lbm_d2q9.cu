@@ -44,7 +44,19 @@ __device__ __forceinline__ int wrap_or_mirror(int i, int n, int per) {
   return i;
 }
 
-__device__ __forceinline__ int ring(int r, int n) { return ((r % n) + n) % n; }
+// Row index inside the lattice for a row that lies at most one period outside
+// it (every row the sweep touches: ys - 4 .. ye + D + 2 with a strip no
+// longer than the lattice), without an integer division; other rows take the
+// general form.
+__device__ __forceinline__ int wrap_or_mirror_row(int i, int n, int per) {
+  if (i >= 0 && i < n) return i;
+  if (per && i >= -n && i < 2 * n) return i < 0 ? i + n : i - n;
+  return wrap_or_mirror(i, n, per);
+}
+
+// Ring slot of row r >= -64 n (the sweep starts at most four rows below 0):
+// one unsigned modulo by the compile-time ring depth.
+__device__ __forceinline__ int ring(int r, int n) { return (int)((unsigned)(r + 64 * n) % (unsigned)n); }
 
 // 3x3 neighbourhood: centre, axis (e, n, w, s) and diagonal (ne, nw, sw, se).
 struct P9 {
@@ -326,9 +338,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
     const bool need_a = ra >= ys - 2 && ra <= ye + 1;
     const bool need_h = rh >= ys - 1 && rh <= ye;
     const bool need_g = rg >= ys && rg < ye;
-    const int ba = wrap_or_mirror(ra, ny, per_y) * nx;
-    const int bh = wrap_or_mirror(rh, ny, per_y) * nx;
-    const int bg = wrap_or_mirror(rg, ny, per_y) * nx;
+    const int ba = wrap_or_mirror_row(ra, ny, per_y) * nx;
+    const int bh = wrap_or_mirror_row(rh, ny, per_y) * nx;
+    const int bg = wrap_or_mirror_row(rg, ny, per_y) * nx;
     auto need = [&](int arr) { return arr < 10 ? need_a : need_h; };
     auto rowb = [&](int arr) { return arr < 10 ? ba : bh; };
     GT* const grow = S.g[ring(rg, D + 1)].rows[0];
@@ -523,10 +535,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
 
       // local viscous rates (s0 = s4 = s2a)
       const float om = fmaxf(one_m0, kOneMinusPhi0Floor);
-      const float ra = rho * om * k.a2a, rb = rho * om * k.a2b;
-      const float s2a = __fdividef(ra, 0.5f * ra + muv);
-      const float s2b = __fdividef(rb, 0.5f * rb + muv);
-      const float inv_s2a = 0.5f + __fdividef(muv, ra);
+      // 1/s2a = 1/2 + mu / (rho (1 - phi0) a2a), likewise s2b; IEEE-rounded reciprocals
+      const float nu_e = muv * __frcp_rn(rho * om);
+      const float inv_s2a = 0.5f + nu_e * k.ia2a;
+      const float s2a = __frcp_rn(inv_s2a);
+      const float s2b = __frcp_rn(0.5f + nu_e * k.ia2b);
 
       // pressure
       const float udg = ux * grx + uy * gry;
@@ -669,7 +682,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
 
 // one tile per CTA: grid (column tiles, row strips, instances)
 template <bool OBS, int D, typename GT, bool PER>
-__global__ void __launch_bounds__(BX) d2q9_step(const StepArgs a) {
+__global__ void __launch_bounds__(BX, 5) d2q9_step(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<D, GT>& S = *reinterpret_cast<StepSmem<D, GT>*>(smem_raw);
   step_tile<OBS, D, GT, PER>(a, S, blockIdx.x * BX, blockIdx.y * a.strip, blockIdx.z);

@@ -484,10 +484,11 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
 
   // local viscous rates (s0 = s4 = s2a)
   const float om = fmaxf(one_m0, kOneMinusPhi0Floor);
-  const float ra = rho * om * k.a2a, rb = rho * om * k.a2b;
-  const float s2a = __fdividef(ra, 0.5f * ra + muv);
-  const float s2b = __fdividef(rb, 0.5f * rb + muv);
-  const float inv_s2a = 0.5f + __fdividef(muv, ra);
+  // 1/s2a = 1/2 + mu / (rho (1 - phi0) a2a), likewise s2b; IEEE-rounded reciprocals
+  const float nu_e = muv * __frcp_rn(rho * om);
+  const float inv_s2a = 0.5f + nu_e * k.ia2a;
+  const float s2a = __frcp_rn(inv_s2a);
+  const float s2b = __frcp_rn(0.5f + nu_e * k.ia2b);
 
   // pressure (Sec. 3)
   const float udg = ux * grx + uy * gry + uz * grz;

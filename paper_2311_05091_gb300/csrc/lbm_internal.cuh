@@ -50,8 +50,9 @@ struct InstanceConsts {
   float rho0, rho1, rho2, mu0, mu1, mu2;
   // body force density
   float bx, by, bz;
-  // viscosity relation: s2a uses (c^2 - cs2)/2, s2b uses cs2
-  float a2a, a2b;
+  // viscosity relation mu / (rho (1 - phi0)) = (1/s2a - 1/2) a2a = (1/s2b - 1/2) a2b with
+  // a2a = (c^2 - cs2)/2, a2b = cs2: their inverses
+  float ia2a, ia2b;
   // pressure formula (Sec. 3): p = pf * [sum_{i!=0} g_i + (1/2 + H) u.grad rho
   //   - wq * (rho u - S).u + K/2 * d_t((rho u - S).u)],
   // H = K * (h0 * inv_s0 - h2 * inv_s2a + h3), pf = cs2/(1-w0), wq = w0/(1-cs2)

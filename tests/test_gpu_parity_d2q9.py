@@ -131,3 +131,12 @@ def test_batch_instances_are_independent(lbm_lib):
     st = oracle_run("D2Q9", phi0, phi1, prms[2], (True, True), 300)
     assert rel_l2(b_phi1[2], st.macro["phi1"]) < 1e-5
     assert rel_l2(b_u[2], st.macro["u"].reshape(2, -1)) < 1e-5
+
+
+def test_free_rates_general_collisions(lbm_lib):
+    # CH free rates 0.8 take the general Hermite CH collision (every moment relaxed, the node's populations
+    # re-read); NS free rates 1.2 relax the first- and third-order NS moments at a rate other than 1
+    geo = wall_droplet(150, 48, 8, 16.0, 4.0, xc=75.0)
+    prm = dict(theta_deg=70.0, sigma=0.01, rho=(2.0, 2.0, 1.0), mu=(0.05, 0.05, 0.02), d0=0.5,
+               s_free_ch=0.8, s_free_ns=1.2)
+    _compare(lbm_lib, "D2Q9", geo, prm, (True, False), 1000, strip=16)
