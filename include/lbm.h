@@ -358,7 +358,13 @@ int lbm_observables(lbm_ctx* ctx, int instance, lbm_obs* out);
  * up (cudaGetSymbolAddress); make it before capturing a stream.  Every call
  * shares the array and it keeps the previous call's contents (nothing needs
  * clearing: each call overwrites the records it reads); calls whose kernels
- * overlap on the GPU race on it.  LBM_ECUDA if the look-up or a launch fails. */
+ * overlap on the GPU race on it.  The buffers and the stream must belong to
+ * the calling thread's current device, whose array the call uses; devices of
+ * ordinal 64 and above are not served (LBM_ECUDA).  The looked-up address is
+ * kept for the life of the process, so do not call this on a device after
+ * cudaDeviceReset.  LBM_ECUDA if the look-up or a launch fails, or if the
+ * device already holds an error from earlier work when the call starts (that
+ * error is left in place for cudaGetLastError). */
 int lbm_observables_noalloc(const float* phi0, const float* phi1, const float* u, int d, const float* p,
                             long long n, double* out, void* stream);
 

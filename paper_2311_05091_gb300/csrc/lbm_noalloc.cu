@@ -146,13 +146,15 @@ extern "C" int lbm_observables_noalloc(const float* phi0, const float* phi1, con
                                        long long n, double* out, void* stream) {
   if (n < 1 || n > kMaxNodes) return LBM_EINVAL;   // beyond the fixed record array
   if (!phi0 || !phi1 || !u || !p || !out || d < 1 || d > 3) return LBM_EINVAL;
+  // an error left by earlier work on this device is reported, not cleared, so the caller can still read it
+  if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
   double* partials = nullptr;
   if (int s = partials_on_current_device(&partials)) return s;
   const int nrec = (int)((n + kNodesPerRecord - 1) / kNodesPerRecord);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   tile_sums<<<nrec, kThreads, 0, st>>>(phi0, phi1, u, d, p, n, partials);
-  if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+  if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
   fold_records<<<1, kThreads, 0, st>>>(partials, nrec, out);
-  if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+  if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
   return LBM_OK;
 }

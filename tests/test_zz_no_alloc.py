@@ -77,3 +77,33 @@ def test_noalloc_matches_observables_on_two_calls(lbm_lib):
                                      100, out.data_ptr(), stream.cuda_stream) == -1
     assert L.lbm_observables_noalloc(0, t1.data_ptr(), tu.data_ptr(), 2, tp.data_ptr(),
                                      100, out.data_ptr(), stream.cuda_stream) == -1
+
+
+def test_noalloc_at_the_size_limit_in_3d(lbm_lib):
+    # n = 16,777,216 nodes fills every one of the 16,384 records, with three velocity planes (a 256^3 field);
+    # checked against float64 sums of the same float32 values on the host
+    L = lbm_lib
+    import torch
+    n = 16_777_216
+    rng = np.random.default_rng(7)
+    phi0 = rng.random(n, dtype=np.float32) * 0.5
+    phi1 = (rng.random(n, dtype=np.float32) * (1.0 - phi0)).astype(np.float32)
+    phi1[::97] = 0.995                     # bulk fluid 1 ...
+    phi0[::89] = 0.0
+    phi1[::89] = 0.0                       # ... and bulk fluid 2
+    u = (rng.standard_normal((3, n), dtype=np.float32) * 1e-3).astype(np.float32)
+    p = rng.standard_normal(n, dtype=np.float32)
+    for _ in range(2):
+        r, _keep = _noalloc(L, phi0, phi1, u, p)
+        del _keep
+        torch.cuda.empty_cache()
+        assert abs(r[0] - phi1.astype(np.float64).sum()) <= 1e-12 * phi1.astype(np.float64).sum()
+        assert abs(r[1] - phi0.astype(np.float64).sum()) <= 1e-12 * phi0.astype(np.float64).sum()
+        umax = float(np.sqrt((u.astype(np.float64) ** 2).sum(axis=0)).max())
+        assert abs(r[2] - umax) <= 1e-6 * umax
+        inside = phi1 >= np.float32(0.99)
+        outside = (np.float32(1.0) - phi0 - phi1) >= np.float32(0.99)
+        assert int(r[4]) == int(inside.sum()) > 0 and int(r[6]) == int(outside.sum()) > 0 and r[7] == 0
+        ps = p.astype(np.float64)
+        assert abs(r[3] - ps[inside].sum()) <= 1e-9 * np.abs(ps[inside]).sum()
+        assert abs(r[5] - ps[outside].sum()) <= 1e-9 * np.abs(ps[outside]).sum()
