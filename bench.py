@@ -379,12 +379,15 @@ def run_reference(args):
     return 0
 
 
-def _settle(th, ref, every, tol_deg):
-    """First sampled step from which every later sample lies within tol_deg of ref (None if the last does not)."""
+def _settle(th, ref, every, tol_deg, min_run=1):
+    """First sampled step from which every later sample lies within tol_deg of ref.
+
+    None unless at least ``min_run`` samples at the end of the run lie there (a run referred to its own last
+    sample needs several, since that sample always matches itself)."""
     k = len(th)
     while k > 0 and abs(th[k - 1] - ref) <= tol_deg:
         k -= 1
-    return None if k == len(th) else (k + 1) * every
+    return None if len(th) - k < min_run else (k + 1) * every
 
 
 def batch_time_to_equilibrium(m, inst, args, tol_deg=0.5):
@@ -404,7 +407,7 @@ def batch_time_to_equilibrium(m, inst, args, tol_deg=0.5):
                 th[k].append(m.contact_angle(k, 1, int(round(cx)), float(cy), float(i["geometry"].disk_radius))[0])
             except Exception:
                 th[k].append(float("nan"))
-    steps = [_settle(t, t[-1], every, tol_deg) if np.isfinite(t[-1]) else None for t in th]
+    steps = [_settle(t, t[-1], every, tol_deg, min_run=5) if np.isfinite(t[-1]) else None for t in th]
     done = [x for x in steps if x is not None]
     return {"criterion": f"first sample after which theta stays within {tol_deg} deg of its value after "
                          f"{args.tte_batch_steps} steps (sampled every {every} steps)",
@@ -464,7 +467,7 @@ def time_to_equilibrium(L, stream, size, total, every, tol_deg=0.5, flags=0, tun
            "steps_run": total, "sample_every": every, "ms_per_step": step_ms, "strip_tuned": strip, "instances": []}
     for i in range(nb):
         eq = th[i][-1] if ref is None else ref[i]
-        steps = _settle(th[i], eq, every, tol_deg)
+        steps = _settle(th[i], eq, every, tol_deg, min_run=5 if ref is None else 1)
         out["instances"].append({"theta_in": wl["params"][i]["theta_deg"], "theta_eq": eq, "theta_end": th[i][-1],
                                  "theta_model_minus_input_deg": eq - wl["params"][i]["theta_deg"], "steps": steps,
                                  "ms": None if steps is None else steps * step_ms, "umax_end": um[i][-1]})

@@ -30,7 +30,7 @@ namespace lbm {
 namespace {
 
 constexpr int BX = 128;   // columns (threads) per CTA
-constexpr int RP = 5;     // ring depth of phi0 / phi1 rows
+constexpr int RP = 4;     // ring depth of phi0 / phi1 rows (y-1 .. y+2 live in one iteration)
 constexpr int RM = 3;     // ring depth of mubar / history rows
 constexpr float kOneMinusPhi0Floor = 5.9604644775390625e-8f;  // 2^-24
 
@@ -266,7 +266,6 @@ struct StepSmem {
   float phi0[RP][BX + 4];
   float mub[RM][BX + 2];
   float acorr[RM][BX + 2];   // S_x u_y - u_x S_y of the previous step
-  float jr[3][2][BX];        // j = sum_i c_i f_i of rows y, y+1, y+2 (owned columns)
   InstanceConsts k;
 };
 
@@ -305,7 +304,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
     return arr < 10 ? S.a[ring(ra, D + 1)].rows[arr] : S.h[ring(rh, D + 2)].rows[arr - 10];
   };
 
-  const bool vec16 = (nx & 3) == 0;
+  // 16-byte copies need 16-byte aligned rows: nx % 4 == 0 and instance bases on 16 bytes (an instance of a
+  // multi-size context follows the others' nodes, whose count need not be a multiple of four)
+  const bool vec16 = (nx & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(f_in) | reinterpret_cast<uintptr_t>(g_in) |
+                       reinterpret_cast<uintptr_t>(p0_in) | reinterpret_cast<uintptr_t>(h_in)) & 15) == 0;
   const int x = x0 + t;
 
   // halo copy assignment: 40 copies of f / phi0 (two columns each side), 10 of the
@@ -394,11 +397,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
 
   const InstanceConsts& k = S.k;
 
-  // stage 1: phi1 = sum f and phi0 of row r into phi ring row sp; j of the owned columns.
-  auto stage1 = [&](int r, int sp) {
+  // stage 1: phi1 = sum f and phi0 of row r into phi ring row sp (ring column c = owned column c - 2); the
+  // first moment j of this thread's own column stays in registers until stage 3 of row r
+  auto stage1 = [&](int r, int sp, float& jx, float& jy) {
     const ARow& slot = S.a[ring(r, D + 1)];
-    float(&jr)[2][BX] = S.jr[ring(r, 3)];
-    auto one = [&](int c) {
+    auto one = [&](int c, bool own) {
       const int xl = x0 - 2 + c;
       if (xl > nx + 1) return;
       const int col = c + PAD - 2;
@@ -410,13 +413,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
       for (int i = 1; i < 9; ++i) sum += v[i];
       S.phi1[sp][c] = sum;
       S.phi0[sp][c] = slot.rows[9][col];
-      if (c >= 2 && c < BX + 2) {
-        jr[0][c - 2] = (v[1] - v[3]) + (v[5] - v[6]) - (v[7] - v[8]);
-        jr[1][c - 2] = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+      if (own) {
+        jx = (v[1] - v[3]) + (v[5] - v[6]) - (v[7] - v[8]);
+        jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
       }
     };
-    one(t);
-    if ((t & 31) == 0) one(BX + (t >> 5));   // the four extra columns, one per warp
+    one(t + 2, true);
+    // the four halo columns 0, 1, BX+2, BX+3, one per warp
+    if ((t & 31) == 0) one((t >> 5) < 2 ? (t >> 5) : BX + (t >> 5), false);
   };
 
   // stage 2: mubar_1 and the correction-force product of row r (phi ring rows
@@ -460,11 +464,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
   int pm = ring(yb - 1, RP), p0 = ring(yb, RP), pp = ring(yb + 1, RP), pq = ring(yb + 2, RP);
   int mm = ring(yb - 1, RM), m0 = ring(yb, RM), mp = ring(yb + 1, RM);
   float d02 = 0.f, d12 = 0.f;       // mu differences of this thread's column, row y
+  float jx0 = 0.f, jy0 = 0.f, jx1 = 0.f, jy1 = 0.f;   // j of this thread's column, rows y and y+1
   for (int y = yb; y < ye; ++y) {
     cp_wait<D - 1>();          // rows of target y have landed
     __syncthreads();           // ... for every thread, and the slots refilled next are no longer read
     issue(y + D);
-    stage1(y + 2, pq);
+    float jx2 = 0.f, jy2 = 0.f;
+    stage1(y + 2, pq, jx2, jy2);
     __syncthreads();
     float n02 = 0.f, n12 = 0.f;
     if (y + 1 >= ys - 1) stage2(y + 1, p0, pp, pq, mp, n02, n12);
@@ -603,7 +609,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
 
       // ---- CH collision ----
       {
-        const float jx = S.jr[ring(y, 3)][0][t], jy = S.jr[ring(y, 3)][1][t];
+        const float jx = jx0, jy = jy0;
         const float emb = k.eta * mub;
         const float corr = k.corr_scale * (1.f - fdeg);
         // R first moment: d_t(phi1 u) + cs2 * corr * eta grad mubar
@@ -673,6 +679,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, StepSmem<D, GT>& S,
     }
     d02 = n02;
     d12 = n12;
+    jx0 = jx1; jy0 = jy1; jx1 = jx2; jy1 = jy2;
     // rotate the rings to row y+1
     pm = p0; p0 = pp; pp = pq; pq = inc_mod(pq, RP);
     mm = m0; m0 = mp; mp = inc_mod(mp, RM);

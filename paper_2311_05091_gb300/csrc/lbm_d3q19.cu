@@ -1087,10 +1087,10 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   for (int z = zs; z < ze; ++z) {
     cp_wait_all();                                      // phi z+2, history z+1
     const unsigned parity = (unsigned)(z - zs) & 1u;
-    if (!bar_wait(&S.bar, parity, a.wait_polls)) {      // owned planes of z
-      ok = false;
-      pending = parity;
-    }
+    // every thread records the phase it waits on: after a block-wide give-up, the drain below waits on that
+    // load (immediately satisfied for threads that saw it land) and not on the next, never-issued phase
+    pending = parity;
+    if (!bar_wait(&S.bar, parity, a.wait_polls)) ok = false;   // owned planes of z
     if (!__syncthreads_and(ok)) {
       if (t == 0) atomicOr(o.flag, 2u);
       ok = false;

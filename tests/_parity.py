@@ -45,7 +45,8 @@ def gpu_run(L, lattice, phi0, phi1, prm: dict, periodic, steps, strip=None):
     return ctx
 
 
-def compare_run(L, lattice, geo, prm, periodic, steps, strip=None, tol=1e-5, tol_pop=1e-4, u_abs=None, p_abs=None):
+def compare_run(L, lattice, geo, prm, periodic, steps, strip=None, tol=1e-5, tol_pop=1e-4, u_abs=None, p_abs=None,
+                tol_u=None):
     phi0, phi1 = as_inputs(geo)
     ctx = gpu_run(L, lattice, phi0, phi1, prm, periodic, steps, strip)
     try:
@@ -70,14 +71,17 @@ def compare_run(L, lattice, geo, prm, periodic, steps, strip=None, tol=1e-5, tol
     g_gg = g_g[0].astype(np.float64)
     g_gg[0] += prm.get("rho", (1.0, 1.0, 1.0))[0]   # the library stores g_0 minus rho_0
     du = np.linalg.norm(g_u[0].astype(np.float64) - o_u)
-    errs = dict(phi1=rel_l2(g_phi1[0], o_phi1), u=du / max(u_peak, 1e-300), u_end=rel_l2(g_u[0], o_u),
+    errs = dict(phi1=rel_l2(g_phi1[0], o_phi1), u_peak=du / max(u_peak, 1e-300), u_end=rel_l2(g_u[0], o_u),
                 p=rel_l2(g_p[0], o_p), f=rel_l2(g_f[0], st.f.reshape(q, n)), g=rel_l2(g_gg, st.g.reshape(q, n)))
-    if u_abs is None:
-        assert errs["phi1"] <= tol and errs["u"] <= tol, errs
-    else:
+    if u_abs is not None:
         errs["u_abs"] = float(np.sqrt(np.mean((g_u[0].astype(np.float64) - o_u) ** 2)))
-        assert errs["phi1"] <= tol and errs["u_abs"] <= u_abs, errs
     print("parity", errs)
+    if u_abs is None:
+        # the plain relative L2 of the final velocity field ("u_peak" divides by the largest norm of the run
+        # and is printed for reference only)
+        assert errs["phi1"] <= tol and errs["u_end"] <= (tol if tol_u is None else tol_u), errs
+    else:
+        assert errs["phi1"] <= tol and errs["u_abs"] <= u_abs, errs
     assert errs["f"] <= tol_pop and errs["g"] <= tol_pop, errs
     if p_abs is None:
         assert errs["p"] <= tol_pop, errs

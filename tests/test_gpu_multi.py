@@ -89,8 +89,9 @@ def test_multi_size_instance_against_oracle(lbm_lib):
     st = olbm.init_state("D2Q9", phi0.astype(np.float64), phi1_in.astype(np.float64), omodel.Params(**prm),
                          (True, True))
     olbm.step(st, nsteps=200)
-    assert rel_l2(phi1, st.macro["phi1"]) < 1e-5
-    assert rel_l2(u, st.macro["u"]) < 1e-4
+    e_phi1, e_u = rel_l2(phi1, st.macro["phi1"]), rel_l2(u, st.macro["u"])
+    print("parity multi", e_phi1, e_u)
+    assert e_phi1 <= 1e-5 and e_u <= 1e-5, (e_phi1, e_u)
 
 
 def test_multi_size_checkpoint_restores_bitwise(lbm_lib):
