@@ -345,6 +345,8 @@ StepArgs step_args(lbm_ctx* c, int from) {
   a.strip = c->strip;
   a.depth = c->depth;
   a.wait_polls = c->wait_polls;
+  a.s_zero = 1;
+  for (const auto& k : c->hconsts) a.s_zero &= k.rho1 == k.rho2 ? 1 : 0;
   a.nodes = c->nodes;
   a.g_half = c->g_half;
   a.q = c->q;

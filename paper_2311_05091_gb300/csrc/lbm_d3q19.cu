@@ -147,7 +147,7 @@ __device__ __forceinline__ float lap3(const float* pm, const float* p0, const fl
     if (d < 7) axis += v;
     else edge += v;
   }
-  return axis * (1.f / 3.f) + edge * (1.f / 6.f);
+  return __fmaf_rn(axis, 1.f / 3.f, __fmul_rn(edge, 1.f / 6.f));   // as lap_v, rounding for rounding
 }
 
 // The same two operators on the 19 values v[d] = v(x + c_d), gathered once.
@@ -178,20 +178,23 @@ __device__ __forceinline__ float lap_v(const float (&v)[NS]) {
     if (d < 7) axis += w;
     else edge += w;
   }
-  return axis * (1.f / 3.f) + edge * (1.f / 6.f);
+  return __fmaf_rn(axis, 1.f / 3.f, __fmul_rn(edge, 1.f / 6.f));   // as lap3, rounding for rounding
 }
 
 // mu_p = gamma_p psi_p, psi_p = (12/D) phi_p (1 - phi_p)(1 - 2 phi_p) - (3D/4) lap phi_p (Sec. 2.1).
 __device__ __forceinline__ void chem_pot(const InstanceConsts& k, float ph0, float ph1, float lap0,
                                          float lap1, float& mu0, float& mu1, float& mu2) {
-  const float ph2 = 1.f - ph0 - ph1;
-  const float lap2 = -lap0 - lap1;
-  const float psi0 = k.c12_W * ph0 * (1.f - ph0) * (1.f - 2.f * ph0) - k.c34_W * lap0;
-  const float psi1 = k.c12_W * ph1 * (1.f - ph1) * (1.f - 2.f * ph1) - k.c34_W * lap1;
-  const float psi2 = k.c12_W * ph2 * (1.f - ph2) * (1.f - 2.f * ph2) - k.c34_W * lap2;
-  mu0 = k.gam0 * psi0;
-  mu1 = k.gam1 * psi1;
-  mu2 = k.gam2 * psi2;
+  // every product and sum is spelled out (no contraction left to the compiler), so the pipelined kernel's
+  // mubar_1 pass and the node update round these values identically wherever they are inlined
+  const float ph2 = __fsub_rn(__fsub_rn(1.f, ph0), ph1);
+  const float lap2 = __fsub_rn(-lap0, lap1);
+  auto psi = [&](float ph, float lap) {
+    const float bulk = __fmul_rn(__fmul_rn(__fmul_rn(k.c12_W, ph), __fsub_rn(1.f, ph)), __fmaf_rn(-2.f, ph, 1.f));
+    return __fmaf_rn(-k.c34_W, lap, bulk);
+  };
+  mu0 = __fmul_rn(k.gam0, psi(ph0, lap0));
+  mu1 = __fmul_rn(k.gam1, psi(ph1, lap1));
+  mu2 = __fmul_rn(k.gam2, psi(ph2, lap2));
 }
 
 // mubar_1 = gamma_T/3 [ (mu1 - mu0)/gamma_0 + (mu1 - mu2)/gamma_2 ] (Eq. CHmodel).
@@ -344,6 +347,7 @@ struct OwnIn {
   float g[QL];
   float jx, jy, jz;
   float php, upx, upy, upz, spx, spy, spz;
+  float d02, d12;   // mu0 - mu2 and mu1 - mu2 of the node, when the caller computed them already (MU_IN)
 };
 
 // Ring planes (z-1, z, z+1) around the node: phi0 / phi1 on the two-halo tile
@@ -368,7 +372,11 @@ struct Outs {
   int nx, ny, nz, per_x, per_y, per_z, nodes, plane;
 };
 
-template <int QL, bool OBS, typename GT>
+// MU_IN: the chemical-potential differences of the node come in `in` (the pipelined kernel keeps them from its
+// mubar_1 pass over the same planes, bitwise the values computed here otherwise).  SZ: rho1 == rho2, so the mass
+// flux S = (rho1 - rho2) M grad(mubar_1) / gamma_1 is zero and with it the correction force F_c = div(S u - u S) / 2;
+// its stencils are skipped (the same values up to the sign of zeros).
+template <int QL, bool OBS, typename GT, bool MU_IN = false, bool SZ = false>
 __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings& R, const OwnIn<QL>& in,
                                             const Outs& o, int x, int y, int z) {
   const int nx = o.nx, ny = o.ny, nz = o.nz, nodes = o.nodes, plane = o.plane;
@@ -385,18 +393,25 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
     g0x = dgrad_v<0>(v);
     g0y = dgrad_v<1>(v);
     g0z = dgrad_v<2>(v);
-    lap0 = lap_v(v);
+    if (!MU_IN) lap0 = lap_v(v);
     gather19(R.p1[0], R.p1[1], R.p1[2], i2, s2, v);
     ph1 = v[0];
     g1x = dgrad_v<0>(v);
     g1y = dgrad_v<1>(v);
     g1z = dgrad_v<2>(v);
-    lap1 = lap_v(v);
+    if (!MU_IN) lap1 = lap_v(v);
   }
   const float ph2 = 1.f - ph0 - ph1;
-  float mu0, mu1, mu2;
-  chem_pot(k, ph0, ph1, lap0, lap1, mu0, mu1, mu2);
-  const float d02 = mu0 - mu2, d12 = mu1 - mu2;
+  float d02, d12;
+  if (MU_IN) {
+    d02 = in.d02;
+    d12 = in.d12;
+  } else {
+    float mu0, mu1, mu2;
+    chem_pot(k, ph0, ph1, lap0, lap1, mu0, mu1, mu2);
+    d02 = mu0 - mu2;
+    d12 = mu1 - mu2;
+  }
   float mub, gmx, gmy, gmz, dAxy_x, dAxy_y, dAxz_x, dAxz_z, dAyz_y, dAyz_z;
   {
     float v[NS];
@@ -406,15 +421,19 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
     gmy = dgrad_v<1>(v);
     gmz = dgrad_v<2>(v);
     // correction force F_c,b = 1/2 sum_a d_a (S_a u_b - u_a S_b), products A_xy, A_xz, A_yz
-    gather19(R.ac[0][0], R.ac[0][1], R.ac[0][2], i1, s1, v);
-    dAxy_x = dgrad_v<0>(v);
-    dAxy_y = dgrad_v<1>(v);
-    gather19(R.ac[1][0], R.ac[1][1], R.ac[1][2], i1, s1, v);
-    dAxz_x = dgrad_v<0>(v);
-    dAxz_z = dgrad_v<2>(v);
-    gather19(R.ac[2][0], R.ac[2][1], R.ac[2][2], i1, s1, v);
-    dAyz_y = dgrad_v<1>(v);
-    dAyz_z = dgrad_v<2>(v);
+    if (SZ) {
+      dAxy_x = dAxy_y = dAxz_x = dAxz_z = dAyz_y = dAyz_z = 0.f;
+    } else {
+      gather19(R.ac[0][0], R.ac[0][1], R.ac[0][2], i1, s1, v);
+      dAxy_x = dgrad_v<0>(v);
+      dAxy_y = dgrad_v<1>(v);
+      gather19(R.ac[1][0], R.ac[1][1], R.ac[1][2], i1, s1, v);
+      dAxz_x = dgrad_v<0>(v);
+      dAxz_z = dgrad_v<2>(v);
+      gather19(R.ac[2][0], R.ac[2][1], R.ac[2][2], i1, s1, v);
+      dAyz_y = dgrad_v<1>(v);
+      dAyz_z = dgrad_v<2>(v);
+    }
   }
   const float Fcx = -0.5f * (dAxy_y + dAxz_z);
   const float Fcy = 0.5f * (dAxy_x - dAyz_z);
@@ -876,6 +895,7 @@ struct alignas(128) PipeSmem3 {
   float hus[2][6][PR1 * PW];        // history u, S (planes 1-6) on the one-halo tile
   float mub[RM][N1];
   float acor[RM][3][N1];
+  float dmu[2][2][NT];              // mu0 - mu2, mu1 - mu2 of the owned points of planes z, z+1
   InstanceConsts k;
   unsigned long long bar;
 };
@@ -920,7 +940,7 @@ __device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int
       : "memory");
 }
 
-template <int QL, bool OBS, typename GT>
+template <int QL, bool OBS, typename GT, bool SZ = false>
 __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const __grid_constant__ TmaMaps maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   PipeSmem3<QL, GT>& S = *reinterpret_cast<PipeSmem3<QL, GT>*>(smem_raw);
@@ -1029,32 +1049,51 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   };
 
   const InstanceConsts& k = S.k;
-  auto calc_mub = [&](int zl) {   // phi ring planes zl-1 .. zl+1 -> mubar ring slot of zl
+  auto mub_at = [&](int zl, int p) {   // phi ring planes zl-1 .. zl+1 -> mubar ring slot of zl, point p
+    const int px = p % HX1, py = p / HX1;
+    if (x0 - 1 + px > nx || y0 - 1 + py > ny) return;
     const float* q0[3] = {S.phi0[ring(zl - 1, RP5)], S.phi0[ring(zl, RP5)], S.phi0[ring(zl + 1, RP5)]};
     const float* q1[3] = {S.phi1[ring(zl - 1, RP5)], S.phi1[ring(zl, RP5)], S.phi1[ring(zl + 1, RP5)]};
-    float* dst = S.mub[ring(zl, RM)];
-    for (int p = t; p < N1; p += NT) {
-      const int px = p % HX1, py = p / HX1;
-      if (x0 - 1 + px > nx || y0 - 1 + py > ny) continue;
-      const int i = (py + 1) * PW + (px + 3);
-      float mu0, mu1, mu2;
-      chem_pot(k, q0[1][i], q1[1][i], lap3(q0[0], q0[1], q0[2], i, PW), lap3(q1[0], q1[1], q1[2], i, PW), mu0, mu1,
-               mu2);
-      dst[p] = mubar1_of(k, mu0, mu1, mu2);
+    const int i = (py + 1) * PW + (px + 3);
+    float mu0, mu1, mu2;
+    chem_pot(k, q0[1][i], q1[1][i], lap3(q0[0], q0[1], q0[2], i, PW), lap3(q1[0], q1[1], q1[2], i, PW), mu0, mu1,
+             mu2);
+    S.mub[ring(zl, RM)][p] = mubar1_of(k, mu0, mu1, mu2);
+    // owned point: keep the differences the node update of plane zl uses
+    if (px >= 1 && px <= TX && py >= 1 && py <= TY) {
+      const int ow = (py - 1) * TX + (px - 1);
+      S.dmu[zl & 1][0][ow] = mu0 - mu2;
+      S.dmu[zl & 1][1][ow] = mu1 - mu2;
     }
   };
-  auto calc_prod = [&](int zl) {  // history slot of zl -> product ring slot of zl
+  auto prod_at = [&](int zl, int p) {  // history slot of zl -> product ring slot of zl, point p
+    const int px = p % HX1, py = p / HX1;
+    if (x0 - 1 + px > nx || y0 - 1 + py > ny) return;
     const int sl = zl & 1;
     const int rm = ring(zl, RM);
-    for (int p = t; p < N1; p += NT) {
-      const int px = p % HX1, py = p / HX1;
-      if (x0 - 1 + px > nx || y0 - 1 + py > ny) continue;
-      const int i = py * PW + (px + 3);
-      const float ux = S.hus[sl][0][i], uy = S.hus[sl][1][i], uz = S.hus[sl][2][i];
-      const float sx = S.hus[sl][3][i], sy = S.hus[sl][4][i], sz = S.hus[sl][5][i];
-      S.acor[rm][0][p] = sx * uy - ux * sy;
-      S.acor[rm][1][p] = sx * uz - ux * sz;
-      S.acor[rm][2][p] = sy * uz - uy * sz;
+    const int i = py * PW + (px + 3);
+    const float ux = S.hus[sl][0][i], uy = S.hus[sl][1][i], uz = S.hus[sl][2][i];
+    const float sx = S.hus[sl][3][i], sy = S.hus[sl][4][i], sz = S.hus[sl][5][i];
+    S.acor[rm][0][p] = sx * uy - ux * sy;
+    S.acor[rm][1][p] = sx * uz - ux * sz;
+    S.acor[rm][2][p] = sy * uz - uy * sz;
+  };
+  auto calc_mub = [&](int zl) {
+    for (int p = t; p < N1; p += NT) mub_at(zl, p);
+  };
+  auto calc_prod = [&](int zl) {
+    for (int p = t; p < N1; p += NT) prod_at(zl, p);
+  };
+  // Both on the one-halo tile (N1 = 340 points, 256 threads), balanced by whole warps: every thread takes the
+  // mubar_1 point t; warps 0-2 the remaining 84 mubar_1 points, warps 3-7 all 340 products (about a seventh of a
+  // mubar_1 point's work each), so no warp runs two of both while the others wait at the barrier.
+  static_assert(N1 - NT <= 96 && N1 <= 3 * (NT - 96), "halo work split of the 32 x 8 tile");
+  auto calc_halo = [&](int zl) {
+    mub_at(zl, t);
+    if (t < 96) {
+      if (t + NT < N1) mub_at(zl, t + NT);
+    } else if (!SZ) {
+      for (int p = t - 96; p < N1; p += NT - 96) prod_at(zl, p);
     }
   };
 
@@ -1073,8 +1112,10 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   __syncthreads();
   calc_mub(zs - 1);
   calc_mub(zs);
-  calc_prod(zs - 1);
-  calc_prod(zs);
+  if (!SZ) {
+    calc_prod(zs - 1);
+    calc_prod(zs);
+  }
   __syncthreads();   // history slot of zs-1 is free again
   issue_phi(zs + 2);
   issue_hist(zs + 1);
@@ -1099,8 +1140,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
     if (z + 3 <= ze + 1) issue_phi(z + 3);
     if (z + 2 <= ze) issue_hist(z + 2);
     cp_commit();
-    calc_prod(z + 1);
-    calc_mub(z + 1);
+    calc_halo(z + 1);
     __syncthreads();
 
     // owned inputs of plane z into registers, then the slot takes plane z+1
@@ -1117,6 +1157,8 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
     in.spx = S.own[7][t];
     in.spy = S.own[8][t];
     in.spz = S.own[9][t];
+    in.d02 = S.dmu[z & 1][0][t];
+    in.d12 = S.dmu[z & 1][1][t];
     __syncthreads();
     if (t == 0 && z + 1 < ze) issue_own(z + 1);
     if (!own) continue;
@@ -1134,7 +1176,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
     R.sw2 = PW;
     R.i1 = (ty + 1) * HX1 + (tx + 1);
     R.sw1 = HX1;
-    node_update<QL, OBS, GT>(k, R, in, o, x, y, z);
+    node_update<QL, OBS, GT, true, SZ>(k, R, in, o, x, y, z);
   }
   // leave no copy in flight: asynchronous copies, and a TMA load issued for a plane not processed
   cp_wait_all();
@@ -1216,10 +1258,16 @@ cudaError_t launch_step_q(const StepArgs& a, int nbatch, bool observe, cudaStrea
     memcpy(&m, maps, sizeof m);
     const size_t smem = sizeof(PipeSmem3<QL, GT>);
     static std::atomic<unsigned long long> configured{0};
-    e = smem_opt_in(configured, smem, d3q19_step_pipe<QL, true, GT>, d3q19_step_pipe<QL, false, GT>);
+    e = smem_opt_in(configured, smem, d3q19_step_pipe<QL, true, GT>, d3q19_step_pipe<QL, false, GT>,
+                    d3q19_step_pipe<QL, true, GT, true>, d3q19_step_pipe<QL, false, GT, true>);
     if (e != cudaSuccess) return e;
-    if (observe) d3q19_step_pipe<QL, true, GT><<<grid, NT, smem, s>>>(a, m);
-    else d3q19_step_pipe<QL, false, GT><<<grid, NT, smem, s>>>(a, m);
+    if (a.s_zero) {   // equal fluid densities: no mass flux, no correction force
+      if (observe) d3q19_step_pipe<QL, true, GT, true><<<grid, NT, smem, s>>>(a, m);
+      else d3q19_step_pipe<QL, false, GT, true><<<grid, NT, smem, s>>>(a, m);
+    } else {
+      if (observe) d3q19_step_pipe<QL, true, GT><<<grid, NT, smem, s>>>(a, m);
+      else d3q19_step_pipe<QL, false, GT><<<grid, NT, smem, s>>>(a, m);
+    }
     return cudaGetLastError();
   }
   const size_t smem = sizeof(StepSmem3);

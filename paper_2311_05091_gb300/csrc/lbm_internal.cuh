@@ -83,6 +83,7 @@ struct StepArgs {
   int g_half;             // NS populations stored as FP16
   int q;                  // lattice directions (9, 15 or 19)
   int wait_polls;         // polls of a bounded tile-load wait before it gives up (3D pipelined kernel)
+  int s_zero;             // rho1 == rho2 in every instance: the mass flux S and the correction force vanish
 };
 
 // Default poll limit of a bounded device wait (mbarrier try_wait polls).
