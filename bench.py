@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS) + ["warmstart256", "wetting"])
+    ap.add_argument("--workload", default="disk1024x5", choices=sorted(WORKLOADS) + ["warmstart256", "wetting", "tte1024"])
     ap.add_argument("--size", type=int, default=None, help="lattice side (default: the workload's)")
     ap.add_argument("--g-f16", action="store_true",
                     help="store the NS populations as FP16 (D2Q9; float32 arithmetic and CH populations)")
@@ -1165,6 +1165,22 @@ def main():
         from paper_2311_05091_gb300.build import build
         build()
         return run_wetting(args)
+    if args.workload == "tte1024":
+        # time to equilibrium of the metric's own 1024^2 x 5 disk sweep (R0 = 120, R0/D = 30): the drops need
+        # of the order of 10^6 steps, minutes of GPU time, so this is a workload of its own
+        import torch
+        from paper_2311_05091_gb300.build import build
+        from paper_2311_05091_gb300 import _lbm as L
+        build()
+        total = args.tte_steps if args.tte_steps != 150000 else 1600000
+        every = args.tte_every if args.tte_every != 2500 else 40000
+        t0 = time.perf_counter()
+        tte = time_to_equilibrium(L, torch.cuda.Stream(), 1024, total, every, tune_trial=args.tune_trial)
+        line = {"metric": "time to equilibrium of the 1024^2 x 5 disk sweep (float32)", "value": None, "unit": "ms",
+                "n_gpus": 1, "dtype": "f32", "data": "synthetic", "seconds": time.perf_counter() - t0,
+                "time_to_equilibrium": tte}
+        print(json.dumps(line), flush=True)
+        return 0
     return run_gpu(args)
 
 
