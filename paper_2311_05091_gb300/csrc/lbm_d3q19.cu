@@ -879,23 +879,28 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
 // CTA.  Every wait on the TMA barrier is bounded.
 // ---------------------------------------------------------------------------
 constexpr int PW = 40;                       // halo tile row: columns x0-4 .. x0+35 (16-byte aligned chunks)
-constexpr int PR2 = TY + 4, PR1 = TY + 2;    // rows of the two-halo and one-halo tiles
+// The pipelined kernel's tile height: 32 x kPipeTY owned columns, one thread each.  16 rows would cut the halo
+// overhead per owned column (two-halo tile 1.41x instead of 1.69x the owned columns, one-halo tile 1.21x instead of
+// 1.33x), but at one CTA of 16 warps per SM instead of two of 8 the barriers of the plane sweep stall the whole SM:
+// measured 9 % slower on the 256^3 porous step, so 8.
+constexpr int kPipeTY = 8;
 constexpr int RP5 = 5;                       // phi ring: z-1 .. z+2 in use, z+3 in flight
 
 struct TmaMaps {
-  CUtensorMap g, j, h;   // g: (nx, ny, nz, QL nb), j: (.., 3 nb), h: (.., 7 nb); boxes 32 x 8 x 1 x {QL, 3, 7}
+  CUtensorMap g, j, h;   // g: (nx, ny, nz, QL nb), j: (.., 3 nb), h: (.., 7 nb); boxes 32 x kPipeTY x 1 x {QL, 3, 7}
 };
 
-template <int QL, typename GT>
+template <int QL, typename GT, int TYP>
 struct alignas(128) PipeSmem3 {
-  GT gown[QL][NT];                  // TMA destinations: g of the owned columns,
-  float own[3 + NH][NT];            // then j 0-2 and history 3-9
-  float phi1[RP5][PR2 * PW];
+  static constexpr int NTP = TX * TYP, PR2 = TYP + 4, PR1 = TYP + 2, N1P = HX1 * (TYP + 2);
+  GT gown[QL][NTP];                 // TMA destinations: g of the owned columns,
+  float own[3 + NH][NTP];           // then j 0-2 and history 3-9
+  float phi1[RP5][PR2 * PW];        // two-halo tile rows y0-2 .. y0+TYP+1
   float phi0[RP5][PR2 * PW];
   float hus[2][6][PR1 * PW];        // history u, S (planes 1-6) on the one-halo tile
-  float mub[RM][N1];
-  float acor[RM][3][N1];
-  float dmu[2][2][NT];              // mu0 - mu2, mu1 - mu2 of the owned points of planes z, z+1
+  float mub[RM][N1P];
+  float acor[RM][3][N1P];
+  float dmu[2][2][NTP];             // mu0 - mu2, mu1 - mu2 of the owned points of planes z, z+1
   InstanceConsts k;
   unsigned long long bar;
 };
@@ -940,11 +945,15 @@ __device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int
       : "memory");
 }
 
-template <int QL, bool OBS, typename GT, bool SZ = false>
-__global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const __grid_constant__ TmaMaps maps) {
+template <int QL, bool OBS, typename GT, bool SZ = false, int TYP = kPipeTY>
+__global__ void __launch_bounds__(TX * TYP, TYP <= 8 ? 2 : 1)
+    d3q19_step_pipe(const StepArgs a, const __grid_constant__ TmaMaps maps) {
+  using Smem = PipeSmem3<QL, GT, TYP>;
+  constexpr int NTP = Smem::NTP, PR2 = Smem::PR2, PR1 = Smem::PR1, N1P = Smem::N1P;
+  static_assert(2 * PR2 * 10 <= NTP && 6 * PR1 * 10 <= 3 * NTP, "one phi chunk, at most three history chunks a thread");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  PipeSmem3<QL, GT>& S = *reinterpret_cast<PipeSmem3<QL, GT>*>(smem_raw);
-  constexpr unsigned kOwnBytes = QL * NT * sizeof(GT) + (3 + NH) * NT * 4;
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  constexpr unsigned kOwnBytes = QL * NTP * sizeof(GT) + (3 + NH) * NTP * 4;
 
   const int t = threadIdx.x;
   const int tx = t % TX, ty = t / TX;
@@ -954,7 +963,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   const int x0 = (blockIdx.x % ntx) * TX;
   const int zs = (blockIdx.x / ntx) * a.strip;
   const int ze = min(zs + a.strip, nz);
-  const int y0 = blockIdx.y * TY;
+  const int y0 = blockIdx.y * TYP;
   const int b = blockIdx.z;
   const int nodes = (int)a.nodes;
   const int plane = nx * ny;
@@ -978,8 +987,8 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   // columns xs .. xs+3 of one row: inside the lattice or wrapped it is one
   // 16-byte copy from column `off`; mirrored it is four 4-byte copies from
   // off, off-1, off-2, off-3; mode -1 skips it.
-  //   phi chunk  t       (t < 240): array t / 120 (phi1, phi0), row, chunk of the two-halo tile
-  //   hist chunk t + 256 m (< 600): array id / 100 (u_x .. S_z), row, chunk of the one-halo tile
+  //   phi chunk  t        (t < 2 PR2 10): array t / (PR2 10) (phi1, phi0), row, chunk of the two-halo tile
+  //   hist chunk t + NTP m (< 6 PR1 10): array id / (PR1 10) (u_x .. S_z), row, chunk of the one-halo tile
   auto chunk = [&](int ylog, int xs, int ymax, int xmax, int& off, int& mode) {
     mode = -1;
     off = 0;
@@ -999,19 +1008,19 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   int pc_off, pc_mode, pc_dst;
   const float* pc_src;
   {
-    const int arr = t / 120, rem = t % 120, r = rem / 10, kk = rem % 10;
+    const int arr = t / (PR2 * 10), rem = t % (PR2 * 10), r = rem / 10, kk = rem % 10;
     chunk(y0 - 2 + r, x0 - 4 + 4 * kk, ny + 1, nx + 1, pc_off, pc_mode);
-    if (t >= 240) pc_mode = -1;
+    if (t >= 2 * PR2 * 10) pc_mode = -1;
     pc_dst = r * PW + 4 * kk;
     pc_src = arr == 0 ? phi1_now : p0_in;
   }
   int hc_off[3], hc_mode[3], hc_dst[3], hc_arr[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    const int id = t + NT * m;
-    const int arr = id / 100, rem = id % 100, r = rem / 10, kk = rem % 10;
+    const int id = t + NTP * m;
+    const int arr = id / (PR1 * 10), rem = id % (PR1 * 10), r = rem / 10, kk = rem % 10;
     chunk(y0 - 1 + r, x0 - 4 + 4 * kk, ny, nx, hc_off[m], hc_mode[m]);
-    if (id >= 600) hc_mode[m] = -1;
+    if (id >= 6 * PR1 * 10) hc_mode[m] = -1;
     hc_dst[m] = r * PW + 4 * kk;
     hc_arr[m] = arr;
   }
@@ -1028,7 +1037,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
   auto issue_phi = [&](int zl) {
     if (pc_mode < 0) return;
     const int zo = wrap_or_mirror(zl, nz, per_z) * plane;
-    float* base = (t / 120 == 0 ? S.phi1 : S.phi0)[ring(zl, RP5)];
+    float* base = (t / (PR2 * 10) == 0 ? S.phi1 : S.phi0)[ring(zl, RP5)];
     copy_chunk(base + pc_dst, pc_src + zo + pc_off, pc_mode);
   };
   auto issue_hist = [&](int zl) {
@@ -1060,7 +1069,7 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
              mu2);
     S.mub[ring(zl, RM)][p] = mubar1_of(k, mu0, mu1, mu2);
     // owned point: keep the differences the node update of plane zl uses
-    if (px >= 1 && px <= TX && py >= 1 && py <= TY) {
+    if (px >= 1 && px <= TX && py >= 1 && py <= TYP) {
       const int ow = (py - 1) * TX + (px - 1);
       S.dmu[zl & 1][0][ow] = mu0 - mu2;
       S.dmu[zl & 1][1][ow] = mu1 - mu2;
@@ -1079,21 +1088,23 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step_pipe(const StepArgs a, const
     S.acor[rm][2][p] = sy * uz - uy * sz;
   };
   auto calc_mub = [&](int zl) {
-    for (int p = t; p < N1; p += NT) mub_at(zl, p);
+    for (int p = t; p < N1P; p += NTP) mub_at(zl, p);
   };
   auto calc_prod = [&](int zl) {
-    for (int p = t; p < N1; p += NT) prod_at(zl, p);
+    for (int p = t; p < N1P; p += NTP) prod_at(zl, p);
   };
-  // Both on the one-halo tile (N1 = 340 points, 256 threads), balanced by whole warps: every thread takes the
-  // mubar_1 point t; warps 0-2 the remaining 84 mubar_1 points, warps 3-7 all 340 products (about a seventh of a
-  // mubar_1 point's work each), so no warp runs two of both while the others wait at the barrier.
-  static_assert(N1 - NT <= 96 && N1 <= 3 * (NT - 96), "halo work split of the 32 x 8 tile");
+  // Both on the one-halo tile (N1P points: 340 on 256 threads for 8 rows, 612 on 512 for 16), balanced by whole
+  // warps: every thread takes the mubar_1 point t; the first XW threads the remaining mubar_1 points, the others
+  // all the products (about a seventh of a mubar_1 point's work each), so no warp runs two of both while the others
+  // wait at the barrier.
+  constexpr int XW = ((N1P - NTP + 31) / 32) * 32;
+  static_assert(N1P > NTP && N1P <= 3 * (NTP - XW), "halo work split of the tile");
   auto calc_halo = [&](int zl) {
     mub_at(zl, t);
-    if (t < 96) {
-      if (t + NT < N1) mub_at(zl, t + NT);
+    if (t < XW) {
+      if (t + NTP < N1P) mub_at(zl, t + NTP);
     } else if (!SZ) {
-      for (int p = t - 96; p < N1; p += NT - 96) prod_at(zl, p);
+      for (int p = t - XW; p < N1P; p += NTP - XW) prod_at(zl, p);
     }
   };
 
@@ -1235,7 +1246,7 @@ int build_d3q19_maps(const void* g, int g_half, const float* mom, const float* h
     const cuuint64_t es = half ? 2 : 4;
     const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)planes * nbatch};
     const cuuint64_t strides[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
-    const cuuint32_t box[4] = {TX, TY, 1, (cuuint32_t)planes};
+    const cuuint32_t box[4] = {TX, kPipeTY, 1, (cuuint32_t)planes};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return encode(map, half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1256,17 +1267,19 @@ cudaError_t launch_step_q(const StepArgs& a, int nbatch, bool observe, cudaStrea
   if (maps) {
     TmaMaps m;
     memcpy(&m, maps, sizeof m);
-    const size_t smem = sizeof(PipeSmem3<QL, GT>);
+    const size_t smem = sizeof(PipeSmem3<QL, GT, kPipeTY>);
+    constexpr int NTP = TX * kPipeTY;
+    grid.y = (a.ny + kPipeTY - 1) / kPipeTY;
     static std::atomic<unsigned long long> configured{0};
     e = smem_opt_in(configured, smem, d3q19_step_pipe<QL, true, GT>, d3q19_step_pipe<QL, false, GT>,
                     d3q19_step_pipe<QL, true, GT, true>, d3q19_step_pipe<QL, false, GT, true>);
     if (e != cudaSuccess) return e;
     if (a.s_zero) {   // equal fluid densities: no mass flux, no correction force
-      if (observe) d3q19_step_pipe<QL, true, GT, true><<<grid, NT, smem, s>>>(a, m);
-      else d3q19_step_pipe<QL, false, GT, true><<<grid, NT, smem, s>>>(a, m);
+      if (observe) d3q19_step_pipe<QL, true, GT, true><<<grid, NTP, smem, s>>>(a, m);
+      else d3q19_step_pipe<QL, false, GT, true><<<grid, NTP, smem, s>>>(a, m);
     } else {
-      if (observe) d3q19_step_pipe<QL, true, GT><<<grid, NT, smem, s>>>(a, m);
-      else d3q19_step_pipe<QL, false, GT><<<grid, NT, smem, s>>>(a, m);
+      if (observe) d3q19_step_pipe<QL, true, GT><<<grid, NTP, smem, s>>>(a, m);
+      else d3q19_step_pipe<QL, false, GT><<<grid, NTP, smem, s>>>(a, m);
     }
     return cudaGetLastError();
   }
