@@ -337,6 +337,55 @@ __global__ void __launch_bounds__(256) d3q_moments(const float* __restrict__ f_a
   }
 }
 
+// Moments of the moving NS populations, summed over pairs of opposite velocities (s = g_i + g_opp,
+// d = g_i - g_opp, i the member listed first): the sum, the first moments m, the off-diagonal second
+// moments p_ab and the third-order sums e_a = sum c_a (c_b^2 + c_c^2) g and b_a = sum c_a (c_b^2 - c_c^2) g
+// (D3Q19, cyclic a, b, c); D3Q15: e_a = sum over corners c_a g, bx = sum cx cy cz g, by = bz = 0.
+template <int QL>
+__device__ __forceinline__ void ns_moments(const float* g, float& sum_nz, float& mx, float& my, float& mz,
+                                           float& pxy, float& pxz, float& pyz, float& ex, float& ey,
+                                           float& ez, float& bxm, float& bym, float& bzm) {
+  auto S = [&](int i) { return g[i] + g[LOPP<QL>(i)]; };
+  auto D = [&](int i) { return g[i] - g[LOPP<QL>(i)]; };
+  const float sa = S(1) + S(3) + S(5);
+  if constexpr (QL == 19) {
+    // first members: 7 (1,1,0), 9 (1,-1,0), 11 (1,0,1), 13 (1,0,-1), 15 (0,1,1), 17 (0,1,-1)
+    const float d7 = D(7), d9 = D(9), d11 = D(11), d13 = D(13), d15 = D(15), d17 = D(17);
+    const float s7 = S(7), s9 = S(9), s11 = S(11), s13 = S(13), s15 = S(15), s17 = S(17);
+    sum_nz = sa + ((s7 + s9) + (s11 + s13) + (s15 + s17));
+    pxy = s7 - s9;
+    pxz = s11 - s13;
+    pyz = s15 - s17;
+    const float xa = d7 + d9, xb = d11 + d13;   // x-edges in the xy and xz planes
+    const float ya = d15 + d17, yb = d7 - d9;   // y-edges in the yz and xy planes
+    const float za = d11 - d13, zb = d15 - d17; // z-edges in the xz and yz planes
+    ex = xa + xb;
+    bxm = xa - xb;
+    ey = ya + yb;
+    bym = ya - yb;
+    ez = za + zb;
+    bzm = za - zb;
+  } else {
+    // first members of the corner pairs: 7 (1,1,1), 8 (-1,1,1), 9 (1,-1,1), 10 (-1,-1,1)
+    const float d7 = D(7), d8 = D(8), d9 = D(9), d10 = D(10);
+    const float s7 = S(7), s8 = S(8), s9 = S(9), s10 = S(10);
+    const float sp = s7 + s10, sq = s8 + s9, sr = s7 - s10, st = s8 - s9;
+    sum_nz = sa + (sp + sq);
+    pxy = sp - sq;
+    pxz = sr - st;
+    pyz = sr + st;
+    const float dp = d7 + d10, dq = d8 + d9, dr = d7 - d10, dt = d8 - d9;
+    ex = dr - dt;
+    ey = dr + dt;
+    ez = dp + dq;
+    bxm = dp - dq;
+    bym = bzm = 0.f;
+  }
+  mx = D(1) + ex;
+  my = D(3) + ey;
+  mz = D(5) + ez;
+}
+
 // ---------------------------------------------------------------------------
 // per-node update shared by both fused kernels
 // ---------------------------------------------------------------------------
@@ -375,8 +424,9 @@ struct Outs {
 // MU_IN: the chemical-potential differences of the node come in `in` (the pipelined kernel keeps them from its
 // mubar_1 pass over the same planes, bitwise the values computed here otherwise).  SZ: rho1 == rho2, so the mass
 // flux S = (rho1 - rho2) M grad(mubar_1) / gamma_1 is zero and with it the correction force F_c = div(S u - u S) / 2;
-// its stencils are skipped (the same values up to the sign of zeros).
-template <int QL, bool OBS, typename GT, bool MU_IN = false, bool SZ = false>
+// its stencils are skipped (the same values up to the sign of zeros).  PER: the lattice is periodic on all
+// three axes (the bounce-back selection of the pushes is compiled out).
+template <int QL, bool OBS, typename GT, bool MU_IN = false, bool SZ = false, bool PER = false>
 __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings& R, const OwnIn<QL>& in,
                                             const Outs& o, int x, int y, int z) {
   const int nx = o.nx, ny = o.ny, nz = o.nz, nodes = o.nodes, plane = o.plane;
@@ -461,36 +511,8 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
 
   // NS moments
   const float* g = in.g;
-  float sum_nz = 0.f, mx = 0.f, my = 0.f, mz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
-  float ex = 0.f, ey = 0.f, ez = 0.f, bxm = 0.f, bym = 0.f, bzm = 0.f;
-#pragma unroll
-  for (int i = 1; i < QL; ++i) {
-    const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
-    const float v = g[i];
-    sum_nz += v;
-    if (cx) mx += cx > 0 ? v : -v;
-    if (cy) my += cy > 0 ? v : -v;
-    if (cz) mz += cz > 0 ? v : -v;
-    if (cx && cy) pxy += cx * cy > 0 ? v : -v;
-    if (cx && cz) pxz += cx * cz > 0 ? v : -v;
-    if (cy && cz) pyz += cy * cz > 0 ? v : -v;
-    // third-order sums.  D3Q19: sum c_a (c_b^2 + c_c^2) g and sum c_a (c_b^2 - c_c^2) g (cyclic a, b, c);
-    // D3Q15: the corner sums sum_corner c_a g and sum cx cy cz g (in bxm)
-    if (cx && (cy || cz)) {
-      ex += cx > 0 ? v : -v;
-      if constexpr (QL == 19) bxm += ((cy ? 1 : -1) * cx > 0) ? v : -v;
-    }
-    if (cy && (cz || cx)) {
-      ey += cy > 0 ? v : -v;
-      if constexpr (QL == 19) bym += ((cz ? 1 : -1) * cy > 0) ? v : -v;
-    }
-    if (cz && (cx || cy)) {
-      ez += cz > 0 ? v : -v;
-      if constexpr (QL == 19) bzm += ((cx ? 1 : -1) * cz > 0) ? v : -v;
-    }
-    if constexpr (QL == 15)
-      if (cx && cy && cz) bxm += cx * cy * cz > 0 ? v : -v;
-  }
+  float sum_nz, mx, my, mz, pxy, pxz, pyz, ex, ey, ez, bxm, bym, bzm;
+  ns_moments<QL>(g, sum_nz, mx, my, mz, pxy, pxz, pyz, ex, ey, ez, bxm, bym, bzm);
 
   // velocity with the solid penalisation force (u_w = 0)
   const float inv_rho = __frcp_rn(rho);
@@ -519,9 +541,10 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
 
   // push destinations without branches: per axis and sign, the offset of the
   // neighbour (periodic wrap folded in) and whether a wall reflects instead
-  const bool wxp = x + 1 >= nx && !o.per_x, wxm = x == 0 && !o.per_x;
-  const bool wyp = y + 1 >= ny && !o.per_y, wym = y == 0 && !o.per_y;
-  const bool wzp = z + 1 >= nz && !o.per_z, wzm = z == 0 && !o.per_z;
+  // (PER: every axis periodic, no push meets a wall)
+  const bool wxp = !PER && x + 1 >= nx && !o.per_x, wxm = !PER && x == 0 && !o.per_x;
+  const bool wyp = !PER && y + 1 >= ny && !o.per_y, wym = !PER && y == 0 && !o.per_y;
+  const bool wzp = !PER && z + 1 >= nz && !o.per_z, wzm = !PER && z == 0 && !o.per_z;
   const int oxp = x + 1 < nx ? 1 : 1 - nx, oxm = x > 0 ? -1 : nx - 1;
   const int oyp = y + 1 < ny ? nx : nx - plane, oym = y > 0 ? -nx : plane - nx;
   const int ozp = z + 1 < nz ? plane : plane - nodes, ozm = z > 0 ? -plane : nodes - plane;
@@ -582,32 +605,43 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
     const float om1 = 1.f - s2a;
     GT* const g_out = static_cast<GT*>(o.g_out);
     store(g_out, 0, om1 * g[0] + k.w0 * base - s2a * p * ic2);
-#pragma unroll
-    for (int i = 1; i < QL; ++i) {
-      const int cx = LX<QL>(i), cy = LY<QL>(i), cz = LZ<QL>(i);
-      float X = base;
-      if (cx) X += cx > 0 ? Dx + Vx : Dx - Vx;
-      if (cy) X += cy > 0 ? Dy + Vy : Dy - Vy;
-      if (cz) X += cz > 0 ? Dz + Vz : Dz - Vz;
-      if (cx && cy) X += cx * cy > 0 ? Oxy : -Oxy;
-      if (cx && cz) X += cx * cz > 0 ? Oxz : -Oxz;
-      if (cy && cz) X += cy * cz > 0 ? Oyz : -Oyz;
-      if (i < 7) {
-        // axis: A_a(c) = -2 cs2 c_a (D3Q19), -cs2 c_a (D3Q15); B = 0
-        const float T = cx ? Tx : (cy ? Ty : Tz);
-        const int c = cx + cy + cz;
-        X += c > 0 ? cA * T : -cA * T;
-      } else if constexpr (QL == 19) {
-        // edge: -c_a [(1 - 2 cs2) T_a + B_a U_a / c_a] over its two axes
-        if (cx) { const float e = cy ? Px : Qx; X -= cx > 0 ? e : -e; }
-        if (cy) { const float e = cz ? Py : Qy; X -= cy > 0 ? e : -e; }
-        if (cz) { const float e = cx ? Pz : Qz; X -= cz > 0 ? e : -e; }
-      } else {
-        // corner: -(1 - cs2) c.T - cx cy cz U
-        const float ct = (cx > 0 ? Tx : -Tx) + (cy > 0 ? Ty : -Ty) + (cz > 0 ? Tz : -Tz);
-        X -= k3 * ct + (cx * cy * cz > 0 ? Ux : -Ux);
+    // X_i = E + O and X_opp(i) = E - O: the part E even in c (base, D, O terms) and the part O odd in c
+    // (V and the third-order terms) are formed once per pair of opposite velocities
+    auto put2 = [&](int i, float E, float O) {
+      store(g_out, i, om1 * g[i] + weight(k, i) * (E + O));
+      store(g_out, LOPP<QL>(i), om1 * g[LOPP<QL>(i)] + weight(k, i) * (E - O));
+    };
+    // axis: A_a(c) = -2 cs2 c_a (D3Q19), -cs2 c_a (D3Q15); B = 0
+    put2(1, base + Dx, Vx + cA * Tx);
+    put2(3, base + Dy, Vy + cA * Ty);
+    put2(5, base + Dz, Vz + cA * Tz);
+    if constexpr (QL == 19) {
+      // edge: -c_a [(1 - 2 cs2) T_a + B_a U_a / c_a] over its two axes, B_a U_a / c_a = +U_a on the edges of
+      // the axis that follows a cyclically (P_a), -U_a on the other (Q_a)
+      const float Bxy = base + Dx + Dy, Bxz = base + Dx + Dz, Byz = base + Dy + Dz;
+      {
+        const float u = Vx - Px, v = Vy - Qy;   // edges (1, +-1, 0)
+        put2(7, Bxy + Oxy, u + v);
+        put2(9, Bxy - Oxy, u - v);
       }
-      store(g_out, i, om1 * g[i] + weight(k, i) * X);
+      {
+        const float u = Vx - Qx, v = Vz - Pz;   // edges (1, 0, +-1)
+        put2(11, Bxz + Oxz, u + v);
+        put2(13, Bxz - Oxz, u - v);
+      }
+      {
+        const float u = Vy - Py, v = Vz - Qz;   // edges (0, 1, +-1)
+        put2(15, Byz + Oyz, u + v);
+        put2(17, Byz - Oyz, u - v);
+      }
+    } else {
+      // corner: -(1 - cs2) c.T - cx cy cz U
+      const float B = base + Dx + Dy + Dz;
+      const float u = Vx - k3 * Tx, v = Vy - k3 * Ty, w = Vz - k3 * Tz;
+      put2(7, B + Oxy + Oxz + Oyz, u + v + w - Ux);     // (1, 1, 1)
+      put2(8, B - Oxy - Oxz + Oyz, v + w - u + Ux);     // (-1, 1, 1)
+      put2(9, B - Oxy + Oxz - Oyz, u - v + w + Ux);     // (1, -1, 1)
+      put2(10, B + Oxy - Oxz - Oyz, w - u - v - Ux);    // (-1, -1, 1)
     }
   }
 
@@ -945,7 +979,7 @@ __device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int
       : "memory");
 }
 
-template <int QL, bool OBS, typename GT, bool SZ = false, int TYP = kPipeTY>
+template <int QL, bool OBS, typename GT, bool SZ = false, bool PER = false, int TYP = kPipeTY>
 __global__ void __launch_bounds__(TX * TYP, TYP <= 8 ? 2 : 1)
     d3q19_step_pipe(const StepArgs a, const __grid_constant__ TmaMaps maps) {
   using Smem = PipeSmem3<QL, GT, TYP>;
@@ -1187,7 +1221,7 @@ __global__ void __launch_bounds__(TX * TYP, TYP <= 8 ? 2 : 1)
     R.sw2 = PW;
     R.i1 = (ty + 1) * HX1 + (tx + 1);
     R.sw1 = HX1;
-    node_update<QL, OBS, GT, true, SZ>(k, R, in, o, x, y, z);
+    node_update<QL, OBS, GT, true, SZ, PER>(k, R, in, o, x, y, z);
   }
   // leave no copy in flight: asynchronous copies, and a TMA load issued for a plane not processed
   cp_wait_all();
@@ -1272,13 +1306,18 @@ cudaError_t launch_step_q(const StepArgs& a, int nbatch, bool observe, cudaStrea
     grid.y = (a.ny + kPipeTY - 1) / kPipeTY;
     static std::atomic<unsigned long long> configured{0};
     e = smem_opt_in(configured, smem, d3q19_step_pipe<QL, true, GT>, d3q19_step_pipe<QL, false, GT>,
-                    d3q19_step_pipe<QL, true, GT, true>, d3q19_step_pipe<QL, false, GT, true>);
+                    d3q19_step_pipe<QL, true, GT, true>, d3q19_step_pipe<QL, false, GT, true>,
+                    d3q19_step_pipe<QL, false, GT, false, true>, d3q19_step_pipe<QL, false, GT, true, true>);
     if (e != cudaSuccess) return e;
+    // the periodic form for the non-observing steps of fully periodic lattices (observing steps are rare)
+    const bool per = a.per_x && a.per_y && a.per_z && !observe;
     if (a.s_zero) {   // equal fluid densities: no mass flux, no correction force
       if (observe) d3q19_step_pipe<QL, true, GT, true><<<grid, NTP, smem, s>>>(a, m);
+      else if (per) d3q19_step_pipe<QL, false, GT, true, true><<<grid, NTP, smem, s>>>(a, m);
       else d3q19_step_pipe<QL, false, GT, true><<<grid, NTP, smem, s>>>(a, m);
     } else {
       if (observe) d3q19_step_pipe<QL, true, GT><<<grid, NTP, smem, s>>>(a, m);
+      else if (per) d3q19_step_pipe<QL, false, GT, false, true><<<grid, NTP, smem, s>>>(a, m);
       else d3q19_step_pipe<QL, false, GT><<<grid, NTP, smem, s>>>(a, m);
     }
     return cudaGetLastError();
