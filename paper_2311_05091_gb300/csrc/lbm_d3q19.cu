@@ -341,12 +341,12 @@ __global__ void __launch_bounds__(256) d3q_moments(const float* __restrict__ f_a
 // d = g_i - g_opp, i the member listed first): the sum, the first moments m, the off-diagonal second
 // moments p_ab and the third-order sums e_a = sum c_a (c_b^2 + c_c^2) g and b_a = sum c_a (c_b^2 - c_c^2) g
 // (D3Q19, cyclic a, b, c); D3Q15: e_a = sum over corners c_a g, bx = sum cx cy cz g, by = bz = 0.
-template <int QL>
-__device__ __forceinline__ void ns_moments(const float* g, float& sum_nz, float& mx, float& my, float& mz,
+template <int QL, typename GA>
+__device__ __forceinline__ void ns_moments(const GA& g, float& sum_nz, float& mx, float& my, float& mz,
                                            float& pxy, float& pxz, float& pyz, float& ex, float& ey,
                                            float& ez, float& bxm, float& bym, float& bzm) {
-  auto S = [&](int i) { return g[i] + g[LOPP<QL>(i)]; };
-  auto D = [&](int i) { return g[i] - g[LOPP<QL>(i)]; };
+  auto S = [&](int i) { return g(i) + g(LOPP<QL>(i)); };
+  auto D = [&](int i) { return g(i) - g(LOPP<QL>(i)); };
   const float sa = S(1) + S(3) + S(5);
   if constexpr (QL == 19) {
     // first members: 7 (1,1,0), 9 (1,-1,0), 11 (1,0,1), 13 (1,0,-1), 15 (0,1,1), 17 (0,1,-1)
@@ -426,13 +426,18 @@ struct Outs {
 // flux S = (rho1 - rho2) M grad(mubar_1) / gamma_1 is zero and with it the correction force F_c = div(S u - u S) / 2;
 // its stencils are skipped (the same values up to the sign of zeros).  PER: the lattice is periodic on all
 // three axes (the bounce-back selection of the pushes is compiled out).
-template <int QL, bool OBS, typename GT, bool MU_IN = false, bool SZ = false, bool PER = false>
+template <int QL, bool OBS, typename GT, bool MU_IN = false, bool SZ = false, bool PER = false, typename GA,
+          typename GB>
 __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings& R, const OwnIn<QL>& in,
-                                            const Outs& o, int x, int y, int z) {
+                                            const GA& g, const GB& g_late, const Outs& o, int x, int y, int z) {
   const int nx = o.nx, ny = o.ny, nz = o.nz, nodes = o.nodes, plane = o.plane;
   const int node = z * plane + y * nx + x;
   const float cs2 = k.cs2, cs4 = k.cs4;
   const int i2 = R.i2, s2 = R.sw2, i1 = R.i1, s1 = R.sw1;
+
+  // NS moments first: the populations then wait in their owned slot (or registers) until the collision
+  float sum_nz, mx, my, mz, pxy, pxz, pyz, ex, ey, ez, bxm, bym, bzm;
+  ns_moments<QL>(g, sum_nz, mx, my, mz, pxy, pxz, pyz, ex, ey, ez, bxm, bym, bzm);
 
   // stencils of phi0, phi1 and mubar_1, products; each neighbourhood is read once
   float ph0, ph1, g0x, g0y, g0z, g1x, g1y, g1z, lap0, lap1;
@@ -508,11 +513,6 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
   const float Fx = d02 * g0x + d12 * g1x + one_m0 * k.bx + Fcx;
   const float Fy = d02 * g0y + d12 * g1y + one_m0 * k.by + Fcy;
   const float Fz = d02 * g0z + d12 * g1z + one_m0 * k.bz + Fcz;
-
-  // NS moments
-  const float* g = in.g;
-  float sum_nz, mx, my, mz, pxy, pxz, pyz, ex, ey, ez, bxm, bym, bzm;
-  ns_moments<QL>(g, sum_nz, mx, my, mz, pxy, pxz, pyz, ex, ey, ez, bxm, bym, bzm);
 
   // velocity with the solid penalisation force (u_w = 0)
   const float inv_rho = __frcp_rn(rho);
@@ -604,12 +604,12 @@ __device__ __forceinline__ void node_update(const InstanceConsts& k, const Rings
     const float Pz = k3 * Tz + Uz, Qz = k3 * Tz - Uz;
     const float om1 = 1.f - s2a;
     GT* const g_out = static_cast<GT*>(o.g_out);
-    store(g_out, 0, om1 * g[0] + k.w0 * base - s2a * p * ic2);
+    store(g_out, 0, om1 * g_late(0) + k.w0 * base - s2a * p * ic2);
     // X_i = E + O and X_opp(i) = E - O: the part E even in c (base, D, O terms) and the part O odd in c
     // (V and the third-order terms) are formed once per pair of opposite velocities
     auto put2 = [&](int i, float E, float O) {
-      store(g_out, i, om1 * g[i] + weight(k, i) * (E + O));
-      store(g_out, LOPP<QL>(i), om1 * g[LOPP<QL>(i)] + weight(k, i) * (E - O));
+      store(g_out, i, om1 * g_late(i) + weight(k, i) * (E + O));
+      store(g_out, LOPP<QL>(i), om1 * g_late(LOPP<QL>(i)) + weight(k, i) * (E - O));
     };
     // axis: A_a(c) = -2 cs2 c_a (D3Q19), -cs2 c_a (D3Q15); B = 0
     put2(1, base + Dx, Vx + cA * Tx);
@@ -900,7 +900,8 @@ __global__ void __launch_bounds__(NT, 2) d3q19_step(const StepArgs a) {
     R.sw2 = HX2;
     R.i1 = (ty + 1) * HX1 + (tx + 1);
     R.sw1 = HX1;
-    node_update<QL, OBS, GT>(k, R, in, o, x, y, z);
+    auto ga = [&](int i) { return in.g[i]; };
+    node_update<QL, OBS, GT>(k, R, in, ga, ga, o, x, y, z);
   }
 }
 
@@ -927,7 +928,7 @@ struct TmaMaps {
 template <int QL, typename GT, int TYP>
 struct alignas(128) PipeSmem3 {
   static constexpr int NTP = TX * TYP, PR2 = TYP + 4, PR1 = TYP + 2, N1P = HX1 * (TYP + 2);
-  GT gown[QL][NTP];                 // TMA destinations: g of the owned columns,
+  GT gown[2][QL][NTP];              // TMA destinations: g of the owned columns (planes z, z+1),
   float own[3 + NH][NTP];           // then j 0-2 and history 3-9
   float phi1[RP5][PR2 * PW];        // two-halo tile rows y0-2 .. y0+TYP+1
   float phi0[RP5][PR2 * PW];
@@ -940,6 +941,18 @@ struct alignas(128) PipeSmem3 {
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// a shared-memory load kept where it is written (volatile asm: never merged with an earlier load)
+__device__ __forceinline__ float lds_again(const float* p) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(smem_u32(p)));
+  return v;
+}
+__device__ __forceinline__ __half lds_again(const __half* p) {
+  unsigned short v;
+  asm volatile("ld.shared.b16 %0, [%1];\n" : "=h"(v) : "r"(smem_u32(p)));
+  return __ushort_as_half(v);
+}
 
 __device__ __forceinline__ void cp16(float* dst, const float* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -987,7 +1000,7 @@ __global__ void __launch_bounds__(TX * TYP, TYP <= 8 ? 2 : 1)
   static_assert(2 * PR2 * 10 <= NTP && 6 * PR1 * 10 <= 3 * NTP, "one phi chunk, at most three history chunks a thread");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
-  constexpr unsigned kOwnBytes = QL * NTP * sizeof(GT) + (3 + NH) * NTP * 4;
+  constexpr unsigned kOwnBytes = QL * NTP * sizeof(GT) + (3 + NH) * NTP * 4;   // one plane's owned tiles
 
   const int t = threadIdx.x;
   const int tx = t % TX, ty = t / TX;
@@ -1083,10 +1096,15 @@ __global__ void __launch_bounds__(TX * TYP, TYP <= 8 ? 2 : 1)
       copy_chunk(&S.hus[sl][hc_arr[m]][hc_dst[m]], h_in + (hc_arr[m] + 1) * nodes + zo + hc_off[m], hc_mode[m]);
     }
   };
-  auto issue_own = [&](int z) {   // one thread
+  // The owned tiles of plane z complete one phase of the barrier: g into its slot of the two-plane ring
+  // (armed with the bytes of all three tiles), then j and the history into their single slot.
+  auto issue_own_g = [&](int z) {   // one thread
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     bar_expect(&S.bar, kOwnBytes);
-    tma_load4(S.gown[0], &maps.g, x0, y0, z, b * QL, &S.bar);
+    tma_load4(S.gown[z & 1][0], &maps.g, x0, y0, z, b * QL, &S.bar);
+  };
+  auto issue_own_jh = [&](int z) {   // one thread, after issue_own_g(z)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     tma_load4(S.own[0], &maps.j, x0, y0, z, b * 3, &S.bar);
     tma_load4(S.own[3], &maps.h, x0, y0, z, b * NH, &S.bar);
   };
@@ -1148,7 +1166,10 @@ __global__ void __launch_bounds__(TX * TYP, TYP <= 8 ? 2 : 1)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();   // constants and barrier visible
-  if (t == 0) issue_own(zs);
+  if (t == 0) {
+    issue_own_g(zs);
+    issue_own_jh(zs);
+  }
   for (int q = -2; q <= 1; ++q) issue_phi(zs + q);
   issue_hist(zs - 1);
   issue_hist(zs);
@@ -1182,16 +1203,17 @@ __global__ void __launch_bounds__(TX * TYP, TYP <= 8 ? 2 : 1)
       ok = false;
       break;
     }
+    // the g slot of z+1 held z-1, whose node updates are done
+    if (t == 0 && z + 1 < ze) issue_own_g(z + 1);
     if (z + 3 <= ze + 1) issue_phi(z + 3);
     if (z + 2 <= ze) issue_hist(z + 2);
     cp_commit();
     calc_halo(z + 1);
     __syncthreads();
 
-    // owned inputs of plane z into registers, then the slot takes plane z+1
+    // owned j and history of plane z into registers, then their slot takes plane z+1; g stays in its slot and
+    // is read where the node update uses it
     OwnIn<QL> in;
-#pragma unroll
-    for (int i = 0; i < QL; ++i) in.g[i] = g_load(S.gown[i][t], k);
     in.jx = S.own[0][t];
     in.jy = S.own[1][t];
     in.jz = S.own[2][t];
@@ -1205,7 +1227,7 @@ __global__ void __launch_bounds__(TX * TYP, TYP <= 8 ? 2 : 1)
     in.d02 = S.dmu[z & 1][0][t];
     in.d12 = S.dmu[z & 1][1][t];
     __syncthreads();
-    if (t == 0 && z + 1 < ze) issue_own(z + 1);
+    if (t == 0 && z + 1 < ze) issue_own_jh(z + 1);
     if (!own) continue;
 
     Rings R;
@@ -1221,7 +1243,12 @@ __global__ void __launch_bounds__(TX * TYP, TYP <= 8 ? 2 : 1)
     R.sw2 = PW;
     R.i1 = (ty + 1) * HX1 + (tx + 1);
     R.sw1 = HX1;
-    node_update<QL, OBS, GT, true, SZ, PER>(k, R, in, o, x, y, z);
+    const GT* gs = &S.gown[z & 1][0][t];
+    auto ga = [&](int i) { return g_load(gs[i * NTP], k); };
+    // the collision reads the populations again, by loads the compiler does not merge with the first ones,
+    // so they need no registers over the stencil and force evaluation
+    auto gl = [&](int i) { return g_load(lds_again(gs + i * NTP), k); };
+    node_update<QL, OBS, GT, true, SZ, PER>(k, R, in, ga, gl, o, x, y, z);
   }
   // leave no copy in flight: asynchronous copies, and a TMA load issued for a plane not processed
   cp_wait_all();
