@@ -7,8 +7,8 @@
 // Tensors are NHWC float32 in memory (pixel p = (n h + y) w + x, channel
 // innermost).  3x3 convolutions run on the tensor cores with BF16 operands
 // and FP32 accumulation: the forward (and data-gradient) convolution with
-// tcgen05.mma and a TMEM accumulator, the weight gradient with mma.sync
-// m16n8k16; activations are rounded to BF16 as they enter a convolution,
+// tcgen05.mma and a TMEM accumulator, the weight gradient likewise with
+// both operands MN-major; activations are rounded to BF16 as they enter a convolution,
 // weights are kept as a BF16 copy of FP32 master weights.  Weight layout: wt[tap][cout][cin], tap = 3 ky + kx, so a
 // pair of input channels is one 32-bit word.
 #include <cuda_bf16.h>
@@ -27,14 +27,6 @@ constexpr int kProjectPasses = 3;   // mass-correction passes of lbm_nn_project
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // ---------------------------------------------------------------------------
@@ -242,115 +234,174 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_fwd_tc(const float* __rest
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient, per chunk z of 64-pixel row segments:
+// weight gradient on the 5th-generation tensor cores, per chunk z of W-pixel row segments (W = 64, or 32 on
+// images narrower than 64):
 //   part[z][tap][co][ci] = sum_{p in chunk z} dy[p][co] x[p + shift(tap)][ci]
-// CTA: a 32 (co) x 32 (ci) tile, 9 warps, warp = tap.  Per row segment
-// (image, row y, columns x0 .. x0 + 63) the CTA stages dy^T [co][px] and, for
-// each column offset kx, x^T [kx][row y + ky - 1][ci][px + kx - 1] in shared
-// memory as BF16 (zero outside the image), so that every mma fragment is one
-// aligned 32-bit shared load; warp (ky, kx) then multiplies dy^T (32 x 64)
-// by its shifted x (64 x 32).  Rows are padded to 72 elements (36 words), so
-// the 32 lanes of a fragment load hit 32 different banks.
-// grid (ceil(cout / 32), ceil(cin / 32), chunks), 288 threads.
+// A CTA owns 128 output channels x 32 input channels of the three taps (ky, 0..2) of one kernel row ky:
+// D_kx (128 x 32, FP32 in TMEM columns 32 kx ..) += A (128 co x 16 pixels) * B_kx^T (32 ci x 16 pixels),
+// sixteen pixels of the chunk at a time.  The reduction runs over pixels, and both tensors keep their channels
+// innermost, so both operands are staged as BF16 in the canonical MN-major layout without swizzle: core
+// matrices of 8 pixels x 16 bytes (8 channels), the pixels of a segment 16 bytes apart (consecutive core
+// matrices along K 128 bytes apart), the 8-channel groups SBO bytes apart:
+//   A: dy of the segment's W pixels, [co group][pixel];
+//   B: x of image row y + ky - 1 at columns x0 - 1 .. x0 + W, [ci group][column]; tap kx is the window that
+//      starts kx columns (16 kx bytes) further.
+// Channels beyond cout or cin and pixels outside the image are zero.  Two stages as in the forward kernel:
+// a stage is refilled only after the bounded wait for the products that read it.
+// grid (cout tiles of 128, 3 x cin tiles of 32, chunks), 256 threads.
 // ---------------------------------------------------------------------------
-constexpr int kSeg = 64, kPad = 72, kWgThreads = 288;
+constexpr int kWtM = 128, kWtN = 32, kWtThreads = 256;
 
-__global__ void __launch_bounds__(kWgThreads) conv3x3_wgrad_seg(const float* __restrict__ x,
-                                                                const float* __restrict__ dy,
-                                                                float* __restrict__ part, int n, int h, int w,
-                                                                int cin, int cout, long long segs_per_chunk) {
-  __shared__ __align__(16) __nv_bfloat16 sdy[32][kPad];
-  __shared__ __align__(16) __nv_bfloat16 sx[3][3][32][kPad];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int ky = warp / 3, kx = warp % 3;
-  const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
-  const int spr = (w + kSeg - 1) / kSeg;                       // segments per image row
+template <int W>
+struct WgTcSmem {
+  static constexpr int kA = (kWtM / 8) * W * 16;
+  static constexpr int kB = (kWtN / 8) * (W + 2) * 16;
+  static constexpr int kStage = kA + kB;
+  static constexpr int bytes() { return 2 * kStage + 64; }
+};
+
+// instruction descriptor of kind::f16 with both operands MN-major (transpose bits 15 and 16)
+__host__ __device__ constexpr uint32_t umma_idesc_mn(int m, int n) { return umma_idesc(m, n) | (1u << 15) | (1u << 16); }
+
+template <int W>
+__global__ void __launch_bounds__(kWtThreads) conv3x3_wgrad_tc(const float* __restrict__ x,
+                                                             const float* __restrict__ dy,
+                                                             float* __restrict__ part, int n, int h, int w,
+                                                             int cin, int cout, long long segs_per_chunk) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  using SM = WgTcSmem<W>;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::kStage);   // one mbarrier per stage
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int co0 = blockIdx.x * kWtM;
+  const int ky = blockIdx.y % 3, ci0 = (blockIdx.y / 3) * kWtN;
+  const int spr = (w + W - 1) / W;                           // segments per image row
   const long long nseg = (long long)n * h * spr;
   const long long s0 = (long long)blockIdx.z * segs_per_chunk;
   const long long s1 = min(nseg, s0 + segs_per_chunk);
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-  for (long long sg = s0; sg < s1; ++sg) {
+  const int cga = min(kWtM, cout - co0) / 8, cgb = min(kWtN, cin - ci0) / 8;   // channel groups present
+  const uint32_t bar0 = smem_addr(bar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int k = 0; k < 2; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8 * k), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // the channel groups that are not present stay zero in both stages
+  for (int st = 0; st < 2; ++st) {
+    unsigned char* sA = smem + st * SM::kStage;
+    for (int e = tid; e < (kWtM / 8 - cga) * W; e += kWtThreads)
+      *reinterpret_cast<uint4*>(sA + (cga * W + e) * 16) = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < (kWtN / 8 - cgb) * (W + 2); e += kWtThreads)
+      *reinterpret_cast<uint4*>(sA + SM::kA + (cgb * (W + 2) + e) * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+
+  bool ok = true;
+  long long it = 0;
+  for (long long sg = s0; sg < s1; ++sg, ++it) {
+    const int st = (int)(it & 1);
+    unsigned char* sA = smem + st * SM::kStage;
+    unsigned char* sB = sA + SM::kA;
+    // the products of segment it - 2 read this stage: wait for them (phase (it - 2) / 2 of its barrier)
+    if (it >= 2) ok = ok && mbar_wait(bar0 + 8 * st, (uint32_t)(((it - 2) >> 1) & 1));
     const int img = (int)(sg / ((long long)h * spr));
     const int y = (int)((sg / spr) % h);
-    const int x0 = (int)(sg % spr) * kSeg;
-    __syncthreads();                                           // the previous segment's fragments are consumed
-    // dy^T: 64 pixels x 32 channels as 8 float4 per pixel
-#pragma unroll 2
-    for (int e = threadIdx.x; e < kSeg * 8; e += kWgThreads) {
-      const int j = e >> 3, c4 = (e & 7) * 4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (x0 + j < w && co0 + c4 < cout)
-        v = *reinterpret_cast<const float4*>(dy + (((long long)img * h + y) * w + x0 + j) * cout + co0 + c4);
-      sdy[c4][j] = __float2bfloat16_rn(v.x);
-      sdy[c4 + 1][j] = __float2bfloat16_rn(v.y);
-      sdy[c4 + 2][j] = __float2bfloat16_rn(v.z);
-      sdy[c4 + 3][j] = __float2bfloat16_rn(v.w);
+    const int x0 = (int)(sg % spr) * W;
+    // A: dy of pixels x0 .. x0 + W - 1 of row y, then B: x of row y + ky - 1 at columns x0 - 1 .. x0 + W, in one
+    // loop (unrolled so that the loads of several items are in flight before their conversions)
+    const int yy = y + ky - 1;
+    const bool row_in = yy >= 0 && yy < h;
+    const int nA = cga * W, nAB = nA + cgb * (W + 2);
+#pragma unroll 4
+    for (int e = tid; e < nAB; e += kWtThreads) {
+      const float* src = nullptr;
+      unsigned char* dst;
+      if (e < nA) {
+        const int px = e % W, cg = e / W;
+        const int xc = x0 + px;
+        if (xc < w) src = dy + (((long long)img * h + y) * w + xc) * cout + co0 + 8 * cg;
+        dst = sA + (cg * W + px) * 16;
+      } else {
+        const int j = (e - nA) % (W + 2), cg = (e - nA) / (W + 2);
+        const int xc = x0 + j - 1;
+        if (row_in && xc >= 0 && xc < w) src = x + (((long long)img * h + yy) * w + xc) * cin + ci0 + 8 * cg;
+        dst = sB + (cg * (W + 2) + j) * 16;
+      }
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (src) {
+        const float4 p = *reinterpret_cast<const float4*>(src);
+        const float4 q = *reinterpret_cast<const float4*>(src + 4);
+        v = make_uint4(pack_bf16(p.x, p.y), pack_bf16(p.z, p.w), pack_bf16(q.x, q.y), pack_bf16(q.z, q.w));
+      }
+      *reinterpret_cast<uint4*>(dst) = v;
     }
-    // x^T: rows y - 1 .. y + 1, columns x0 - 1 .. x0 + 64, 32 channels; column xc goes to copy kx at xc - x0 - kx + 1
-#pragma unroll 3
-    for (int e = threadIdx.x; e < 3 * (kSeg + 2) * 8; e += kWgThreads) {
-      const int r = e / ((kSeg + 2) * 8), rem = e % ((kSeg + 2) * 8);
-      const int jc = rem >> 3, c4 = (rem & 7) * 4;             // jc = xc - x0 + 1 in 0 .. 65
-      const int yy = y + r - 1, xc = x0 + jc - 1;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (yy >= 0 && yy < h && xc >= 0 && xc < w && ci0 + c4 < cin)
-        v = *reinterpret_cast<const float4*>(x + (((long long)img * h + yy) * w + xc) * cin + ci0 + c4);
-      const __nv_bfloat16 b0 = __float2bfloat16_rn(v.x), b1 = __float2bfloat16_rn(v.y);
-      const __nv_bfloat16 b2 = __float2bfloat16_rn(v.z), b3 = __float2bfloat16_rn(v.w);
+    asm volatile("fence.proxy.async.shared::cta;");       // generic-proxy stores visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0 && ok) {
+      constexpr uint32_t idesc = umma_idesc_mn(kWtM, kWtN);
+#pragma unroll 1
+      for (int kx = 0; kx < 3; ++kx) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int j = jc - k;
-        if (j >= 0 && j < kSeg) {
-          sx[k][r][c4][j] = b0;
-          sx[k][r][c4 + 1][j] = b1;
-          sx[k][r][c4 + 2][j] = b2;
-          sx[k][r][c4 + 3][j] = b3;
+        for (int ks = 0; ks < W / 16; ++ks) {
+          // MN-major, no swizzle: LBO = stride of core matrices along K, SBO = along M / N
+          const uint64_t ad = umma_desc(smem_addr(sA + ks * 256), 128, W * 16);
+          const uint64_t bd = umma_desc(smem_addr(sB + (kx + 16 * ks) * 16), 128, (W + 2) * 16);
+          const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 32u * kx),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * st));
+    }
+  }
+  // the last commit completes after every product issued before it
+  if (it > 0) ok = ok && mbar_wait(bar0 + 8 * (int)((it - 1) & 1), (uint32_t)(((it - 1) >> 1) & 1));
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // warps w and w + 4 read TMEM lanes 32 (w % 4) .. + 31 (= output channels); of the six 16-column blocks
+    // (kx = block / 2) warps 0-3 take the first three, warps 4-7 the others
+    const int q = warp & 3;
+    const int co = co0 + q * 32 + lane;
+#pragma unroll 1
+    for (int blk = 3 * (warp >> 2); blk < 3 * (warp >> 2) + 3; ++blk) {
+      const int kx = blk >> 1, c0 = (blk & 1) * 16;
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(32 * kx + c0)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (co < cout && c0 < cgb * 8) {
+        float* dst = part + (((long long)blockIdx.z * 9 + 3 * ky + kx) * cout + co) * cin + ci0 + c0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          const float4 o = it > 0 ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(dst + j) = o;
         }
       }
     }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < kSeg / 16; ++ks) {
-      const int k0 = ks * 16 + 2 * t;
-      uint32_t a[2][4];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        a[mt][0] = *reinterpret_cast<const uint32_t*>(&sdy[mt * 16 + g][k0]);
-        a[mt][1] = *reinterpret_cast<const uint32_t*>(&sdy[mt * 16 + g + 8][k0]);
-        a[mt][2] = *reinterpret_cast<const uint32_t*>(&sdy[mt * 16 + g][k0 + 8]);
-        a[mt][3] = *reinterpret_cast<const uint32_t*>(&sdy[mt * 16 + g + 8][k0 + 8]);
-      }
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&sx[kx][ky][nt * 8 + g][k0]);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&sx[kx][ky][nt * 8 + g][k0 + 8]);
-        mma_bf16(acc[0][nt], a[0], b0, b1);
-        mma_bf16(acc[1][nt], a[1], b0, b1);
-      }
-    }
+  } else if (tid == 0) {
+    atomicExch(&g_nn_fault, 1u);
   }
-  // acc[mt][nt]: rows co0 + 16 mt + g (+8), columns ci0 + 8 nt + 2 t (+1)
-  const int tap = warp;
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int co = co0 + mt * 16 + g + 8 * half;
-      if (co >= cout) continue;
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int ci = ci0 + nt * 8 + 2 * t;
-        if (ci >= cin) continue;
-        *reinterpret_cast<float2*>(part + (((long long)blockIdx.z * 9 + tap) * cout + co) * cin + ci) =
-            make_float2(acc[mt][nt][2 * half], acc[mt][nt][2 * half + 1]);
-      }
-    }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
 }
 
 // out[i] = sum_z part[z][i]: 8 lanes per output take the chunks z = lane, lane + 8, ... in order, then the 8 lane
@@ -706,16 +757,19 @@ namespace {
 
 constexpr long long kBiasChunk = 4096;
 
-// row segments per CTA of the weight gradient: about four CTAs per SM over the (co, ci) tiles
+// row segments per CTA of the weight gradient: at most four CTAs per SM (the TMEM of 4 x 128 columns) over the
+// (co, ky, ci) tiles, so that every CTA is resident in one wave
 struct WgradPlan {
-  long long segs, per_chunk, chunks, bias_chunks;
+  int W;
+  long long segs, per_chunk, chunks, bias_chunks, tiles;
 };
 
 WgradPlan wgrad_plan(int n, int h, int w, int cin, int cout) {
   WgradPlan p;
-  p.segs = (long long)n * h * ((w + kSeg - 1) / kSeg);
-  const long long tiles = (long long)((cout + 31) / 32) * ((cin + 31) / 32);
-  const long long want = std::max(1LL, (4LL * 152 + tiles - 1) / tiles);
+  p.W = w >= 64 ? 64 : 32;
+  p.segs = (long long)n * h * ((w + p.W - 1) / p.W);
+  p.tiles = (long long)((cout + kWtM - 1) / kWtM) * 3 * ((cin + kWtN - 1) / kWtN);
+  const long long want = std::max(1LL, (4LL * 152) / p.tiles);
   p.per_chunk = std::max(1LL, (p.segs + want - 1) / want);
   p.chunks = (p.segs + p.per_chunk - 1) / p.per_chunk;
   p.bias_chunks = ((long long)n * h * w + kBiasChunk - 1) / kBiasChunk;
@@ -740,8 +794,23 @@ int lbm_nn_conv3x3_wgrad(const float* x, const float* dy, float* dw, float* db, 
   cudaStream_t s = (cudaStream_t)stream;
   const WgradPlan p = wgrad_plan(n, h, w, cin, cout);
   const long long nw = 9LL * cin * cout;
-  dim3 grid((cout + 31) / 32, (cin + 31) / 32, (unsigned)p.chunks);
-  conv3x3_wgrad_seg<<<grid, kWgThreads, 0, s>>>(x, dy, work, n, h, w, cin, cout, p.per_chunk);
+  if (p.chunks > 65535) return -1;
+  static unsigned long long attr_set = 0;   // shared-memory opt-in, per device
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -3;
+  if (!(attr_set & (1ull << dev))) {
+    if (cudaFuncSetAttribute((const void*)conv3x3_wgrad_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             WgTcSmem<64>::bytes()) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)conv3x3_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             WgTcSmem<32>::bytes()) != cudaSuccess)
+      return -3;
+    attr_set |= 1ull << dev;
+  }
+  const dim3 grid((cout + kWtM - 1) / kWtM, 3 * ((cin + kWtN - 1) / kWtN), (unsigned)p.chunks);
+  if (p.W == 64)
+    conv3x3_wgrad_tc<64><<<grid, kWtThreads, WgTcSmem<64>::bytes(), s>>>(x, dy, work, n, h, w, cin, cout, p.per_chunk);
+  else
+    conv3x3_wgrad_tc<32><<<grid, kWtThreads, WgTcSmem<32>::bytes(), s>>>(x, dy, work, n, h, w, cin, cout, p.per_chunk);
   sum_parts<<<(unsigned)((nw + 31) / 32), 256, 0, s>>>(work, dw, nw, (int)p.chunks);
   if (db) {
     float* bpart = work + p.chunks * nw;
