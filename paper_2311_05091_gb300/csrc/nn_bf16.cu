@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_fwd_tc(const float* __rest
 // a stage is refilled only after the bounded wait for the products that read it.
 // grid (cout tiles of 128, 3 x cin tiles of 32, chunks), 256 threads.
 // ---------------------------------------------------------------------------
-constexpr int kWtM = 128, kWtN = 32, kWtThreads = 256;
+constexpr int kWtM = 128, kWtN = 32, kWtThreads = 256, kWtBatch = 4;
 
 template <int W>
 struct WgTcSmem {
@@ -315,33 +315,43 @@ __global__ void __launch_bounds__(kWtThreads) conv3x3_wgrad_tc(const float* __re
     const int img = (int)(sg / ((long long)h * spr));
     const int y = (int)((sg / spr) % h);
     const int x0 = (int)(sg % spr) * W;
-    // A: dy of pixels x0 .. x0 + W - 1 of row y, then B: x of row y + ky - 1 at columns x0 - 1 .. x0 + W, in one
-    // loop (unrolled so that the loads of several items are in flight before their conversions)
+    // A: dy of pixels x0 .. x0 + W - 1 of row y, then B: x of row y + ky - 1 at columns x0 - 1 .. x0 + W, in
+    // batches of kWtBatch items per thread whose global loads are all issued before the first conversion and
+    // shared store (a store may not be moved above a later load through pointers that could alias)
     const int yy = y + ky - 1;
     const bool row_in = yy >= 0 && yy < h;
     const int nA = cga * W, nAB = nA + cgb * (W + 2);
-#pragma unroll 4
-    for (int e = tid; e < nAB; e += kWtThreads) {
-      const float* src = nullptr;
-      unsigned char* dst;
-      if (e < nA) {
-        const int px = e % W, cg = e / W;
-        const int xc = x0 + px;
-        if (xc < w) src = dy + (((long long)img * h + y) * w + xc) * cout + co0 + 8 * cg;
-        dst = sA + (cg * W + px) * 16;
-      } else {
-        const int j = (e - nA) % (W + 2), cg = (e - nA) / (W + 2);
-        const int xc = x0 + j - 1;
-        if (row_in && xc >= 0 && xc < w) src = x + (((long long)img * h + yy) * w + xc) * cin + ci0 + 8 * cg;
-        dst = sB + (cg * (W + 2) + j) * 16;
+    for (int e0 = 0; e0 < nAB; e0 += kWtBatch * kWtThreads) {
+      float4 pv[kWtBatch], qv[kWtBatch];
+      int off[kWtBatch];   // destination byte offset from sA, -1: none
+#pragma unroll
+      for (int k = 0; k < kWtBatch; ++k) {
+        const int e = e0 + k * kWtThreads + tid;
+        const float* src = nullptr;
+        off[k] = -1;
+        if (e < nA) {
+          const int px = e % W, cg = e / W;
+          const int xc = x0 + px;
+          if (xc < w) src = dy + (((long long)img * h + y) * w + xc) * cout + co0 + 8 * cg;
+          off[k] = (cg * W + px) * 16;
+        } else if (e < nAB) {
+          const int j = (e - nA) % (W + 2), cg = (e - nA) / (W + 2);
+          const int xc = x0 + j - 1;
+          if (row_in && xc >= 0 && xc < w) src = x + (((long long)img * h + yy) * w + xc) * cin + ci0 + 8 * cg;
+          off[k] = SM::kA + (cg * (W + 2) + j) * 16;
+        }
+        pv[k] = qv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (src) {
+          pv[k] = __ldg(reinterpret_cast<const float4*>(src));
+          qv[k] = __ldg(reinterpret_cast<const float4*>(src + 4));
+        }
       }
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (src) {
-        const float4 p = *reinterpret_cast<const float4*>(src);
-        const float4 q = *reinterpret_cast<const float4*>(src + 4);
-        v = make_uint4(pack_bf16(p.x, p.y), pack_bf16(p.z, p.w), pack_bf16(q.x, q.y), pack_bf16(q.z, q.w));
-      }
-      *reinterpret_cast<uint4*>(dst) = v;
+#pragma unroll
+      for (int k = 0; k < kWtBatch; ++k)
+        if (off[k] >= 0)
+          *reinterpret_cast<uint4*>(sA + off[k]) =
+              make_uint4(pack_bf16(pv[k].x, pv[k].y), pack_bf16(pv[k].z, pv[k].w), pack_bf16(qv[k].x, qv[k].y),
+                         pack_bf16(qv[k].z, qv[k].w));
     }
     asm volatile("fence.proxy.async.shared::cta;");       // generic-proxy stores visible to the tensor cores
     asm volatile("tcgen05.fence::before_thread_sync;");
