@@ -80,6 +80,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 constexpr int kTcM = 128;
 constexpr int kTcThreads = 256;   // 8 warps stage the tiles; warps w and w + 4 share TMEM lane quarter w % 4
+constexpr int kFwdBatch = 3;      // staging items whose loads a thread has in flight at once
 
 // (A, B) tiles in S stages: with two, one chunk is staged while the tensor cores multiply the previous one.
 // Two stages pay only where the tiles are small enough to keep several CTAs per SM (measured on GB300: wide
@@ -142,30 +143,46 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_fwd_tc(const float* __rest
     unsigned char* sB = sA + SM::kA;
     // the products of chunk c - S read this stage: wait for them (phase (c - S) / S of this stage's barrier)
     if (c >= S) ok = ok && mbar_wait(bar0 + 8 * st, ((c - S) / S) & 1);
-    // A: WIDE, one copy of rows y0 - 1 .. y0 + 1 at columns x0 - 1 .. x0 + 128; else one copy per kx
-    // (unrolled so that several iterations' global loads are in flight before their conversions)
-#pragma unroll 4
-    for (int e = tid; e < (WIDE ? 2 : 6) * rows * pitch; e += kTcThreads) {
-      const int px = e % pitch, r = (e / pitch) % rows, kc = (e / (pitch * rows)) & 1;
-      const int kx = WIDE ? 0 : e / (pitch * rows * 2);
-      const int yy = y0 + r - 1, xc = x0 + px + kx - 1;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (yy >= 0 && yy < h && xc >= 0 && xc < w) {
-        const float* src = x + (((long long)img * h + yy) * w + xc) * cin + ci0 + 8 * kc;
-        const float4 a = *reinterpret_cast<const float4*>(src);
-        const float4 b = *reinterpret_cast<const float4*>(src + 4);
-        v = make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, b.w));
-      }
-      *reinterpret_cast<uint4*>(sA + (((kx * 2 + kc) * rows + r) * pitch + px) * 16) = v;
-    }
-    // B: weights of the nine taps
-#pragma unroll 4
+    // B: the BF16 weights of the nine taps, copied asynchronously (16 bytes, no register round trip)
     for (int e = tid; e < 18 * N; e += kTcThreads) {
       const int co = e % N, kc = (e / N) & 1, tap = e / (2 * N);
-      const uint4 v =
-          *reinterpret_cast<const uint4*>(wt + ((long long)tap * cout + co0 + co) * cin + ci0 + 8 * kc);
-      *reinterpret_cast<uint4*>(sB + ((tap * 2 + kc) * N + co) * 16) = v;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(sB + ((tap * 2 + kc) * N + co) * 16)),
+                   "l"(wt + ((long long)tap * cout + co0 + co) * cin + ci0 + 8 * kc)
+                   : "memory");
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // A: WIDE, one copy of rows y0 - 1 .. y0 + 1 at columns x0 - 1 .. x0 + 128; else one copy per kx.  The global
+    // loads of kFwdBatch items per thread are issued before their conversions and shared stores (a store may not
+    // be moved above a later load through pointers that could alias)
+    const int nA = (WIDE ? 2 : 6) * rows * pitch;
+    for (int e0 = 0; e0 < nA; e0 += kFwdBatch * kTcThreads) {
+      float4 pv[kFwdBatch], qv[kFwdBatch];
+      int off[kFwdBatch];   // destination byte offset from sA, -1: none
+#pragma unroll
+      for (int k = 0; k < kFwdBatch; ++k) {
+        const int e = e0 + k * kTcThreads + tid;
+        off[k] = -1;
+        pv[k] = qv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < nA) {
+          const int px = e % pitch, r = (e / pitch) % rows, kc = (e / (pitch * rows)) & 1;
+          const int kx = WIDE ? 0 : e / (pitch * rows * 2);
+          const int yy = y0 + r - 1, xc = x0 + px + kx - 1;
+          off[k] = (((kx * 2 + kc) * rows + r) * pitch + px) * 16;
+          if (yy >= 0 && yy < h && xc >= 0 && xc < w) {
+            const float* src = x + (((long long)img * h + yy) * w + xc) * cin + ci0 + 8 * kc;
+            pv[k] = __ldg(reinterpret_cast<const float4*>(src));
+            qv[k] = __ldg(reinterpret_cast<const float4*>(src + 4));
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kFwdBatch; ++k)
+        if (off[k] >= 0)
+          *reinterpret_cast<uint4*>(sA + off[k]) =
+              make_uint4(pack_bf16(pv[k].x, pv[k].y), pack_bf16(pv[k].z, pv[k].w), pack_bf16(qv[k].x, qv[k].y),
+                         pack_bf16(qv[k].z, qv[k].w));
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;");       // generic-proxy stores visible to the tensor cores
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
