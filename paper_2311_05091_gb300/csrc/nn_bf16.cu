@@ -431,6 +431,165 @@ __global__ void __launch_bounds__(kWtThreads) conv3x3_wgrad_tc(const float* __re
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
 }
 
+// ---------------------------------------------------------------------------
+// weight gradient for at most 32 output channels: the three kernel rows folded into the 128 rows of M.
+// With q = p + shift(tap), part[z][tap][co][ci] = sum_q dy[q - shift(tap)][co] x[q][ci]: for a segment of W
+// pixels q of row y, B is x of those pixels (32 input channels, unshifted) and A row (ky, co), 32 ky + co, is dy
+// of image row y - ky + 1, so one product per column offset kx covers the three kernel rows:
+// D_kx (128 x 32, rows 96 .. 127 zero, TMEM columns 32 kx ..) += A_kx (128 x 16 pixels) * B^T (32 x 16 pixels).
+// Both operands are BF16 in the canonical MN-major layout without swizzle, as in conv3x3_wgrad_tc:
+//   A: [ky][co group][column] for columns x0 - 1 .. x0 + W of dy rows y + 1, y, y - 1; the window of kx starts
+//      2 - kx columns (16 (2 - kx) bytes) in;
+//   B: [ci group][pixel] for pixels x0 .. x0 + W - 1 of x row y.
+// grid (1, cin tiles of 32, chunks), 256 threads, two stages.
+// ---------------------------------------------------------------------------
+template <int W>
+struct WgRowsSmem {
+  static constexpr int kA = (kWtM / 8) * (W + 2) * 16;
+  static constexpr int kB = (kWtN / 8) * W * 16;
+  static constexpr int kStage = kA + kB;
+  static constexpr int bytes() { return 2 * kStage + 64; }
+};
+
+template <int W>
+__global__ void __launch_bounds__(kWtThreads) conv3x3_wgrad_tc_rows(const float* __restrict__ x,
+                                                                  const float* __restrict__ dy,
+                                                                  float* __restrict__ part, int n, int h, int w,
+                                                                  int cin, int cout, long long segs_per_chunk) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  using SM = WgRowsSmem<W>;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::kStage);   // one mbarrier per stage
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ci0 = blockIdx.y * kWtN;
+  const int spr = (w + W - 1) / W;                           // segments per image row
+  const long long nseg = (long long)n * h * spr;
+  const long long s0 = (long long)blockIdx.z * segs_per_chunk;
+  const long long s1 = min(nseg, s0 + segs_per_chunk);
+  const int cga = min(32, cout) / 8, cgb = min(kWtN, cin - ci0) / 8;   // channel groups present
+  const uint32_t bar0 = smem_addr(bar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int k = 0; k < 2; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8 * k), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // both stages start zero: the channel groups that are not present, and rows 96 .. 127 of A, stay so
+  for (int e = tid; e < 2 * SM::kStage / 16; e += kWtThreads)
+    *reinterpret_cast<uint4*>(smem + 16 * e) = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+
+  bool ok = true;
+  long long it = 0;
+  for (long long sg = s0; sg < s1; ++sg, ++it) {
+    const int st = (int)(it & 1);
+    unsigned char* sA = smem + st * SM::kStage;
+    // the products of segment it - 2 read this stage: wait for them (phase (it - 2) / 2 of its barrier)
+    if (it >= 2) ok = ok && mbar_wait(bar0 + 8 * st, (uint32_t)(((it - 2) >> 1) & 1));
+    const int img = (int)(sg / ((long long)h * spr));
+    const int y = (int)((sg / spr) % h);
+    const int x0 = (int)(sg % spr) * W;
+    // A: dy rows y + 1, y, y - 1 (ky = 0, 1, 2) at columns x0 - 1 .. x0 + W; then B: x row y at x0 .. x0 + W - 1.
+    // The global loads of kWtBatch items per thread are issued before their conversions and shared stores.
+    const int nA = 3 * cga * (W + 2), nAB = nA + cgb * W;
+    for (int e0 = 0; e0 < nAB; e0 += kWtBatch * kWtThreads) {
+      float4 pv[kWtBatch], qv[kWtBatch];
+      int off[kWtBatch];   // destination byte offset from sA, -1: none
+#pragma unroll
+      for (int k = 0; k < kWtBatch; ++k) {
+        const int e = e0 + k * kWtThreads + tid;
+        const float* src = nullptr;
+        off[k] = -1;
+        if (e < nA) {
+          const int j = e % (W + 2), cg = (e / (W + 2)) % cga, ky = e / ((W + 2) * cga);
+          const int yy = y - ky + 1, xc = x0 + j - 1;
+          if (yy >= 0 && yy < h && xc >= 0 && xc < w) src = dy + (((long long)img * h + yy) * w + xc) * cout + 8 * cg;
+          off[k] = ((ky * 4 + cg) * (W + 2) + j) * 16;
+        } else if (e < nAB) {
+          const int j = (e - nA) % W, cg = (e - nA) / W;
+          const int xc = x0 + j;
+          if (xc < w) src = x + (((long long)img * h + y) * w + xc) * cin + ci0 + 8 * cg;
+          off[k] = SM::kA + (cg * W + j) * 16;
+        }
+        pv[k] = qv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (src) {
+          pv[k] = __ldg(reinterpret_cast<const float4*>(src));
+          qv[k] = __ldg(reinterpret_cast<const float4*>(src + 4));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kWtBatch; ++k)
+        if (off[k] >= 0)
+          *reinterpret_cast<uint4*>(sA + off[k]) =
+              make_uint4(pack_bf16(pv[k].x, pv[k].y), pack_bf16(pv[k].z, pv[k].w), pack_bf16(qv[k].x, qv[k].y),
+                         pack_bf16(qv[k].z, qv[k].w));
+    }
+    asm volatile("fence.proxy.async.shared::cta;");       // generic-proxy stores visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0 && ok) {
+      constexpr uint32_t idesc = umma_idesc_mn(kWtM, kWtN);
+#pragma unroll 1
+      for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+        for (int ks = 0; ks < W / 16; ++ks) {
+          const uint64_t ad = umma_desc(smem_addr(sA + (2 - kx + 16 * ks) * 16), 128, (W + 2) * 16);
+          const uint64_t bd = umma_desc(smem_addr(sA + SM::kA + ks * 256), 128, W * 16);
+          const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 32u * kx),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * st));
+    }
+  }
+  // the last commit completes after every product issued before it
+  if (it > 0) ok = ok && mbar_wait(bar0 + 8 * (int)((it - 1) & 1), (uint32_t)(((it - 1) >> 1) & 1));
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // warps w and w + 4 read TMEM lanes 32 (w % 4) .. + 31 = (ky = w % 4, co); lanes 96 .. 127 are the zero rows.
+    // Of the six 16-column blocks (kx = block / 2) warps 0-3 take the first three, warps 4-7 the others.
+    const int ky = warp & 3, co = lane;
+#pragma unroll 1
+    for (int blk = 3 * (warp >> 2); blk < 3 * (warp >> 2) + 3; ++blk) {
+      const int kx = blk >> 1, c0 = (blk & 1) * 16;
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(ky * 32) << 16) + (uint32_t)(32 * kx + c0)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (ky < 3 && co < cout && c0 < cgb * 8) {
+        float* dst = part + (((long long)blockIdx.z * 9 + 3 * ky + kx) * cout + co) * cin + ci0 + c0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          const float4 o = it > 0 ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<float4*>(dst + j) = o;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(&g_nn_fault, 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
 // out[i] = sum_z part[z][i]: 8 lanes per output take the chunks z = lane, lane + 8, ... in order, then the 8 lane
 // sums are added in a fixed tree (deterministic).  Block = 32 outputs x 8 lanes.
 __global__ void __launch_bounds__(256) sum_parts(const float* __restrict__ part, float* __restrict__ out, long long n,
@@ -795,7 +954,9 @@ WgradPlan wgrad_plan(int n, int h, int w, int cin, int cout) {
   WgradPlan p;
   p.W = w >= 64 ? 64 : 32;
   p.segs = (long long)n * h * ((w + p.W - 1) / p.W);
-  p.tiles = (long long)((cout + kWtM - 1) / kWtM) * 3 * ((cin + kWtN - 1) / kWtN);
+  // at most 32 output channels: the kernel rows folded into M (one CTA per cin tile); else one CTA per kernel row
+  p.tiles = cout <= 32 ? (long long)((cin + kWtN - 1) / kWtN)
+                       : (long long)((cout + kWtM - 1) / kWtM) * 3 * ((cin + kWtN - 1) / kWtN);
   const long long want = std::max(1LL, (4LL * 152) / p.tiles);
   p.per_chunk = std::max(1LL, (p.segs + want - 1) / want);
   p.chunks = (p.segs + p.per_chunk - 1) / p.per_chunk;
@@ -829,15 +990,31 @@ int lbm_nn_conv3x3_wgrad(const float* x, const float* dy, float* dw, float* db, 
     if (cudaFuncSetAttribute((const void*)conv3x3_wgrad_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              WgTcSmem<64>::bytes()) != cudaSuccess ||
         cudaFuncSetAttribute((const void*)conv3x3_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             WgTcSmem<32>::bytes()) != cudaSuccess)
+                             WgTcSmem<32>::bytes()) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)conv3x3_wgrad_tc_rows<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             WgRowsSmem<64>::bytes()) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)conv3x3_wgrad_tc_rows<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             WgRowsSmem<32>::bytes()) != cudaSuccess)
       return -3;
     attr_set |= 1ull << dev;
   }
-  const dim3 grid((cout + kWtM - 1) / kWtM, 3 * ((cin + kWtN - 1) / kWtN), (unsigned)p.chunks);
-  if (p.W == 64)
-    conv3x3_wgrad_tc<64><<<grid, kWtThreads, WgTcSmem<64>::bytes(), s>>>(x, dy, work, n, h, w, cin, cout, p.per_chunk);
-  else
-    conv3x3_wgrad_tc<32><<<grid, kWtThreads, WgTcSmem<32>::bytes(), s>>>(x, dy, work, n, h, w, cin, cout, p.per_chunk);
+  if (cout <= 32) {
+    const dim3 grid(1, (cin + kWtN - 1) / kWtN, (unsigned)p.chunks);
+    if (p.W == 64)
+      conv3x3_wgrad_tc_rows<64><<<grid, kWtThreads, WgRowsSmem<64>::bytes(), s>>>(x, dy, work, n, h, w, cin, cout,
+                                                                                  p.per_chunk);
+    else
+      conv3x3_wgrad_tc_rows<32><<<grid, kWtThreads, WgRowsSmem<32>::bytes(), s>>>(x, dy, work, n, h, w, cin, cout,
+                                                                                  p.per_chunk);
+  } else {
+    const dim3 grid((cout + kWtM - 1) / kWtM, 3 * ((cin + kWtN - 1) / kWtN), (unsigned)p.chunks);
+    if (p.W == 64)
+      conv3x3_wgrad_tc<64><<<grid, kWtThreads, WgTcSmem<64>::bytes(), s>>>(x, dy, work, n, h, w, cin, cout,
+                                                                           p.per_chunk);
+    else
+      conv3x3_wgrad_tc<32><<<grid, kWtThreads, WgTcSmem<32>::bytes(), s>>>(x, dy, work, n, h, w, cin, cout,
+                                                                           p.per_chunk);
+  }
   sum_parts<<<(unsigned)((nw + 31) / 32), 256, 0, s>>>(work, dw, nw, (int)p.chunks);
   if (db) {
     float* bpart = work + p.chunks * nw;
