@@ -432,7 +432,8 @@ __global__ void __launch_bounds__(kWtThreads) conv3x3_wgrad_tc(const float* __re
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient for at most 32 output channels: the three kernel rows folded into the 128 rows of M.
+// weight gradient for at most 64 output channels: the three kernel rows folded into the 128 rows of M, 32
+// output channels per CTA.
 // With q = p + shift(tap), part[z][tap][co][ci] = sum_q dy[q - shift(tap)][co] x[q][ci]: for a segment of W
 // pixels q of row y, B is x of those pixels (32 input channels, unshifted) and A row (ky, co), 32 ky + co, is dy
 // of image row y - ky + 1, so one product per column offset kx covers the three kernel rows:
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(kWtThreads) conv3x3_wgrad_tc(const float* __re
 //   A: [ky][co group][column] for columns x0 - 1 .. x0 + W of dy rows y + 1, y, y - 1; the window of kx starts
 //      2 - kx columns (16 (2 - kx) bytes) in;
 //   B: [ci group][pixel] for pixels x0 .. x0 + W - 1 of x row y.
-// grid (1, cin tiles of 32, chunks), 256 threads, two stages.
+// grid (cout tiles of 32, cin tiles of 32, chunks), 256 threads, two stages.
 // ---------------------------------------------------------------------------
 template <int W>
 struct WgRowsSmem {
@@ -461,12 +462,12 @@ __global__ void __launch_bounds__(kWtThreads) conv3x3_wgrad_tc_rows(const float*
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::kStage);   // one mbarrier per stage
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ci0 = blockIdx.y * kWtN;
+  const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * kWtN;
   const int spr = (w + W - 1) / W;                           // segments per image row
   const long long nseg = (long long)n * h * spr;
   const long long s0 = (long long)blockIdx.z * segs_per_chunk;
   const long long s1 = min(nseg, s0 + segs_per_chunk);
-  const int cga = min(32, cout) / 8, cgb = min(kWtN, cin - ci0) / 8;   // channel groups present
+  const int cga = min(32, cout - co0) / 8, cgb = min(kWtN, cin - ci0) / 8;   // channel groups present
   const uint32_t bar0 = smem_addr(bar);
 
   if (warp == 0) {
@@ -510,7 +511,8 @@ __global__ void __launch_bounds__(kWtThreads) conv3x3_wgrad_tc_rows(const float*
         if (e < nA) {
           const int j = e % (W + 2), cg = (e / (W + 2)) % cga, ky = e / ((W + 2) * cga);
           const int yy = y - ky + 1, xc = x0 + j - 1;
-          if (yy >= 0 && yy < h && xc >= 0 && xc < w) src = dy + (((long long)img * h + yy) * w + xc) * cout + 8 * cg;
+          if (yy >= 0 && yy < h && xc >= 0 && xc < w)
+            src = dy + (((long long)img * h + yy) * w + xc) * cout + co0 + 8 * cg;
           off[k] = ((ky * 4 + cg) * (W + 2) + j) * 16;
         } else if (e < nAB) {
           const int j = (e - nA) % W, cg = (e - nA) / W;
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(kWtThreads) conv3x3_wgrad_tc_rows(const float*
   if (ok) {
     // warps w and w + 4 read TMEM lanes 32 (w % 4) .. + 31 = (ky = w % 4, co); lanes 96 .. 127 are the zero rows.
     // Of the six 16-column blocks (kx = block / 2) warps 0-3 take the first three, warps 4-7 the others.
-    const int ky = warp & 3, co = lane;
+    const int ky = warp & 3, co = co0 + lane;
 #pragma unroll 1
     for (int blk = 3 * (warp >> 2); blk < 3 * (warp >> 2) + 3; ++blk) {
       const int kx = blk >> 1, c0 = (blk & 1) * 16;
@@ -954,8 +956,9 @@ WgradPlan wgrad_plan(int n, int h, int w, int cin, int cout) {
   WgradPlan p;
   p.W = w >= 64 ? 64 : 32;
   p.segs = (long long)n * h * ((w + p.W - 1) / p.W);
-  // at most 32 output channels: the kernel rows folded into M (one CTA per cin tile); else one CTA per kernel row
-  p.tiles = cout <= 32 ? (long long)((cin + kWtN - 1) / kWtN)
+  // at most 64 output channels: the kernel rows folded into M (a CTA per 32 x 32 channel tile); else a CTA per
+  // kernel row and 128 x 32 tile
+  p.tiles = cout <= 64 ? (long long)((cout + 31) / 32) * ((cin + kWtN - 1) / kWtN)
                        : (long long)((cout + kWtM - 1) / kWtM) * 3 * ((cin + kWtN - 1) / kWtN);
   const long long want = std::max(1LL, (4LL * 152) / p.tiles);
   p.per_chunk = std::max(1LL, (p.segs + want - 1) / want);
@@ -998,8 +1001,8 @@ int lbm_nn_conv3x3_wgrad(const float* x, const float* dy, float* dw, float* db, 
       return -3;
     attr_set |= 1ull << dev;
   }
-  if (cout <= 32) {
-    const dim3 grid(1, (cin + kWtN - 1) / kWtN, (unsigned)p.chunks);
+  if (cout <= 64) {
+    const dim3 grid((cout + 31) / 32, (cin + kWtN - 1) / kWtN, (unsigned)p.chunks);
     if (p.W == 64)
       conv3x3_wgrad_tc_rows<64><<<grid, kWtThreads, WgRowsSmem<64>::bytes(), s>>>(x, dy, work, n, h, w, cin, cout,
                                                                                   p.per_chunk);
