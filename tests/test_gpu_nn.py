@@ -71,7 +71,7 @@ def test_conv3x3_forward(nn, n, h, w, cin, cout, relu):
 
 # cout <= 64 runs the kernel with the three kernel rows folded into M, cout >= 128 the one with a CTA per kernel row
 WGRAD_SHAPES = [(2, 13, 17, 16, 32), (1, 70, 70, 32, 16), (1, 8, 8, 48, 32), (2, 40, 64, 64, 64), (1, 12, 70, 32, 128),
-                (1, 9, 40, 48, 256)]
+                (1, 9, 40, 48, 256), (1, 1, 3, 16, 16), (2, 2, 3, 16, 128)]   # the last two: images of one and two rows
 
 
 @pytest.mark.parametrize("n,h,w,cin,cout", WGRAD_SHAPES)
