@@ -46,3 +46,18 @@ def test_invalid_arguments_rejected(lbm_lib):
     assert lib.lbm_nn_project(p, 32, p, p, p, p, 191, 1, 8, 8, None) == -1
     assert lib.lbm_nn_relu_bwd(None, p, p, 4, None) == -1
     assert lib.lbm_nn_add(p, p, None, 1.0, 4, None) == -1
+
+
+def test_wgrad_plan_fits_one_wave(lbm_lib):
+    # the weight gradient's partial-sum chunks times its channel tiles never exceed the four CTAs per SM (of 152)
+    # that the TMEM allocation of 128 columns lets reside at once, so no CTA runs in a second wave
+    from paper_2311_05091_gb300 import _nn
+    lib = _nn.library()
+    for n, h, w, cin, cout in [(16, 256, 256, 32, 32), (16, 256, 256, 16, 32), (16, 128, 128, 64, 64),
+                               (16, 64, 64, 128, 128), (16, 32, 32, 256, 256), (16, 64, 64, 256, 128), (1, 1, 3, 16, 16)]:
+        ws = lib.lbm_nn_wgrad_workspace(n, h, w, cin, cout)
+        bias_chunks = -(-n * h * w // 4096)
+        chunks, rem = divmod(ws - bias_chunks * cout, 9 * cin * cout)
+        assert rem == 0 and chunks >= 1, (n, h, w, cin, cout, ws)
+        tiles = (-(-cout // 32)) * (-(-cin // 32)) if cout <= 64 else (-(-cout // 128)) * 3 * (-(-cin // 32))
+        assert chunks * tiles <= 4 * 152, (n, h, w, cin, cout, chunks, tiles)
