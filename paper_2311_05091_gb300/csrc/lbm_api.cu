@@ -80,6 +80,7 @@ struct lbm_ctx {
   long long total = 0;                 // nodes of all instances
   StepArgs* dargs[2] = {nullptr, nullptr};
   int4* ditems = nullptr;
+  unsigned int* dqueue = nullptr;   // work-item claims and finished CTAs of the batched kernel (zero between launches)
   int nitems = 0, items_cap = 0;
   // D3Q19 tensor maps of the step's input buffers, one set per starting buffer
   alignas(64) unsigned char d3maps[2][512];
@@ -419,7 +420,7 @@ cudaError_t launch_step(lbm_ctx* c, int from, bool observe, cudaStream_t s, cuda
   if (c->multi) {
     if (mid) cudaEventRecord(mid, s);
     return lbm::launch_d2q9_items(c->dargs[from], c->ditems, c->nitems, c->depth, c->g_half, 0, observe,
-                                  c->per[0] && c->per[1], s);
+                                  c->per[0] && c->per[1], c->dqueue, s);
   }
   const StepArgs a = step_args(c, from);
   cudaError_t e = cudaSuccess;
@@ -525,6 +526,7 @@ void free_all(lbm_ctx* c) {
   dev_free(c, c->dargs[0]);
   dev_free(c, c->dargs[1]);
   dev_free(c, c->ditems);
+  dev_free(c, c->dqueue);
   dev_free(c, c->phi0);
   dev_free(c, c->p);
   dev_free(c, c->mom);
@@ -748,6 +750,8 @@ static int create_impl(lbm_lattice lattice, int nbatch, const int* nxs, const in
   if (e == cudaSuccess && multi) {
     e = dalloc(c, &c->dargs[0], sizeof(StepArgs) * nbatch);
     if (e == cudaSuccess) e = dalloc(c, &c->dargs[1], sizeof(StepArgs) * nbatch);
+    if (e == cudaSuccess) e = dalloc(c, &c->dqueue, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(c->dqueue, 0, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = upload_multi(c);
   }
   if (e == cudaSuccess && is3d && lbm::d3q19_maps_bytes() <= sizeof(c->d3maps[0])) {

@@ -695,19 +695,37 @@ __global__ void __launch_bounds__(BX, 5) d2q9_step(const StepArgs a) {
   step_tile<OBS, D, GT, PER>(a, S, blockIdx.x * BX, blockIdx.y * a.strip, blockIdx.z);
 }
 
-// Persistent form for instances of different sizes: CTA k takes work items
-// k, k + gridDim.x, ...; item = (instance, x0, ys), with per-instance launch
-// arguments (base pointers of that instance, its sizes and strip).
+// Persistent form for instances of different sizes: every CTA claims the next
+// work item from a device counter (queue[0]) until the list is done, so CTAs
+// that drew smaller items take more of them; item = (instance, x0, ys), with
+// per-instance launch arguments (base pointers of that instance, its sizes and
+// strip).  Which CTA runs an item does not change its result.  The CTA that
+// finishes last (queue[1] counts finished CTAs) zeroes both counters for the
+// next launch on the stream.
 template <bool OBS, int D, typename GT, bool PER>
 __global__ void __launch_bounds__(BX, 5) d2q9_step_items(const StepArgs* __restrict__ args,
-                                                      const int4* __restrict__ items, int nitems) {
+                                                      const int4* __restrict__ items, int nitems,
+                                                      unsigned int* __restrict__ queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<D, GT>& S = *reinterpret_cast<StepSmem<D, GT>*>(smem_raw);
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(&queue[0], 1u);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();   // every thread has read the claim before the next one overwrites it
+    if (it >= nitems) break;
     const int4 w = items[it];
     const StepArgs a = args[w.x];
     step_tile<OBS, D, GT, PER>(a, S, w.y, w.z, 0);
     __syncthreads();   // shared memory is reused by the next item
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&queue[1], 1u) == gridDim.x - 1) {   // every other CTA has made its last claim
+      queue[0] = 0u;
+      queue[1] = 0u;
+    }
   }
 }
 
@@ -759,7 +777,7 @@ cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaSt
 
 template <int D, typename GT, bool PER>
 cudaError_t items_per(const StepArgs* args, const int4* items, int nitems, int grid, bool observe,
-                      cudaStream_t s) {
+                      unsigned int* queue, cudaStream_t s) {
   const size_t smem = step_smem_bytes<D, GT>();
   static std::atomic<unsigned long long> configured{0};
   if (cudaError_t e =
@@ -775,32 +793,32 @@ cudaError_t items_per(const StepArgs* args, const int4* items, int nitems, int g
   }
   if (grid > nitems) grid = nitems;
   if (grid < 1) return cudaSuccess;
-  if (observe) d2q9_step_items<true, D, GT, PER><<<grid, BX, smem, s>>>(args, items, nitems);
-  else d2q9_step_items<false, D, GT, PER><<<grid, BX, smem, s>>>(args, items, nitems);
+  if (observe) d2q9_step_items<true, D, GT, PER><<<grid, BX, smem, s>>>(args, items, nitems, queue);
+  else d2q9_step_items<false, D, GT, PER><<<grid, BX, smem, s>>>(args, items, nitems, queue);
   return cudaGetLastError();
 }
 
 template <int D, typename GT>
 cudaError_t items_depth(const StepArgs* args, const int4* items, int nitems, int grid, bool observe, bool periodic,
-                        cudaStream_t s) {
-  return periodic ? items_per<D, GT, true>(args, items, nitems, grid, observe, s)
-                  : items_per<D, GT, false>(args, items, nitems, grid, observe, s);
+                        unsigned int* queue, cudaStream_t s) {
+  return periodic ? items_per<D, GT, true>(args, items, nitems, grid, observe, queue, s)
+                  : items_per<D, GT, false>(args, items, nitems, grid, observe, queue, s);
 }
 
 template <typename GT>
 cudaError_t items_typed(const StepArgs* args, const int4* items, int nitems, int depth, int grid, bool observe,
-                        bool periodic, cudaStream_t s) {
+                        bool periodic, unsigned int* queue, cudaStream_t s) {
   switch (depth) {
-    case 1: return items_depth<1, GT>(args, items, nitems, grid, observe, periodic, s);
-    case 3: return items_depth<3, GT>(args, items, nitems, grid, observe, periodic, s);
-    default: return items_depth<2, GT>(args, items, nitems, grid, observe, periodic, s);
+    case 1: return items_depth<1, GT>(args, items, nitems, grid, observe, periodic, queue, s);
+    case 3: return items_depth<3, GT>(args, items, nitems, grid, observe, periodic, queue, s);
+    default: return items_depth<2, GT>(args, items, nitems, grid, observe, periodic, queue, s);
   }
 }
 
 cudaError_t launch_d2q9_items(const StepArgs* args, const int4* items, int nitems, int depth, int g_half, int grid,
-                              bool observe, bool periodic, cudaStream_t s) {
-  return g_half ? items_typed<__half>(args, items, nitems, depth, grid, observe, periodic, s)
-                : items_typed<float>(args, items, nitems, depth, grid, observe, periodic, s);
+                              bool observe, bool periodic, unsigned int* queue, cudaStream_t s) {
+  return g_half ? items_typed<__half>(args, items, nitems, depth, grid, observe, periodic, queue, s)
+                : items_typed<float>(args, items, nitems, depth, grid, observe, periodic, queue, s);
 }
 
 }  // namespace lbm

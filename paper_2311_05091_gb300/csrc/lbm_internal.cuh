@@ -98,8 +98,10 @@ cudaError_t launch_d2q9_step(const StepArgs& a, int nbatch, bool observe, cudaSt
 // instance's own base pointers, sizes and strip (device memory), items[k] =
 // (inst, x0, ys, 0).  grid <= 0 picks a persistent grid of SMs x occupancy.
 // periodic: every instance is periodic on both axes (no pushes meet walls).
+// queue: two zeroed device counters (item claims, finished CTAs), zero again
+// when the launch ends.
 cudaError_t launch_d2q9_items(const StepArgs* args, const int4* items, int nitems, int depth, int g_half, int grid,
-                              bool observe, bool periodic, cudaStream_t s);
+                              bool observe, bool periodic, unsigned int* queue, cudaStream_t s);
 
 // Velocity inlet (mode bit 0, x = 0) and pressure outlet (bit 1, x = nx - 1)
 // by non-equilibrium extrapolation, applied to the streamed populations of
